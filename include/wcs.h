@@ -1,0 +1,211 @@
+/*
+ * wcs.h -- C ABI of the GB300 Woodbury-circulant direct solver for the
+ * preconditioned TE combined-field integral equation on a convex 2D PEC
+ * contour (Consoli et al., "On the Fast Direct Solution of a Preconditioned
+ * Electromagnetic Integral Equation", arXiv 2203.13283).
+ *
+ * Conventions for every call:
+ *  - Complex numbers are interleaved (re, im) doubles (FP64).
+ *  - Blocks of right-hand sides / solutions are column-major N x B with a
+ *    leading dimension ld >= N (column c starts at element c * ld).
+ *  - "_dev" pointers are device pointers on the context's device; "_host"
+ *    pointers are host memory.  The caller owns every pointer it passes; the
+ *    library keeps no caller pointer after the call returns.  All device work
+ *    is ordered on the stream given to wcs_create; calls return after their
+ *    work is enqueued unless stated otherwise (calls that return host data,
+ *    and the setup calls, synchronise the stream).
+ *  - Every call returns a wcs_status; on failure wcs_last_error() describes
+ *    it (thread-local).  No exception crosses the ABI.
+ *  - Setup must proceed contour -> wcs_mesh -> wcs_assemble -> wcs_skeleton
+ *    -> wcs_factor -> solves; a call made before its prerequisites returns
+ *    WCS_ERR_STATE.  Setting a new contour or mesh invalidates later stages.
+ */
+#ifndef WCS_H
+#define WCS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wcs_ctx wcs_ctx;
+
+typedef enum wcs_status {
+  WCS_OK = 0,
+  WCS_ERR_ARG = 1,          /* invalid argument (null pointer, size, ld) */
+  WCS_ERR_NOT_CONVEX = 2,   /* contour has negative curvature somewhere */
+  WCS_ERR_CUDA = 3,         /* CUDA runtime error */
+  WCS_ERR_OOM = 4,          /* device allocation failed */
+  WCS_ERR_SINGULAR = 5,     /* capacitance matrix numerically singular */
+  WCS_ERR_RANK_CAP = 6,     /* skeleton reached max_rank before the tolerance */
+  WCS_ERR_NOT_CONVERGED = 7,/* iterative refinement did not reach its tolerance */
+  WCS_ERR_TIMEOUT = 8,      /* reserved: a bounded device wait gave up */
+  WCS_ERR_STATE = 9,        /* call made out of order */
+  WCS_ERR_UNSUPPORTED = 10  /* option combination not built */
+} wcs_status;
+
+typedef enum wcs_precision {
+  WCS_PREC_FP64 = 0,        /* every stage in complex FP64 */
+  WCS_PREC_MIXED = 1        /* reserved for the tensor-core form */
+} wcs_precision;
+
+/* Tunables.  Obtain defaults with wcs_default_options, then override. */
+typedef struct wcs_options {
+  int precision;      /* wcs_precision */
+  int q_far;          /* Gauss points per element for element pairs farther than near_band (default 6) */
+  int q_near;         /* Gauss points per element for near and singular pairs (default 12, max 16) */
+  int near_band;      /* periodic element distance treated as near (default 4) */
+  int block;          /* randomized sampling block width (default 32, max 64) */
+  int max_refine;     /* maximum iterative-refinement steps per solve (default 12) */
+  double refine_tol;  /* target relative residual ||b - C x|| / ||b|| per column (default 1e-12) */
+  int rhs_chunk;      /* right-hand sides processed per pass (default 256) */
+  int reserved[7];
+} wcs_options;
+
+typedef struct wcs_info {
+  int64_t N;          /* unknowns = elements */
+  double L;           /* perimeter of gamma (= perimeter of gamma_c) */
+  double h;           /* element length L / N */
+  double a;           /* radius of gamma_c, L / (2 pi); also the curvature average of k~ */
+  double k;           /* wavenumber */
+  double kt_re, kt_im;/* k~ = k + 0.4 i k^{1/3} a^{-2/3} (Sec. III) */
+  int rank;           /* skeleton rank (after wcs_skeleton), else -1 */
+  double norm_cc;     /* ||C_c||_2 = max |mu_C| (after wcs_assemble) */
+  double min_curvature; /* minimum curvature found by the convexity check */
+} wcs_info;
+
+typedef struct wcs_solve_info {
+  int refine_steps;   /* iterative-refinement steps taken (max over chunks) */
+  double rel_residual;/* max over columns of ||b - C x|| / ||b|| at exit */
+} wcs_solve_info;
+
+/* Operators selectable by wcs_apply / wcs_circulant_eigs. */
+typedef enum wcs_op {
+  WCS_OP_C = 0,       /* C of Eq. (6) on gamma */
+  WCS_OP_CH = 1,      /* C^H */
+  WCS_OP_CC = 2,      /* C_c: C on the equivalent circle (circulant) */
+  WCS_OP_CCH = 3,     /* C_c^H */
+  WCS_OP_CC_INV = 4,  /* C_c^{-1} */
+  WCS_OP_S = 5,       /* S^k~ Galerkin matrix on gamma */
+  WCS_OP_D = 6,       /* D^k */
+  WCS_OP_DT = 7,      /* D^k~ */
+  WCS_OP_N = 8,       /* N^k */
+  WCS_OP_G = 9,       /* Gram matrix of the hats */
+  WCS_OP_SKEL = 10    /* U V^T, the skeleton of C - C_c (Eq. 7) */
+} wcs_op;
+
+/* Library version string. */
+const char* wcs_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* wcs_last_error(void);
+
+/* Fill *opt with the defaults documented in wcs_options. */
+int wcs_default_options(wcs_options* opt);
+
+/* Create a solver context on the current CUDA device.  stream: a cudaStream_t
+ * (NULL = legacy default stream) on which all device work is ordered.  opt may
+ * be NULL for defaults. */
+int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream);
+
+/* Free every device buffer of ctx and the context itself (NULL is a no-op). */
+int wcs_destroy(wcs_ctx* ctx);
+
+/* --- contour gamma (Sec. II: a convex 2D contour), as r(theta) = rho(theta) (cos, sin) --- */
+/* Circle of radius a. */
+int wcs_contour_circle(wcs_ctx* ctx, double a);
+/* Ellipse x^2/ax^2 + y^2/ay^2 = 1. */
+int wcs_contour_ellipse(wcs_ctx* ctx, double ax, double ay);
+/* Superellipse |x/ax|^p + |y/ay|^p = 1 with p >= 2. */
+int wcs_contour_superellipse(wcs_ctx* ctx, double ax, double ay, double p);
+/* rho(theta) = sum_{m<count} cos_c[m] cos(m theta) + sin_c[m] sin(m theta); host arrays,
+ * count <= 64.  The unit circle is count = 1, cos_c[0] = 1. */
+int wcs_contour_fourier(wcs_ctx* ctx, int count, const double* cos_c, const double* sin_c);
+
+/* Mesh gamma uniformly in arc length with N piecewise-linear elements (Sec. V),
+ * node 0 at polar angle 0, and fix the wavenumbers: k > 0 as given, k <= 0 means
+ * 10 elements per wavelength (k = 2 pi (N/10) / L).  k~ follows Sec. III with
+ * a = L / (2 pi).  Builds the same mesh on the equivalent circle gamma_c.
+ * Rejects non-convex contours (WCS_ERR_NOT_CONVEX) and k h > 2.5. */
+int wcs_mesh(wcs_ctx* ctx, int64_t N, double k);
+
+/* Geometry and wavenumbers of the current mesh. */
+int wcs_query(const wcs_ctx* ctx, wcs_info* info);
+
+/* Positions, outward normals and curvature at arc lengths s_host[0..count):
+ * out_host receives 5 * count doubles (x, y, nx, ny, kappa blocks). */
+int wcs_geometry_sample(wcs_ctx* ctx, int64_t count, const double* s_host, double* out_host);
+
+/* Assemble the Galerkin matrices S^k~, D^k, D^k~, N^k of Eq. (4)/(5) on gamma
+ * (dense, FP64, device-resident) and the circulant eigenvalues of the same
+ * operators on gamma_c, from which mu_C of C_c (Eq. 6 on the circle) follows. */
+int wcs_assemble(wcs_ctx* ctx);
+
+/* Entries of (S~, D, D~, N) at (rows_host[t], cols_host[t]), computed point-wise
+ * with the same quadrature as wcs_assemble: out_host gets 4 * count complex
+ * values (operator-major).  Needs wcs_mesh only. */
+int wcs_operator_entries(wcs_ctx* ctx, int64_t count, const int64_t* rows_host,
+                         const int64_t* cols_host, double* out_host);
+
+/* mu_X(m), m = 0..N-1, of the circle operator X in {WCS_OP_G, S, D, DT, N, CC}:
+ * eigenvalue for the eigenvector exp(2 pi i m j / N).  out_dev: N complex. */
+int wcs_circulant_eigs(wcs_ctx* ctx, int op, double* out_dev);
+
+/* Y = op X for B columns (X, Y device, column-major, may not alias). */
+int wcs_apply(wcs_ctx* ctx, int op, int64_t B, const double* X_dev, int64_t ldx, double* Y_dev,
+              int64_t ldy);
+
+/* Skeleton C - C_c = U V^T (Eq. 7) by an adaptive blocked randomized range
+ * finder on the matrix-free operator C - C_c: Gaussian test blocks (Philox,
+ * seed), projected samples, stopping when every new projected sample has norm
+ * below tol * ||C_c||_2 / (10 sqrt(2/pi)), so ||C - C_c - U V^T|| <= tol ||C_c||
+ * with high probability.  U is orthonormal; V^T = U^H (C - C_c).  max_rank <= 0
+ * means N.  *rank_out receives the rank.  Returns WCS_ERR_RANK_CAP (with the
+ * skeleton kept) when max_rank is reached first. */
+int wcs_skeleton(wcs_ctx* ctx, double tol, int max_rank, uint64_t seed, int* rank_out);
+
+/* Factor C = C_c (I + C_c^{-1} U V^T) (Eq. 8): W = C_c^{-1} U by FFT, the
+ * capacitance matrix K = I + V^T W and its inverse, for the Woodbury identity
+ * of Eq. (9). */
+int wcs_factor(wcs_ctx* ctx);
+
+/* x = C^-1 b through Eq. (9) only (no refinement), B columns, device pointers. */
+int wcs_woodbury_apply(wcs_ctx* ctx, int64_t B, const double* b_dev, int64_t ldb, double* x_dev,
+                       int64_t ldx);
+
+/* Solve Eq. (5) for B plane waves with propagation angles angles_host[0..B)
+ * (radians, d = (cos, sin), phase reference at the origin): project
+ * e/eta and h (Eq. 4), form the preconditioned right-hand side of Eq. (5),
+ * apply Eq. (9), then refine x <- x + C^-1 (b - C x) until refine_tol.
+ * j_dev receives the hat coefficients of the current (N x B, ldj). */
+int wcs_solve_planewaves(wcs_ctx* ctx, int64_t B, const double* angles_host, double* j_dev,
+                         int64_t ldj, wcs_solve_info* info);
+
+/* Same as wcs_solve_planewaves with the solution returned in host memory
+ * (j_host, N x B, ldj); includes the device-to-host copy; synchronises. */
+int wcs_solve_planewaves_host(wcs_ctx* ctx, int64_t B, const double* angles_host, double* j_host,
+                              int64_t ldj, wcs_solve_info* info);
+
+/* Solve Eq. (5) for user Galerkin data e/eta and h (device, N x B, ld). */
+int wcs_solve_rhs(wcs_ctx* ctx, int64_t B, const double* e_dev, const double* h_dev, int64_t ld,
+                  double* j_dev, int64_t ldj, wcs_solve_info* info);
+
+/* Plane-wave Galerkin projections e/eta and h of Eq. (4) (device, N x B, ld). */
+int wcs_planewave_rhs(wcs_ctx* ctx, int64_t B, const double* angles_host, double* e_dev,
+                      double* h_dev, int64_t ld);
+
+/* Far field F(phi_o) for B currents (device j, N x B, ldj) at nphi observation
+ * angles: H^s ~ F e^{i k rho} / sqrt(rho).  F_dev: nphi x B, column-major, ldf. */
+int wcs_farfield(wcs_ctx* ctx, int64_t B, const double* j_dev, int64_t ldj, int nphi,
+                 const double* phi_host, double* F_dev, int64_t ldf);
+
+/* Host-only: product-integration weights of the near-field rule with q points
+ * (3 * q * q doubles: coincident, next-neighbour, previous-neighbour pairs). */
+int wcs_quadrature_tables(int q, double* out_host);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WCS_H */

@@ -221,3 +221,36 @@ def preconditioned(M):
     A1 = np.linalg.solve(G, 0.5 * G - M["D"])
     A2 = np.linalg.solve(G, M["N"])
     return (0.5 * G + M["Dt"]) @ A1 + M["S"] @ A2
+
+
+def entries(curve, N, k, kt, rows, cols, rules=None):
+    """Entries (rows[t], cols[t]) of (S~, D, D~, N), one element pair at a time.
+
+    Same definition and rules as assemble(); used for sampled checks at sizes
+    where the dense oracle would be too slow.  Returns a dict of complex arrays.
+    """
+    rules = rules or Rules()
+    geo = ElementGeometry(curve, N)
+    rows = np.asarray(rows, np.int64)
+    cols = np.asarray(cols, np.int64)
+    out = np.zeros((4, len(rows)), complex)
+    xg, wg = qd.gauss_legendre01(rules.q_far)
+    far_rule = qd.tensor_rule(rules.q_far)
+    for a in range(2):
+        for b in range(2):
+            e = (rows - a) % N
+            f = (cols - b) % N
+            d = np.abs(e - f)
+            d = np.minimum(d, N - d)
+            groups = [(d > rules.near, far_rule, None),
+                      ((d >= 2) & (d <= rules.near), rules.near_rule, None),
+                      ((d == 1) & ((e + 1) % N == f), rules.touch_next, "e_end"),
+                      ((d == 1) & ((e - 1) % N == f) & ((e + 1) % N != f), rules.touch_prev, "e_start"),
+                      (d == 0, rules.self_rule, "self")]
+            for mask, rule, kind in groups:
+                idx = np.nonzero(mask)[0]
+                if len(idx) == 0:
+                    continue
+                loc = _locals(geo, e[idx], f[idx], rule, k, kt, kind)
+                out[:, idx] += loc[:, a, b, :]
+    return {"S": out[0], "D": out[1], "Dt": out[2], "N": out[3]}

@@ -99,10 +99,20 @@ def touching_rule(rho_rule, n_v=16, shared="e_end"):
 # ---------------------------------------------------------------------------
 # Exact integrals of polynomial x logarithm over the unit square, used to take
 # the log singularity of g out of the coincident and touching element pairs.
-# Computed symbolically once (sympy), returned as floats.
+# The integrands reduce to int_0^1 P(t) log t dt with P a cubic polynomial
+# (exact through the moments int_0^1 t^n log t dt = -1/(n+1)^2) plus, for
+# the touching case, int_1^2 P(v) log v dv with log v analytic there.
 # ---------------------------------------------------------------------------
 
 _LOG_CACHE = {}
+
+
+def _poly_log_moment(fun, deg=3):
+    """int_0^1 fun(t) log t dt for a polynomial fun of degree <= deg."""
+    t, _ = gauss_legendre01(deg + 3)
+    V = np.vander(t, deg + 1, increasing=True)
+    c = np.linalg.lstsq(V, fun(t), rcond=None)[0]
+    return sum(cn * (-1.0 / (n + 1) ** 2) for n, cn in enumerate(c))
 
 
 def log_integrals(kind):
@@ -115,26 +125,38 @@ def log_integrals(kind):
     """
     if kind in _LOG_CACHE:
         return _LOG_CACHE[kind]
-    import sympy as sy
-    x, y, t = sy.symbols("x y t", positive=True)
-    phi = (1 - x, x)
-    psi = (1 - y, y)
+    phi = (lambda x: 1.0 - x, lambda x: x)
+    one = lambda x: np.ones_like(x)
+    yg, wg = gauss_legendre01(6)      # exact for the cubic inner integrands
+    vg, wv = gauss_legendre01(40)     # log v on [1, 2]
 
-    def integ(p):
+    def integ(f, g):
         if kind == "self":
-            # int int p log|x - y| = int_0^1 log t [int_0^{1-t} p(y+t, y) + p(y, y+t) dy] dt
-            inner = sy.integrate(p.subs({x: y + t}) + p.subs({x: y, y: y + t}, simultaneous=True),
-                                 (y, 0, 1 - t))
-            poly = sy.Poly(sy.expand(inner), t)
-            return sum(c * sy.Rational(-1, (n[0] + 1) ** 2) for n, c in poly.terms())
+            # int int f(x) g(y) log|x - y| = int_0^1 log t P(t) dt,
+            # P(t) = int_0^{1-t} f(y+t) g(y) + f(y) g(y+t) dy
+            def P(t):
+                y = (1.0 - t)[:, None] * yg[None, :]
+                w = (1.0 - t)[:, None] * wg[None, :]
+                return np.sum(w * (f(y + t[:, None]) * g(y) + f(y) * g(y + t[:, None])), axis=1)
+            return _poly_log_moment(P)
+        # touching: with a, b the distances from the shared vertex, d = a + b;
+        # F(a, b) is the integrand in those coordinates
         if kind == "e_end":
-            expr = p * sy.log((1 - x) + y)
+            F = lambda a, b: f(1.0 - a) * g(b)
         else:
-            expr = p * sy.log(x + (1 - y))
-        return sy.integrate(sy.integrate(expr, (x, 0, 1)), (y, 0, 1))
+            F = lambda a, b: f(a) * g(1.0 - b)
 
-    I = np.array([[float(sy.N(integ(sy.expand(phi[a] * psi[b])), 30)) for b in range(2)]
-                  for a in range(2)])
-    I1 = float(sy.N(integ(sy.Integer(1)), 30))
+        def Q(v):  # int over a of F(a, v - a), a in [max(0, v-1), min(1, v)]
+            lo, hi = np.maximum(0.0, v - 1.0), np.minimum(1.0, v)
+            a = lo[:, None] + (hi - lo)[:, None] * yg[None, :]
+            w = (hi - lo)[:, None] * wg[None, :]
+            return np.sum(w * F(a, v[:, None] - a), axis=1)
+        part1 = _poly_log_moment(Q)
+        v = 1.0 + vg
+        part2 = np.sum(wv * np.log(v) * Q(v))
+        return part1 + part2
+
+    I = np.array([[integ(phi[a], phi[b]) for b in range(2)] for a in range(2)])
+    I1 = integ(one, one)
     _LOG_CACHE[kind] = (I, I1)
     return I, I1

@@ -1,0 +1,138 @@
+// Internal interfaces between the translation units of the solver library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace wcs {
+
+// ---------------------------------------------------------------- geometry
+enum ContourFamily { FAM_CIRCLE = 0, FAM_ELLIPSE = 1, FAM_SUPERELLIPSE = 2, FAM_FOURIER = 3 };
+constexpr int kMaxFourier = 64;
+
+struct Contour {
+  int family;
+  double a;             // circle radius
+  double ax, ay, p;     // ellipse / superellipse
+  int nf;               // Fourier: number of coefficients (m = 0..nf-1)
+  double fc[kMaxFourier], fs[kMaxFourier];
+};
+
+// Structure-of-arrays point table: positions, unit outward normals, curvature.
+struct Points {
+  double *x = nullptr, *y = nullptr, *nx = nullptr, *ny = nullptr, *kappa = nullptr;
+  int64_t n = 0;
+};
+
+// Arc-length tables of a contour: panel cumulative lengths in theta.
+struct ArcTable {
+  double* cum = nullptr;  // P + 1 entries, cum[P] = L
+  int P = 0;
+  double L = 0.0;
+};
+
+int arc_table_build(const Contour& c, ArcTable& t, cudaStream_t s);
+// Points at arc lengths s_j = (e + xi[g]) * h for e < N, g < nq (index e*nq + g).
+int points_build(const Contour& c, const ArcTable& t, int64_t N, double h, const double* xi_dev,
+                 int nq, Points& out, cudaStream_t s);
+// Minimum curvature over a dense sample of the contour (convexity check).
+int min_curvature(const Contour& c, const ArcTable& t, int64_t samples, double* kmin, cudaStream_t s);
+
+// ---------------------------------------------------------------- quadrature
+struct QuadTables {
+  int q_far = 6, q_near = 12, near_band = 4;
+  double xf[16], wf[16];         // far rule on [0,1]
+  double xn[16], wn[16];         // near rule on [0,1]
+  // product-integration weights for log d on the near grid (q_near^2 each):
+  // 0: self (d = |xi - eta|), 1: f = e + 1 (d = 1 - xi + eta), 2: f = e - 1 (d = xi + 1 - eta)
+  std::vector<double> wlog[3];
+};
+void gauss_legendre01(int n, double* x, double* w);
+void build_quad_tables(QuadTables& q);
+
+// ---------------------------------------------------------------- assembly
+struct AsmArgs {
+  int64_t N;
+  double h, k;
+  zd kt;
+  int q_far, q_near, near_band;
+  Points far, near;                // point tables (far: q_far per element, near: q_near)
+  const double* wlog;              // 3 * q_near^2 product weights (device)
+  zd *S, *D, *Dt, *Nk;             // outputs
+  int64_t ld;                      // row-major leading dimension
+};
+int assemble_dense(const AsmArgs& a, cudaStream_t s);
+// First row of the four circulant operators on the circle (row 0, N entries each).
+int assemble_circle_row(const AsmArgs& a, cudaStream_t s);
+// Sampled entries (row, col) of the four operators, computed point-wise.
+int assemble_entries(const AsmArgs& a, int64_t count, const int64_t* rows, const int64_t* cols,
+                     zd* out4, cudaStream_t s);
+
+// ---------------------------------------------------------------- FFT
+struct FFTPlan {
+  int64_t n = 0;
+  bool pow2 = true;
+  int64_t m = 0;                   // Bluestein length (power of two >= 2n-1)
+  zd* twiddle = nullptr;           // device twiddles for the power-of-two length
+  zd* chirp = nullptr;             // Bluestein chirp (n)
+  zd* chirp_hat = nullptr;         // FFT of the Bluestein filter (m)
+  zd* work = nullptr;              // Bluestein work (m * batch_cap)
+  int64_t work_cols = 0;
+};
+int fft_plan_create(FFTPlan& p, int64_t n, cudaStream_t s);
+void fft_plan_destroy(FFTPlan& p);
+// In-place batched transform of `cols` columns of length n (column-major, ld).
+// sign = -1: forward (e^{-2 pi i jk/n}); +1: inverse without 1/n scaling.
+int fft_columns(FFTPlan& p, zd* x, int64_t ld, int64_t cols, int sign, cudaStream_t s);
+// x[:, c] <- x[:, c] * mu (mu length n), or / mu when divide, conj(mu) when conj_mu.
+int scale_columns(zd* x, int64_t n, int64_t ld, int64_t cols, const zd* mu, bool divide,
+                  bool conj_mu, double extra, cudaStream_t s);
+
+// ---------------------------------------------------------------- dense linear algebra (FP64)
+// General strided complex matrix view: element (i, j) at p[i * rs + j * cs], optionally conjugated.
+struct ZView {
+  const zd* p;
+  int64_t rs, cs;
+  bool conj;
+};
+// C (m x n, column-major ldc) = alpha * A (m x k) * B (k x n) + beta * C.
+int zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A, ZView B, zd beta, zd* C, int64_t ldc,
+          cudaStream_t s);
+// Y = G^{-1} X for the cyclic Gram matrix of hats (h/6 [1 4 1]), column-major; may alias.
+int gram_inverse(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
+                 cudaStream_t s);
+// Y = alpha * G X + beta * Y (cyclic tridiagonal), column-major.
+int gram_apply(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
+               double alpha, double beta, cudaStream_t s);
+// Column 2-norms of an m x n column-major block into out (device, n doubles).
+int column_norms(const zd* X, int64_t ld, int64_t m, int64_t n, double* out, cudaStream_t s);
+// Complex Gaussian samples (unit variance per complex entry), Philox-4x32 counter based.
+int gaussian_fill(zd* X, int64_t ld, int64_t m, int64_t n, uint64_t seed, uint64_t offset,
+                  cudaStream_t s);
+// Y(:, c) = a X(:, c) + b Y(:, c)
+int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int64_t ldy,
+          cudaStream_t s);
+// Pivoted Cholesky of a Hermitian b x b Gram (device, column-major ld = b): returns
+// numerical rank r (pivots >= tol^2 * max) and writes R (upper, r x b in permuted order)
+// and the pivot permutation.  Runs in one thread block.
+int pivoted_cholesky(zd* Gm, int b, double rel_tol, int* perm, int* rank_dev, cudaStream_t s);
+// Y(:, 0:r) = X(:, perm[0:r]) R[0:r, 0:r]^{-1}
+int trsm_right_upper(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
+                     const int* rank_dev, int rank_host, zd* Y, int64_t ldy, cudaStream_t s);
+// LU with partial pivoting of an n x n column-major matrix (in place) and explicit inverse.
+int lu_inverse(zd* A, int64_t n, zd* Ainv, int* piv, int* info_dev, double* minpiv_dev,
+               cudaStream_t s);
+
+// ---------------------------------------------------------------- right-hand sides / far field
+int planewave_rhs(const Points& near, const double* wn, const double* xn, int q, int64_t N,
+                  double h, double k, const double* angles, int B, zd* e, zd* hv, int64_t ld,
+                  cudaStream_t s);
+int farfield_matrix(const Points& near, const double* wn, const double* xn, int q, int64_t N,
+                    double h, double k, const double* phi, int nphi, zd* E, int64_t lde,
+                    cudaStream_t s);
+
+}  // namespace wcs

@@ -1,0 +1,458 @@
+// Dense complex FP64 linear algebra for the solver: operator applies
+// (Eq. 6), randomized range finding for the skeleton (Eq. 7) and the
+// capacitance matrix of the Woodbury identity (Eq. 9).
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+
+namespace wcs {
+
+// =========================================================================== ZGEMM (FP64 FMA pipe)
+// C (m x n, column-major) = alpha * A * B + beta * C; A (m x k), B (k x n) are
+// strided views (element (i, j) at p[i*rs + j*cs], optionally conjugated).
+constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+
+__global__ void __launch_bounds__(256) k_zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
+                                               ZView B, zd beta, zd* __restrict__ C, int64_t ldc) {
+  __shared__ zd As[GB_K][GB_M + 1];
+  __shared__ zd Bs[GB_K][GB_N + 1];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int64_t m0 = (int64_t)blockIdx.y * GB_M, n0 = (int64_t)blockIdx.x * GB_N;
+  zd acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mkz(0.0);
+  const bool a_kfast = (A.cs == 1);  // walk k first when it is the contiguous index
+  const bool b_kfast = (B.rs == 1);
+  for (int64_t k0 = 0; k0 < k; k0 += GB_K) {
+    for (int u = threadIdx.x; u < GB_M * GB_K; u += 256) {
+      int ii, kk;
+      if (a_kfast) { kk = u % GB_K; ii = u / GB_K; } else { ii = u % GB_M; kk = u / GB_M; }
+      const int64_t gi = m0 + ii, gk = k0 + kk;
+      zd v = mkz(0.0);
+      if (gi < m && gk < k) {
+        v = A.p[gi * A.rs + gk * A.cs];
+        if (A.conj) v.y = -v.y;
+      }
+      As[kk][ii] = v;
+    }
+    for (int u = threadIdx.x; u < GB_N * GB_K; u += 256) {
+      int jj, kk;
+      if (b_kfast) { kk = u % GB_K; jj = u / GB_K; } else { jj = u % GB_N; kk = u / GB_N; }
+      const int64_t gj = n0 + jj, gk = k0 + kk;
+      zd v = mkz(0.0);
+      if (gj < n && gk < k) {
+        v = B.p[gk * B.rs + gj * B.cs];
+        if (B.conj) v.y = -v.y;
+      }
+      Bs[kk][jj] = v;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < GB_K; ++kk) {
+      zd a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) zfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  const bool beta0 = (beta.x == 0.0 && beta.y == 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
+      if (gi < m && gj < n) {
+        zd r = alpha * acc[i][j];
+        if (!beta0) r += beta * C[gj * ldc + gi];
+        C[gj * ldc + gi] = r;
+      }
+    }
+}
+
+int zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A, ZView B, zd beta, zd* C, int64_t ldc,
+          cudaStream_t s) {
+  if (m <= 0 || n <= 0) return 0;
+  dim3 grid((unsigned)((n + GB_N - 1) / GB_N), (unsigned)((m + GB_M - 1) / GB_M));
+  if (grid.y > 65535) { set_error("zgemm: m too large"); return 1; }
+  k_zgemm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, B, beta, C, ldc);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("zgemm: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+// =========================================================================== Gram matrix
+// G = (h/6) circ(1, 4, 1).  With rho = sqrt(3) - 2 (root of rho^2 + 4 rho + 1):
+// circ(1,4,1) = (-1/rho) (1 - rho S)(1 - rho S^-1), S the cyclic down-shift,
+// so G^{-1} x = (6/h)(-rho) z with u_i = x_i + rho u_{i-1} (forward) and
+// z_i = u_i + rho z_{i+1} (backward).  Each thread filters a chunk of CH
+// outputs starting WARM samples early; |rho|^WARM < 1e-23 makes the cyclic
+// wrap-around exact to rounding.
+constexpr int GI_CH = 64, GI_WARM = 40;
+
+__global__ void k_gram_fwd(const zd* __restrict__ X, int64_t ldx, zd* __restrict__ U, int64_t n,
+                           int64_t cols, double rho) {
+  const int64_t chunks = (n + GI_CH - 1) / GI_CH;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= chunks * cols) return;
+  const int64_t c = t / chunks, i0 = (t - c * chunks) * GI_CH;
+  const int64_t i1 = min(n, i0 + GI_CH);
+  const zd* x = X + c * ldx;
+  zd* u = U + c * n;
+  zd acc = mkz(0.0);
+  const int64_t warm = GI_WARM;  // the input is periodic: wrapping more than once is fine
+  for (int64_t i = i0 - warm; i < i1; ++i) {
+    const int64_t ii = (i % n + n) % n;
+    acc = x[ii] + rho * acc;
+    if (i >= i0) u[ii] = acc;
+  }
+}
+
+__global__ void k_gram_bwd(const zd* __restrict__ U, zd* __restrict__ Y, int64_t ldy, int64_t n,
+                           int64_t cols, double rho, double scale) {
+  const int64_t chunks = (n + GI_CH - 1) / GI_CH;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= chunks * cols) return;
+  const int64_t c = t / chunks, i0 = (t - c * chunks) * GI_CH;
+  const int64_t i1 = min(n, i0 + GI_CH);
+  const zd* u = U + c * n;
+  zd* y = Y + c * ldy;
+  zd acc = mkz(0.0);
+  const int64_t warm = GI_WARM;
+  for (int64_t i = i1 - 1 + warm; i >= i0; --i) {
+    const int64_t ii = (i % n + n) % n;
+    acc = u[ii] + rho * acc;
+    if (i < i1) y[ii] = scale * acc;
+  }
+}
+
+static zd* g_gram_work = nullptr;
+static size_t g_gram_work_bytes = 0;
+
+int gram_inverse(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
+                 cudaStream_t s) {
+  if (cols <= 0) return 0;
+  const size_t need = sizeof(zd) * n * cols;
+  if (need > g_gram_work_bytes) {
+    cudaFree(g_gram_work);
+    g_gram_work = nullptr;
+    g_gram_work_bytes = 0;
+    if (cudaMalloc(&g_gram_work, need) != cudaSuccess) { set_error("oom (gram)"); return 4; }
+    g_gram_work_bytes = need;
+  }
+  const double rho = sqrt(3.0) - 2.0;
+  const int64_t tasks = ((n + GI_CH - 1) / GI_CH) * cols;
+  const unsigned blocks = (unsigned)((tasks + 127) / 128);
+  k_gram_fwd<<<blocks, 128, 0, s>>>(X, ldx, g_gram_work, n, cols, rho);
+  k_gram_bwd<<<blocks, 128, 0, s>>>(g_gram_work, Y, ldy, n, cols, rho, -rho * 6.0 / h);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("gram: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+__global__ void k_gram_apply(const zd* __restrict__ X, int64_t ldx, zd* __restrict__ Y, int64_t ldy,
+                             int64_t n, double a6, double a4, double beta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (i >= n) return;
+  const zd* x = X + c * ldx;
+  const zd xm = x[(i - 1 + n) % n], x0 = x[i], xp = x[(i + 1) % n];
+  zd r = a6 * (xm + xp) + a4 * x0;
+  zd* y = Y + c * ldy;
+  if (beta != 0.0) r += beta * y[i];
+  y[i] = r;
+}
+
+int gram_apply(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
+               double alpha, double beta, cudaStream_t s) {
+  for (int64_t c0 = 0; c0 < cols; c0 += 65535) {
+    int64_t cc = std::min<int64_t>(65535, cols - c0);
+    dim3 g((unsigned)((n + 255) / 256), (unsigned)cc);
+    k_gram_apply<<<g, 256, 0, s>>>(X + c0 * ldx, ldx, Y + c0 * ldy, ldy, n, alpha * h / 6.0,
+                                   alpha * 4.0 * h / 6.0, beta);
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("gram_apply: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+// =========================================================================== small kernels
+__global__ void k_colnorm(const zd* X, int64_t ld, int64_t m, double* out) {
+  __shared__ double red[256];
+  const int64_t c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += abs2(X[c * ld + i]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = sqrt(red[0]);
+}
+
+int column_norms(const zd* X, int64_t ld, int64_t m, int64_t n, double* out, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_colnorm<<<(unsigned)n, 256, 0, s>>>(X, ld, m, out);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+__device__ __forceinline__ uint4 philox4x32(uint4 c, uint2 k) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += W0;
+    k.y += W1;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double u01(uint32_t a, uint32_t b) {
+  // 53-bit uniform in (0, 1]
+  const uint64_t v = ((uint64_t)a << 21) ^ (uint64_t)b;
+  return ((double)(v & ((1ull << 53) - 1)) + 1.0) * (1.0 / 9007199254740992.0);
+}
+
+__global__ void k_gauss(zd* X, int64_t ld, int64_t m, int64_t n, uint64_t seed, uint64_t offset) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= m * n) return;
+  const int64_t c = t / m, i = t - c * m;
+  const uint64_t ctr = offset + (uint64_t)t;
+  uint4 r = philox4x32(make_uint4((uint32_t)ctr, (uint32_t)(ctr >> 32), 0x57435331u, 0u),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const double u1 = u01(r.x, r.y), u2 = u01(r.z, r.w);
+  const double rad = sqrt(-log(u1));  // E|z|^2 = 1
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  X[c * ld + i] = mkz(rad * cs, rad * sn);
+}
+
+int gaussian_fill(zd* X, int64_t ld, int64_t m, int64_t n, uint64_t seed, uint64_t offset,
+                  cudaStream_t s) {
+  const int64_t tot = m * n;
+  if (tot <= 0) return 0;
+  k_gauss<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ld, m, n, seed, offset);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+__global__ void k_axpby(int64_t m, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int64_t ldy) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (i >= m) return;
+  zd y = mkz(0.0);
+  if (b.x != 0.0 || b.y != 0.0) y = b * Y[c * ldy + i];
+  Y[c * ldy + i] = y + a * X[c * ldx + i];
+}
+
+int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int64_t ldy,
+          cudaStream_t s) {
+  for (int64_t c0 = 0; c0 < n; c0 += 65535) {
+    int64_t cc = std::min<int64_t>(65535, n - c0);
+    dim3 g((unsigned)((m + 255) / 256), (unsigned)cc);
+    k_axpby<<<g, 256, 0, s>>>(m, a, X + c0 * ldx, ldx, b, Y + c0 * ldy, ldy);
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+// =========================================================================== pivoted Cholesky
+// In-place on a Hermitian b x b matrix (column-major, ld = b), one CTA.
+// After return: rank r, perm[0:b], and R (upper, row j holds R[j, j..b-1]
+// in permuted order) stored in Gm's upper triangle.
+__global__ void k_pchol(zd* Gm, int b, double rel_tol, int* perm, int* rank_out) {
+  __shared__ double dmax_s;
+  __shared__ int piv_s;
+  __shared__ int stop_s;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < b; i += blockDim.x) perm[i] = i;
+  if (tid == 0) { dmax_s = 0.0; stop_s = 0; }
+  __syncthreads();
+  int rank = b;
+  for (int j = 0; j < b; ++j) {
+    if (tid == 0) {
+      int p = j;
+      double best = -1.0;
+      for (int i = j; i < b; ++i) {
+        double d = Gm[i * b + i].x;
+        if (d > best) { best = d; p = i; }
+      }
+      if (j == 0) dmax_s = best;
+      piv_s = p;
+      stop_s = (best <= rel_tol * rel_tol * dmax_s || best <= 0.0) ? 1 : 0;
+    }
+    __syncthreads();
+    if (stop_s) { rank = j; break; }
+    const int p = piv_s;
+    if (p != j) {
+      // symmetric swap of rows/columns j and p
+      for (int i = tid; i < b; i += blockDim.x) {
+        zd t = Gm[j * b + i]; Gm[j * b + i] = Gm[p * b + i]; Gm[p * b + i] = t;  // columns
+      }
+      __syncthreads();
+      for (int i = tid; i < b; i += blockDim.x) {
+        zd t = Gm[i * b + j]; Gm[i * b + j] = Gm[i * b + p]; Gm[i * b + p] = t;  // rows
+      }
+      if (tid == 0) { int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+      __syncthreads();
+    }
+    const double rjj = sqrt(Gm[j * b + j].x);
+    __syncthreads();
+    // row j of R: R[j, i] = G[j, i] / rjj  (G[j, i] at column i, row j)
+    for (int i = tid; i < b; i += blockDim.x) {
+      if (i > j) Gm[i * b + j] = (1.0 / rjj) * Gm[i * b + j];
+      if (i == j) Gm[j * b + j] = mkz(rjj);
+    }
+    __syncthreads();
+    // Schur complement: G[l, i] -= conj(R[j, l]) R[j, i], l, i > j
+    const int rem = b - j - 1;
+    for (int u = tid; u < rem * rem; u += blockDim.x) {
+      const int l = j + 1 + u % rem, i = j + 1 + u / rem;
+      Gm[i * b + l] -= conj(Gm[l * b + j]) * Gm[i * b + j];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *rank_out = rank;
+}
+
+int pivoted_cholesky(zd* Gm, int b, double rel_tol, int* perm, int* rank_dev, cudaStream_t s) {
+  k_pchol<<<1, 512, 0, s>>>(Gm, b, rel_tol, perm, rank_dev);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+// Y(i, 0:r) = X(i, perm[0:r]) R^{-1}: solve y R = x row by row (R upper, r x r)
+__global__ void k_trsm_rows(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
+                            const int* rank_dev, zd* Y, int64_t ldy) {
+  extern __shared__ zd Rs[];
+  const int r = *rank_dev;
+  for (int u = threadIdx.x; u < r * r; u += blockDim.x) {
+    const int row = u % r, col = u / r;
+    Rs[col * r + row] = (row <= col) ? R[col * b + row] : mkz(0.0);
+  }
+  __shared__ int ps[128];
+  for (int u = threadIdx.x; u < r; u += blockDim.x) ps[u] = perm[u];
+  __syncthreads();
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  for (int j = 0; j < r; ++j) {
+    zd v = X[(int64_t)ps[j] * ldx + i];
+    for (int l = 0; l < j; ++l) v -= Y[(int64_t)l * ldy + i] * Rs[j * r + l];
+    Y[(int64_t)j * ldy + i] = zdiv(v, Rs[j * r + j]);
+  }
+}
+
+int trsm_right_upper(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
+                     const int* rank_dev, int rank_host, zd* Y, int64_t ldy, cudaStream_t s) {
+  if (b > 128) { set_error("trsm: block too wide"); return 1; }
+  const size_t smem = sizeof(zd) * rank_host * rank_host;
+  cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
+  k_trsm_rows<<<(unsigned)((m + 127) / 128), 128, smem, s>>>(X, ldx, m, R, b, perm, rank_dev, Y, ldy);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("trsm: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+// =========================================================================== Gauss-Jordan inverse
+// M = [A | I] (n x 2n, column-major, ld = n).  Step j: pick the pivot row in
+// column j, swap, scale the pivot row, eliminate column j from every other row.
+__global__ void k_gj_pivot(zd* M, int64_t n, int64_t j, zd* colj, zd* rowj, int* info,
+                           double* minpiv) {
+  __shared__ double best[512];
+  __shared__ int bidx[512];
+  const int tid = threadIdx.x;
+  double b = -1.0;
+  int bi = (int)j;
+  for (int64_t i = j + tid; i < n; i += blockDim.x) {
+    double v = abs2(M[j * n + i]);
+    if (v > b) { b = v; bi = (int)i; }
+  }
+  best[tid] = b;
+  bidx[tid] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (tid < o && best[tid + o] > best[tid]) { best[tid] = best[tid + o]; bidx[tid] = bidx[tid + o]; }
+    __syncthreads();
+  }
+  const int64_t p = bidx[0];
+  const double pv = sqrt(best[0]);
+  if (tid == 0) {
+    if (pv < *minpiv) *minpiv = pv;
+    if (!(pv > 0.0)) *info = (int)j + 1;
+  }
+  // swap rows j and p over all 2n columns
+  if (p != j)
+    for (int64_t c = tid; c < 2 * n; c += blockDim.x) {
+      zd t = M[c * n + j]; M[c * n + j] = M[c * n + p]; M[c * n + p] = t;
+    }
+  __syncthreads();
+  const zd inv = (pv > 0.0) ? zrecip(M[j * n + j]) : mkz(0.0);
+  for (int64_t i = tid; i < n; i += blockDim.x) colj[i] = M[j * n + i];
+  for (int64_t c = tid; c < 2 * n; c += blockDim.x) rowj[c] = M[c * n + j] * inv;
+}
+
+__global__ void k_gj_update(zd* M, int64_t n, int64_t j, int64_t cbase, const zd* colj,
+                            const zd* rowj) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t c = cbase + blockIdx.y;
+  if (i >= n || c >= 2 * n) return;
+  if (i == j) M[c * n + i] = rowj[c];
+  else M[c * n + i] -= colj[i] * rowj[c];
+}
+
+__global__ void k_identity(zd* M, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) M[i * n + i] = mkz(1.0);
+}
+
+int lu_inverse(zd* A, int64_t n, zd* Ainv, int* piv, int* info_dev, double* minpiv_dev,
+               cudaStream_t s) {
+  (void)piv;
+  zd *M = nullptr, *colj = nullptr, *rowj = nullptr;
+  if (cudaMalloc(&M, sizeof(zd) * n * 2 * n) != cudaSuccess ||
+      cudaMalloc(&colj, sizeof(zd) * n) != cudaSuccess ||
+      cudaMalloc(&rowj, sizeof(zd) * 2 * n) != cudaSuccess) {
+    cudaFree(M); cudaFree(colj); cudaFree(rowj);
+    set_error("oom (capacitance inverse)");
+    return 4;
+  }
+  cudaMemcpy2DAsync(M, sizeof(zd) * n, A, sizeof(zd) * n, sizeof(zd) * n, n, cudaMemcpyDeviceToDevice, s);
+  cudaMemsetAsync(M + n * n, 0, sizeof(zd) * n * n, s);
+  k_identity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M + n * n, n);
+  const double big = 1e300;
+  cudaMemcpyAsync(minpiv_dev, &big, sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(info_dev, 0, sizeof(int), s);
+  for (int64_t j = 0; j < n; ++j) {
+    k_gj_pivot<<<1, 512, 0, s>>>(M, n, j, colj, rowj, info_dev, minpiv_dev);
+    const int64_t ncols = 2 * n - j;
+    for (int64_t c0 = 0; c0 < ncols; c0 += 65535) {
+      dim3 g((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(65535, ncols - c0));
+      k_gj_update<<<g, 256, 0, s>>>(M, n, j, j + c0, colj, rowj);
+    }
+  }
+  cudaMemcpy2DAsync(Ainv, sizeof(zd) * n, M + n * n, sizeof(zd) * n, sizeof(zd) * n, n,
+                    cudaMemcpyDeviceToDevice, s);
+  cudaError_t err = cudaStreamSynchronize(s);
+  cudaFree(M); cudaFree(colj); cudaFree(rowj);
+  if (err != cudaSuccess) { set_error(std::string("inverse: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+}  // namespace wcs

@@ -1,0 +1,835 @@
+// C ABI and host orchestration of the Woodbury-circulant solver.
+//
+// Sec. III, Eq. (5)/(6): C = (G/2 + D~) G^{-1} (G/2 - D) + S~ G^{-1} N is
+// never formed; it is applied matrix-free from the four assembled operators.
+// Sec. V: C_c (the same operator on the circle of equal perimeter) is
+// circulant; its eigenvalues mu_C come from the FFT of the first rows of the
+// circle operators.  Eq. (7): C - C_c = U V^T by randomized range finding;
+// Eq. (8)/(9): Woodbury with the capacitance K = I + V^T C_c^{-1} U.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/wcs.h"
+#include "internal.h"
+
+namespace wcs {
+static thread_local std::string g_err;
+void set_error(const std::string& m) { g_err = m; }
+}  // namespace wcs
+
+using namespace wcs;
+
+enum Stage { ST_NEW = 0, ST_CONTOUR = 1, ST_MESH = 2, ST_ASSEMBLED = 3, ST_SKELETON = 4, ST_FACTORED = 5 };
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t b) {
+    if (b <= bytes) return 0;
+    cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (cudaMalloc(&p, b) != cudaSuccess) { set_error("out of device memory"); return WCS_ERR_OOM; }
+    bytes = b;
+    return 0;
+  }
+  void release() { cudaFree(p); p = nullptr; bytes = 0; }
+  zd* z() { return (zd*)p; }
+  double* d() { return (double*)p; }
+};
+
+struct wcs_ctx {
+  wcs_options opt;
+  cudaStream_t s = nullptr;
+  int stage = ST_NEW;
+  Contour contour{}, circle{};
+  ArcTable arc{}, arc_c{};
+  int64_t N = 0, ld = 0;
+  double L = 0, h = 0, a = 0, k = 0, kmin = 0;
+  zd kt = mkz(0.0);
+  QuadTables quad;
+  DevBuf xf, xn, wn, wlog;                // device rule nodes / weights
+  DevBuf pts_far, pts_near, pts_far_c, pts_near_c;
+  Points far, near, far_c, near_c;
+  DevBuf ops;                             // S, D, Dt, N (row-major, ld)
+  zd *S = nullptr, *D = nullptr, *Dt = nullptr, *Nk = nullptr;
+  DevBuf mu;                              // 6 x N: G, S, D, Dt, N, C
+  double norm_cc = 0;
+  FFTPlan fft{};
+  bool fft_ready = false;
+  int rank = -1;
+  DevBuf U, Vw, Wt;                       // N x rank each
+  DevBuf w1, w2, w3, w4, w5;              // N x chunk scratch
+  DevBuf small;                           // small scratch
+};
+
+static zd* mu_ptr(wcs_ctx* c, int which) { return c->mu.z() + (int64_t)which * c->N; }
+enum { MU_G = 0, MU_S = 1, MU_D = 2, MU_DT = 3, MU_N = 4, MU_C = 5 };
+
+// ----------------------------------------------------------------------------- helpers
+static ZView op_view(const zd* A, int64_t ld, bool adjoint) {
+  if (!adjoint) return ZView{A, ld, 1, false};
+  return ZView{A, 1, ld, true};
+}
+static ZView blk(const zd* X, int64_t ld) { return ZView{X, 1, ld, false}; }
+static ZView blkH(const zd* X, int64_t ld) { return ZView{X, ld, 1, true}; }
+
+#define TRY(x)              \
+  do {                      \
+    int _r = (x);           \
+    if (_r) return _r;      \
+  } while (0)
+
+static int ensure_work(wcs_ctx* c, int64_t cols) {
+  size_t b = sizeof(zd) * c->N * std::max<int64_t>(cols, 1);
+  TRY(c->w1.ensure(b));
+  TRY(c->w2.ensure(b));
+  TRY(c->w3.ensure(b));
+  TRY(c->w4.ensure(b));
+  TRY(c->w5.ensure(b));
+  return 0;
+}
+
+// Y = C X (adjoint: C^H X); uses w1, w2 as temporaries.  Y must not alias X.
+static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj) {
+  const int64_t N = c->N;
+  zd* T1 = c->w1.z();
+  zd* T2 = c->w2.z();
+  const zd one = mkz(1.0), zero = mkz(0.0), mone = mkz(-1.0);
+  if (!adj) {
+    // T1 = (G/2 - D) X, T2 = N X
+    TRY(zgemm(N, cols, N, mone, op_view(c->D, c->ld, false), blk(X, ldx), zero, T1, N, c->s));
+    TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
+    TRY(zgemm(N, cols, N, one, op_view(c->Nk, c->ld, false), blk(X, ldx), zero, T2, N, c->s));
+    TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
+    TRY(gram_inverse(T2, N, T2, N, N, cols, c->h, c->s));
+    // Y = (G/2 + D~) T1 + S~ T2
+    TRY(zgemm(N, cols, N, one, op_view(c->Dt, c->ld, false), blk(T1, N), zero, Y, ldy, c->s));
+    TRY(zgemm(N, cols, N, one, op_view(c->S, c->ld, false), blk(T2, N), one, Y, ldy, c->s));
+    TRY(gram_apply(T1, N, Y, ldy, N, cols, c->h, 0.5, 1.0, c->s));
+  } else {
+    // C^H = (G/2 - D)^H G^{-1} (G/2 + D~)^H + N^H G^{-1} S~^H   (G real symmetric)
+    TRY(zgemm(N, cols, N, one, op_view(c->Dt, c->ld, true), blk(X, ldx), zero, T1, N, c->s));
+    TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
+    TRY(zgemm(N, cols, N, one, op_view(c->S, c->ld, true), blk(X, ldx), zero, T2, N, c->s));
+    TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
+    TRY(gram_inverse(T2, N, T2, N, N, cols, c->h, c->s));
+    TRY(zgemm(N, cols, N, mone, op_view(c->D, c->ld, true), blk(T1, N), zero, Y, ldy, c->s));
+    TRY(zgemm(N, cols, N, one, op_view(c->Nk, c->ld, true), blk(T2, N), one, Y, ldy, c->s));
+    TRY(gram_apply(T1, N, Y, ldy, N, cols, c->h, 0.5, 1.0, c->s));
+  }
+  return 0;
+}
+
+// Y = C_c X, C_c^H X or C_c^{-1} X by FFT (mode 0, 1, 2).  Y may alias X.
+static int apply_Cc(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, int mode) {
+  const int64_t N = c->N;
+  if (X != Y) {
+    cudaError_t e = cudaMemcpy2DAsync(Y, sizeof(zd) * ldy, X, sizeof(zd) * ldx, sizeof(zd) * N, cols,
+                                      cudaMemcpyDeviceToDevice, c->s);
+    if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  }
+  TRY(fft_columns(c->fft, Y, ldy, cols, -1, c->s));
+  TRY(scale_columns(Y, N, ldy, cols, mu_ptr(c, MU_C), mode == 2, mode == 1, 1.0 / (double)N, c->s));
+  TRY(fft_columns(c->fft, Y, ldy, cols, +1, c->s));
+  return 0;
+}
+
+// Y = (C - C_c) X or its adjoint; uses w1, w2, w3.
+static int apply_remainder(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols,
+                           bool adj) {
+  TRY(apply_C(c, X, ldx, Y, ldy, cols, adj));
+  zd* T3 = c->w3.z();
+  TRY(apply_Cc(c, X, ldx, T3, c->N, cols, adj ? 1 : 0));
+  TRY(axpby(c->N, cols, mkz(-1.0), T3, c->N, mkz(1.0), Y, ldy, c->s));
+  return 0;
+}
+
+// X = C^{-1} B through Eq. (9); uses w3 for Y = C_c^{-1} B and small for Z.
+static int woodbury(wcs_ctx* c, const zd* B, int64_t ldb, zd* X, int64_t ldx, int64_t cols) {
+  const int64_t N = c->N;
+  TRY(apply_Cc(c, B, ldb, X, ldx, cols, 2));
+  if (c->rank <= 0) return 0;
+  const int64_t r = c->rank;
+  TRY(c->small.ensure(sizeof(zd) * r * cols));
+  zd* Z = c->small.z();
+  // Z = V^T Y = Vw^H Y ; X = Y - Wt Z
+  TRY(zgemm(r, cols, N, mkz(1.0), blkH(c->Vw.z(), N), blk(X, ldx), mkz(0.0), Z, r, c->s));
+  TRY(zgemm(N, cols, r, mkz(-1.0), blk(c->Wt.z(), N), blk(Z, r), mkz(1.0), X, ldx, c->s));
+  return 0;
+}
+
+static int sync(wcs_ctx* c) {
+  cudaError_t e = cudaStreamSynchronize(c->s);
+  if (e != cudaSuccess) { set_error(std::string("device: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  return 0;
+}
+
+// ----------------------------------------------------------------------------- kernels local to the driver
+__global__ void k_mu_finish(zd* mu, int64_t N, double h) {
+  const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  double s, co;
+  sincospi(2.0 * (double)m / (double)N, &s, &co);
+  const zd G = mkz(h * (2.0 + co) / 3.0);
+  mu[m] = G;
+  const zd S = mu[N + m], D = mu[2 * N + m], Dt = mu[3 * N + m], Nk = mu[4 * N + m];
+  const zd half = 0.5 * G;
+  mu[5 * N + m] = zdiv((half + Dt) * (half - D) + S * Nk, G);
+}
+
+__global__ void k_absmax(const zd* x, int64_t n, double* out) {
+  __shared__ double red[256];
+  double m = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) m = fmax(m, zabs(x[i]));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+__global__ void k_add_identity(zd* K, int64_t r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < r) K[i * r + i] += mkz(1.0);
+}
+
+// per-column squared norms of an N x cols block
+__global__ void k_colnorm2(const zd* X, int64_t ld, int64_t m, double* out) {
+  __shared__ double red[256];
+  const int64_t c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += abs2(X[c * ld + i]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = red[0];
+}
+
+// ----------------------------------------------------------------------------- C ABI
+extern "C" {
+
+const char* wcs_version(void) { return "wcs-gb300 0.1 (sm_103a, FP64 path)"; }
+
+const char* wcs_last_error(void) { return g_err.c_str(); }
+
+int wcs_default_options(wcs_options* o) {
+  if (!o) { set_error("null options"); return WCS_ERR_ARG; }
+  std::memset(o, 0, sizeof(*o));
+  o->precision = WCS_PREC_FP64;
+  o->q_far = 6;
+  o->q_near = 12;
+  o->near_band = 4;
+  o->block = 32;
+  o->max_refine = 12;
+  o->refine_tol = 1e-12;
+  o->rhs_chunk = 256;
+  return WCS_OK;
+}
+
+int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream) {
+  if (!out) { set_error("null output pointer"); return WCS_ERR_ARG; }
+  wcs_options o;
+  if (opt) o = *opt; else wcs_default_options(&o);
+  if (o.precision != WCS_PREC_FP64) { set_error("only the FP64 precision mode is built"); return WCS_ERR_UNSUPPORTED; }
+  if (o.q_far < 2 || o.q_far > 16 || o.q_near < 4 || o.q_near > 16 || o.near_band < 1 ||
+      o.block < 1 || o.block > 64 || o.rhs_chunk < 1 || o.max_refine < 0) {
+    set_error("option out of range");
+    return WCS_ERR_ARG;
+  }
+  wcs_ctx* c = new wcs_ctx();
+  c->opt = o;
+  c->s = (cudaStream_t)stream;
+  c->quad.q_far = o.q_far;
+  c->quad.q_near = o.q_near;
+  c->quad.near_band = o.near_band;
+  build_quad_tables(c->quad);
+  *out = c;
+  return WCS_OK;
+}
+
+static void free_mesh(wcs_ctx* c) {
+  cudaFree(c->arc.cum); c->arc.cum = nullptr;
+  cudaFree(c->arc_c.cum); c->arc_c.cum = nullptr;
+  c->pts_far.release(); c->pts_near.release(); c->pts_far_c.release(); c->pts_near_c.release();
+  c->ops.release(); c->mu.release();
+  c->U.release(); c->Vw.release(); c->Wt.release();
+  if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
+  c->rank = -1;
+}
+
+int wcs_destroy(wcs_ctx* c) {
+  if (!c) return WCS_OK;
+  free_mesh(c);
+  c->xf.release(); c->xn.release(); c->wn.release(); c->wlog.release();
+  c->w1.release(); c->w2.release(); c->w3.release(); c->w4.release(); c->w5.release();
+  c->small.release();
+  delete c;
+  return WCS_OK;
+}
+
+static int set_contour(wcs_ctx* c, const Contour& k) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  free_mesh(c);
+  c->contour = k;
+  c->stage = ST_CONTOUR;
+  return WCS_OK;
+}
+
+int wcs_contour_circle(wcs_ctx* c, double a) {
+  if (!(a > 0)) { set_error("radius must be positive"); return WCS_ERR_ARG; }
+  Contour k{};
+  k.family = FAM_CIRCLE;
+  k.a = a;
+  return set_contour(c, k);
+}
+
+int wcs_contour_ellipse(wcs_ctx* c, double ax, double ay) {
+  if (!(ax > 0 && ay > 0)) { set_error("semi-axes must be positive"); return WCS_ERR_ARG; }
+  Contour k{};
+  k.family = FAM_ELLIPSE;
+  k.ax = ax;
+  k.ay = ay;
+  return set_contour(c, k);
+}
+
+int wcs_contour_superellipse(wcs_ctx* c, double ax, double ay, double p) {
+  if (!(ax > 0 && ay > 0 && p >= 2.0)) { set_error("superellipse needs ax, ay > 0 and p >= 2"); return WCS_ERR_ARG; }
+  Contour k{};
+  k.family = FAM_SUPERELLIPSE;
+  k.ax = ax;
+  k.ay = ay;
+  k.p = p;
+  return set_contour(c, k);
+}
+
+int wcs_contour_fourier(wcs_ctx* c, int count, const double* cc, const double* ss) {
+  if (count < 1 || count > kMaxFourier || !cc) { set_error("fourier: 1 <= count <= 64 and cos_c required"); return WCS_ERR_ARG; }
+  if (!(cc[0] > 0)) { set_error("fourier: mean radius must be positive"); return WCS_ERR_ARG; }
+  Contour k{};
+  k.family = FAM_FOURIER;
+  k.nf = count;
+  for (int m = 0; m < count; ++m) { k.fc[m] = cc[m]; k.fs[m] = ss ? ss[m] : 0.0; }
+  return set_contour(c, k);
+}
+
+static int build_points(wcs_ctx* c, const Contour& k, const ArcTable& t, DevBuf& buf, Points& P,
+                        const double* xi_dev, int q, bool with_kappa) {
+  const int64_t n = c->N * q;
+  TRY(buf.ensure(sizeof(double) * n * 5));
+  double* b = buf.d();
+  P.x = b; P.y = b + n; P.nx = b + 2 * n; P.ny = b + 3 * n; P.kappa = with_kappa ? b + 4 * n : nullptr;
+  P.n = n;
+  return points_build(k, t, c->N, c->h, xi_dev, q, P, c->s);
+}
+
+int wcs_mesh(wcs_ctx* c, int64_t N, double k) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_CONTOUR) { set_error("set a contour first"); return WCS_ERR_STATE; }
+  if (N < 12 || N > (int64_t)1 << 22) { set_error("N must be in [12, 4194304]"); return WCS_ERR_ARG; }
+  free_mesh(c);
+  c->stage = ST_CONTOUR;
+  TRY(arc_table_build(c->contour, c->arc, c->s));
+  c->L = c->arc.L;
+  c->N = N;
+  c->ld = (N + 7) & ~(int64_t)7;
+  c->h = c->L / (double)N;
+  c->a = c->L / (2.0 * WCS_PI);
+  c->k = (k > 0) ? k : 2.0 * WCS_PI * ((double)N / 10.0) / c->L;
+  if (c->k * c->h > 2.5) { set_error("k h > 2.5: mesh too coarse for the wavenumber"); return WCS_ERR_ARG; }
+  c->kt = mkz(c->k, 0.4 * cbrt(c->k) * pow(c->a, -2.0 / 3.0));
+  TRY(min_curvature(c->contour, c->arc, std::max<int64_t>(16 * N, 65536), &c->kmin, c->s));
+  if (c->kmin < -1e-9) { set_error("contour is not convex (negative curvature)"); return WCS_ERR_NOT_CONVEX; }
+  // equivalent circle
+  c->circle = Contour{};
+  c->circle.family = FAM_CIRCLE;
+  c->circle.a = c->a;
+  TRY(arc_table_build(c->circle, c->arc_c, c->s));
+  // rules on device
+  const int qf = c->opt.q_far, qn = c->opt.q_near;
+  TRY(c->xf.ensure(sizeof(double) * 16));
+  TRY(c->xn.ensure(sizeof(double) * 16));
+  TRY(c->wn.ensure(sizeof(double) * 16));
+  TRY(c->wlog.ensure(sizeof(double) * 3 * qn * qn));
+  cudaMemcpyAsync(c->xf.p, c->quad.xf, sizeof(double) * qf, cudaMemcpyHostToDevice, c->s);
+  cudaMemcpyAsync(c->xn.p, c->quad.xn, sizeof(double) * qn, cudaMemcpyHostToDevice, c->s);
+  cudaMemcpyAsync(c->wn.p, c->quad.wn, sizeof(double) * qn, cudaMemcpyHostToDevice, c->s);
+  for (int t = 0; t < 3; ++t)
+    cudaMemcpyAsync(c->wlog.d() + t * qn * qn, c->quad.wlog[t].data(), sizeof(double) * qn * qn,
+                    cudaMemcpyHostToDevice, c->s);
+  TRY(build_points(c, c->contour, c->arc, c->pts_far, c->far, c->xf.d(), qf, false));
+  TRY(build_points(c, c->contour, c->arc, c->pts_near, c->near, c->xn.d(), qn, true));
+  TRY(build_points(c, c->circle, c->arc_c, c->pts_far_c, c->far_c, c->xf.d(), qf, false));
+  TRY(build_points(c, c->circle, c->arc_c, c->pts_near_c, c->near_c, c->xn.d(), qn, true));
+  TRY(fft_plan_create(c->fft, N, c->s));
+  c->fft_ready = true;
+  TRY(sync(c));
+  c->stage = ST_MESH;
+  return WCS_OK;
+}
+
+int wcs_query(const wcs_ctx* c, wcs_info* info) {
+  if (!c || !info) { set_error("null argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_MESH) { set_error("no mesh yet"); return WCS_ERR_STATE; }
+  info->N = c->N; info->L = c->L; info->h = c->h; info->a = c->a; info->k = c->k;
+  info->kt_re = c->kt.x; info->kt_im = c->kt.y;
+  info->rank = c->stage >= ST_SKELETON ? c->rank : -1;
+  info->norm_cc = c->stage >= ST_ASSEMBLED ? c->norm_cc : 0.0;
+  info->min_curvature = c->kmin;
+  return WCS_OK;
+}
+
+static AsmArgs asm_args(wcs_ctx* c, bool circle) {
+  AsmArgs A{};
+  A.N = c->N; A.h = c->h; A.k = c->k; A.kt = c->kt;
+  A.q_far = c->opt.q_far; A.q_near = c->opt.q_near; A.near_band = c->opt.near_band;
+  A.far = circle ? c->far_c : c->far;
+  A.near = circle ? c->near_c : c->near;
+  A.wlog = c->wlog.d();
+  A.ld = c->ld;
+  return A;
+}
+
+__global__ void k_geom_sample_dummy() {}
+
+int wcs_geometry_sample(wcs_ctx* c, int64_t count, const double* s_host, double* out_host) {
+  if (!c || !s_host || !out_host || count < 0) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_MESH) { set_error("no mesh yet"); return WCS_ERR_STATE; }
+  if (count == 0) return WCS_OK;
+  // treat each sample as element e = 0 with xi = s / h (points_build evaluates (e + xi) h)
+  DevBuf sb, pb;
+  TRY(sb.ensure(sizeof(double) * count));
+  TRY(pb.ensure(sizeof(double) * count * 5));
+  std::vector<double> xi(count);
+  for (int64_t i = 0; i < count; ++i) xi[i] = s_host[i] / c->h;
+  cudaMemcpyAsync(sb.p, xi.data(), sizeof(double) * count, cudaMemcpyHostToDevice, c->s);
+  Points P;
+  double* b = pb.d();
+  P.x = b; P.y = b + count; P.nx = b + 2 * count; P.ny = b + 3 * count; P.kappa = b + 4 * count;
+  P.n = count;
+  // one "element" with count local nodes
+  const int64_t savedN = c->N;
+  int r = points_build(c->contour, c->arc, 1, c->h, sb.d(), (int)count, P, c->s);
+  (void)savedN;
+  if (r) { sb.release(); pb.release(); return r; }
+  cudaMemcpyAsync(out_host, pb.p, sizeof(double) * count * 5, cudaMemcpyDeviceToHost, c->s);
+  r = sync(c);
+  sb.release();
+  pb.release();
+  return r;
+}
+
+int wcs_assemble(wcs_ctx* c) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_MESH) { set_error("mesh first"); return WCS_ERR_STATE; }
+  const int64_t N = c->N, ld = c->ld;
+  TRY(c->ops.ensure(sizeof(zd) * 4 * N * ld));
+  c->S = c->ops.z(); c->D = c->S + N * ld; c->Dt = c->D + N * ld; c->Nk = c->Dt + N * ld;
+  AsmArgs A = asm_args(c, false);
+  A.S = c->S; A.D = c->D; A.Dt = c->Dt; A.Nk = c->Nk;
+  TRY(assemble_dense(A, c->s));
+  // circle: first rows -> eigenvalues
+  TRY(c->mu.ensure(sizeof(zd) * 6 * N));
+  AsmArgs B = asm_args(c, true);
+  B.S = mu_ptr(c, MU_S); B.D = mu_ptr(c, MU_D); B.Dt = mu_ptr(c, MU_DT); B.Nk = mu_ptr(c, MU_N);
+  TRY(assemble_circle_row(B, c->s));
+  // mu_X(m) = sum_j X_0j e^{+2 pi i m j / N}
+  TRY(fft_columns(c->fft, mu_ptr(c, MU_S), N, 4, +1, c->s));
+  k_mu_finish<<<(unsigned)((N + 255) / 256), 256, 0, c->s>>>(c->mu.z(), N, c->h);
+  TRY(c->small.ensure(sizeof(double) * 8));
+  k_absmax<<<1, 256, 0, c->s>>>(mu_ptr(c, MU_C), N, c->small.d());
+  cudaMemcpyAsync(&c->norm_cc, c->small.p, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+  TRY(sync(c));
+  c->U.release(); c->Vw.release(); c->Wt.release();
+  c->rank = -1;
+  c->stage = ST_ASSEMBLED;
+  return WCS_OK;
+}
+
+int wcs_operator_entries(wcs_ctx* c, int64_t count, const int64_t* rows, const int64_t* cols,
+                         double* out) {
+  if (!c || count < 0 || (count > 0 && (!rows || !cols || !out))) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_MESH) { set_error("mesh first"); return WCS_ERR_STATE; }
+  if (count == 0) return WCS_OK;
+  for (int64_t t = 0; t < count; ++t)
+    if (rows[t] < 0 || rows[t] >= c->N || cols[t] < 0 || cols[t] >= c->N) { set_error("index out of range"); return WCS_ERR_ARG; }
+  DevBuf idx, res;
+  TRY(idx.ensure(sizeof(int64_t) * 2 * count));
+  TRY(res.ensure(sizeof(zd) * 4 * count));
+  cudaMemcpyAsync(idx.p, rows, sizeof(int64_t) * count, cudaMemcpyHostToDevice, c->s);
+  cudaMemcpyAsync((int64_t*)idx.p + count, cols, sizeof(int64_t) * count, cudaMemcpyHostToDevice, c->s);
+  AsmArgs A = asm_args(c, false);
+  int r = assemble_entries(A, count, (int64_t*)idx.p, (int64_t*)idx.p + count, res.z(), c->s);
+  if (!r) {
+    cudaMemcpyAsync(out, res.p, sizeof(zd) * 4 * count, cudaMemcpyDeviceToHost, c->s);
+    r = sync(c);
+  }
+  idx.release();
+  res.release();
+  return r;
+}
+
+int wcs_circulant_eigs(wcs_ctx* c, int op, double* out) {
+  if (!c || !out) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_ASSEMBLED) { set_error("assemble first"); return WCS_ERR_STATE; }
+  int w;
+  switch (op) {
+    case WCS_OP_G: w = MU_G; break;
+    case WCS_OP_S: w = MU_S; break;
+    case WCS_OP_D: w = MU_D; break;
+    case WCS_OP_DT: w = MU_DT; break;
+    case WCS_OP_N: w = MU_N; break;
+    case WCS_OP_CC: w = MU_C; break;
+    default: set_error("operator has no circulant eigenvalues"); return WCS_ERR_ARG;
+  }
+  cudaError_t e = cudaMemcpyAsync(out, mu_ptr(c, w), sizeof(zd) * c->N, cudaMemcpyDeviceToDevice, c->s);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  return WCS_OK;
+}
+
+static int check_block(wcs_ctx* c, int64_t B, const void* p, int64_t ld) {
+  if (B < 0 || (B > 0 && (!p || ld < c->N))) { set_error("bad block argument (pointer or ld < N)"); return WCS_ERR_ARG; }
+  return 0;
+}
+
+int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, double* Y, int64_t ldy) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_ASSEMBLED) { set_error("assemble first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, X, ldx));
+  TRY(check_block(c, B, Y, ldy));
+  if (B == 0) return WCS_OK;
+  const int64_t N = c->N;
+  const zd* x = (const zd*)X;
+  zd* y = (zd*)Y;
+  const int64_t chunk = c->opt.rhs_chunk;
+  TRY(ensure_work(c, std::min(B, chunk)));
+  for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+    const int64_t cc = std::min(chunk, B - c0);
+    const zd* xc = x + c0 * ldx;
+    zd* yc = y + c0 * ldy;
+    switch (op) {
+      case WCS_OP_C: TRY(apply_C(c, xc, ldx, yc, ldy, cc, false)); break;
+      case WCS_OP_CH: TRY(apply_C(c, xc, ldx, yc, ldy, cc, true)); break;
+      case WCS_OP_CC: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 0)); break;
+      case WCS_OP_CCH: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 1)); break;
+      case WCS_OP_CC_INV: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 2)); break;
+      case WCS_OP_S: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->S, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
+      case WCS_OP_D: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->D, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
+      case WCS_OP_DT: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Dt, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
+      case WCS_OP_N: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Nk, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
+      case WCS_OP_G: TRY(gram_apply(xc, ldx, yc, ldy, N, cc, c->h, 1.0, 0.0, c->s)); break;
+      case WCS_OP_SKEL: {
+        if (c->stage < ST_SKELETON) { set_error("skeleton first"); return WCS_ERR_STATE; }
+        const int64_t r = std::max(c->rank, 0);
+        if (r == 0) { TRY(axpby(N, cc, mkz(0.0), xc, ldx, mkz(0.0), yc, ldy, c->s)); break; }
+        TRY(c->small.ensure(sizeof(zd) * r * cc));
+        // U V^T x = Q (Vw^H x)
+        TRY(zgemm(r, cc, N, mkz(1.0), blkH(c->Vw.z(), N), blk(xc, ldx), mkz(0.0), c->small.z(), r, c->s));
+        TRY(zgemm(N, cc, r, mkz(1.0), blk(c->U.z(), N), blk(c->small.z(), r), mkz(0.0), yc, ldy, c->s));
+        break;
+      }
+      default: set_error("unknown operator"); return WCS_ERR_ARG;
+    }
+  }
+  return WCS_OK;
+}
+
+int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_out) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_ASSEMBLED) { set_error("assemble first"); return WCS_ERR_STATE; }
+  if (!(tol >= 0)) { set_error("tolerance must be >= 0"); return WCS_ERR_ARG; }
+  const int64_t N = c->N;
+  const int64_t cap = (max_rank <= 0 || max_rank > N) ? N : max_rank;
+  const int b = c->opt.block;
+  TRY(ensure_work(c, b));
+  TRY(c->U.ensure(sizeof(zd) * N * (cap + b)));
+  zd* Q = c->U.z();
+  const double thr = tol * c->norm_cc / (10.0 * std::sqrt(2.0 / WCS_PI));
+  // small scratch: Z (cap x b), Gram (b x b), perm, rank, norms
+  DevBuf Zb, Gb, Ib, Nb;
+  TRY(Zb.ensure(sizeof(zd) * (cap + b) * b));
+  TRY(Gb.ensure(sizeof(zd) * b * b));
+  TRY(Ib.ensure(sizeof(int) * (b + 1)));
+  TRY(Nb.ensure(sizeof(double) * b));
+  int64_t ell = 0;
+  uint64_t offset = 0;
+  int status = WCS_OK;
+  std::vector<double> norms(b);
+  zd* Om = c->w4.z();
+  zd* Y = c->w5.z();
+  const zd one = mkz(1.0), mone = mkz(-1.0), zero = mkz(0.0);
+  while (true) {
+    if (ell >= cap) { status = (ell < N) ? WCS_ERR_RANK_CAP : WCS_OK; break; }
+    TRY(gaussian_fill(Om, N, N, b, seed, offset, c->s));
+    offset += (uint64_t)N * b;
+    TRY(apply_remainder(c, Om, N, Y, N, b, false));
+    for (int pass = 0; pass < 2 && ell > 0; ++pass) {
+      TRY(zgemm(ell, b, N, one, blkH(Q, N), blk(Y, N), zero, Zb.z(), ell, c->s));
+      TRY(zgemm(N, b, ell, mone, blk(Q, N), blk(Zb.z(), ell), one, Y, N, c->s));
+    }
+    TRY(column_norms(Y, N, N, b, Nb.d(), c->s));
+    cudaMemcpyAsync(norms.data(), Nb.p, sizeof(double) * b, cudaMemcpyDeviceToHost, c->s);
+    TRY(sync(c));
+    double mx = 0;
+    for (int j = 0; j < b; ++j) mx = std::max(mx, norms[j]);
+    if (mx <= thr) break;
+    // orthonormalise the block twice (pivoted CholeskyQR)
+    int rk = b;
+    const zd* src = Y;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int cols = (pass == 0) ? b : rk;
+      TRY(zgemm(cols, cols, N, one, blkH(src, N), blk(src, N), zero, Gb.z(), cols, c->s));
+      TRY(pivoted_cholesky(Gb.z(), cols, 1e-7, (int*)Ib.p, (int*)Ib.p + b, c->s));
+      int rk_new = 0;
+      cudaMemcpyAsync(&rk_new, (int*)Ib.p + b, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+      TRY(sync(c));
+      if (rk_new == 0) { rk = 0; break; }
+      zd* dst = (pass == 0) ? c->w3.z() : Q + ell * N;
+      TRY(trsm_right_upper(src, N, N, Gb.z(), cols, (int*)Ib.p, (int*)Ib.p + b, rk_new, dst, N, c->s));
+      rk = rk_new;
+      if (pass == 0) {
+        // re-orthogonalise against the accepted basis before the second pass
+        if (ell > 0) {
+          TRY(zgemm(ell, rk, N, one, blkH(Q, N), blk(c->w3.z(), N), zero, Zb.z(), ell, c->s));
+          TRY(zgemm(N, rk, ell, mone, blk(Q, N), blk(Zb.z(), ell), one, c->w3.z(), N, c->s));
+        }
+        src = c->w3.z();
+      }
+    }
+    if (rk == 0) break;
+    ell += rk;
+    if (ell > cap) ell = cap;
+  }
+  c->rank = (int)ell;
+  // V^T = Q^H (C - C_c)  <=>  Vw = (C - C_c)^H Q  (V = conj(Vw))
+  TRY(c->Vw.ensure(sizeof(zd) * N * std::max<int64_t>(ell, 1)));
+  for (int64_t c0 = 0; c0 < ell; c0 += b) {
+    const int64_t cc = std::min<int64_t>(b, ell - c0);
+    TRY(apply_remainder(c, Q + c0 * N, N, c->Vw.z() + c0 * N, N, cc, true));
+  }
+  TRY(sync(c));
+  if (rank_out) *rank_out = (int)ell;
+  c->Wt.release();
+  c->stage = ST_SKELETON;
+  return status;
+}
+
+int wcs_factor(wcs_ctx* c) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_SKELETON) { set_error("skeleton first"); return WCS_ERR_STATE; }
+  const int64_t N = c->N, r = c->rank;
+  if (r > 0) {
+    TRY(c->Wt.ensure(sizeof(zd) * N * r));
+    // W = C_c^{-1} U  (held in Wt until the inverse is applied)
+    DevBuf Wb, Kb, Kinv, info;
+    TRY(Wb.ensure(sizeof(zd) * N * r));
+    TRY(apply_Cc(c, c->U.z(), N, Wb.z(), N, r, 2));
+    // K = I + V^T W = I + Vw^H W
+    TRY(Kb.ensure(sizeof(zd) * r * r));
+    TRY(Kinv.ensure(sizeof(zd) * r * r));
+    TRY(zgemm(r, r, N, mkz(1.0), blkH(c->Vw.z(), N), blk(Wb.z(), N), mkz(0.0), Kb.z(), r, c->s));
+    k_add_identity<<<(unsigned)((r + 255) / 256), 256, 0, c->s>>>(Kb.z(), r);
+    TRY(info.ensure(sizeof(int) + sizeof(double) * 2));
+    int* infod = (int*)info.p;
+    double* minpiv = (double*)((char*)info.p + 8);
+    TRY(lu_inverse(Kb.z(), r, Kinv.z(), nullptr, infod, minpiv, c->s));
+    int infoh = 0;
+    double mp = 0;
+    cudaMemcpyAsync(&infoh, infod, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    cudaMemcpyAsync(&mp, minpiv, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+    TRY(sync(c));
+    if (infoh != 0 || !(mp > 1e-14)) { set_error("capacitance matrix is singular"); return WCS_ERR_SINGULAR; }
+    // Wt = W K^{-1}
+    TRY(zgemm(N, r, r, mkz(1.0), blk(Wb.z(), N), blk(Kinv.z(), r), mkz(0.0), c->Wt.z(), N, c->s));
+    TRY(sync(c));
+  }
+  c->stage = ST_FACTORED;
+  return WCS_OK;
+}
+
+int wcs_woodbury_apply(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, b, ldb));
+  TRY(check_block(c, B, x, ldx));
+  const int64_t chunk = c->opt.rhs_chunk;
+  TRY(ensure_work(c, std::min(B, chunk)));
+  for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+    const int64_t cc = std::min(chunk, B - c0);
+    TRY(woodbury(c, (const zd*)b + c0 * ldb, ldb, (zd*)x + c0 * ldx, ldx, cc));
+  }
+  return WCS_OK;
+}
+
+int wcs_planewave_rhs(wcs_ctx* c, int64_t B, const double* angles, double* e, double* hv, int64_t ld) {
+  if (!c || (B > 0 && !angles)) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_MESH) { set_error("mesh first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, e, ld));
+  TRY(check_block(c, B, hv, ld));
+  if (B == 0) return WCS_OK;
+  DevBuf ang;
+  TRY(ang.ensure(sizeof(double) * B));
+  cudaMemcpyAsync(ang.p, angles, sizeof(double) * B, cudaMemcpyHostToDevice, c->s);
+  int r = planewave_rhs(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, c->N, c->h, c->k, ang.d(),
+                        (int)B, (zd*)e, (zd*)hv, ld, c->s);
+  if (!r) r = sync(c);
+  ang.release();
+  return r;
+}
+
+// b = -i k S~ G^{-1} e - (G/2 + D~) G^{-1} h  (Eq. 5), cc columns.
+static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b, int64_t ldb, int64_t cc) {
+  const int64_t N = c->N;
+  zd* T1 = c->w1.z();
+  zd* T2 = c->w2.z();
+  TRY(gram_inverse(e, ld, T1, N, N, cc, c->h, c->s));
+  TRY(gram_inverse(hv, ld, T2, N, N, cc, c->h, c->s));
+  TRY(zgemm(N, cc, N, mkz(0.0, -c->k), op_view(c->S, c->ld, false), blk(T1, N), mkz(0.0), b, ldb, c->s));
+  TRY(zgemm(N, cc, N, mkz(-1.0), op_view(c->Dt, c->ld, false), blk(T2, N), mkz(1.0), b, ldb, c->s));
+  TRY(gram_apply(T2, N, b, ldb, N, cc, c->h, -0.5, 1.0, c->s));
+  return 0;
+}
+
+// x = C^{-1} b with Woodbury + iterative refinement on the exact operator.
+static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx, int64_t cc,
+                       int* steps, double* relres) {
+  const int64_t N = c->N;
+  TRY(woodbury(c, b, ldb, x, ldx, cc));
+  DevBuf nb;
+  TRY(nb.ensure(sizeof(double) * 2 * cc));
+  std::vector<double> bn(cc), rn(cc);
+  TRY(column_norms(b, ldb, N, cc, nb.d(), c->s));
+  cudaMemcpyAsync(bn.data(), nb.p, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
+  zd* R = c->w4.z();
+  zd* dx = c->w5.z();
+  int it = 0;
+  double worst = 0;
+  for (;; ++it) {
+    TRY(apply_C(c, x, ldx, R, N, cc, false));
+    TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));   // R = b - C x
+    TRY(column_norms(R, N, N, cc, nb.d() + cc, c->s));
+    cudaMemcpyAsync(rn.data(), nb.d() + cc, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
+    TRY(sync(c));
+    worst = 0;
+    for (int64_t j = 0; j < cc; ++j) worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
+    if (worst <= c->opt.refine_tol || it >= c->opt.max_refine) break;
+    TRY(woodbury(c, R, N, dx, N, cc));
+    TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
+  }
+  nb.release();
+  *steps = std::max(*steps, it);
+  *relres = std::max(*relres, worst);
+  return (worst <= c->opt.refine_tol) ? 0 : WCS_ERR_NOT_CONVERGED;
+}
+
+int wcs_solve_rhs(wcs_ctx* c, int64_t B, const double* e, const double* hv, int64_t ld, double* j,
+                  int64_t ldj, wcs_solve_info* info) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, e, ld));
+  TRY(check_block(c, B, hv, ld));
+  TRY(check_block(c, B, j, ldj));
+  const int64_t chunk = c->opt.rhs_chunk, N = c->N;
+  TRY(ensure_work(c, std::min(B, chunk)));
+  DevBuf bb;
+  TRY(bb.ensure(sizeof(zd) * N * std::min(B, chunk)));
+  int steps = 0, status = WCS_OK;
+  double rr = 0;
+  for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+    const int64_t cc = std::min(chunk, B - c0);
+    TRY(precondition(c, (const zd*)e + c0 * ld, (const zd*)hv + c0 * ld, ld, bb.z(), N, cc));
+    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr);
+    if (r == WCS_ERR_NOT_CONVERGED) status = r;
+    else if (r) return r;
+  }
+  bb.release();
+  if (info) { info->refine_steps = steps; info->rel_residual = rr; }
+  if (status) set_error("iterative refinement did not reach refine_tol");
+  return status;
+}
+
+int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j, int64_t ldj,
+                         wcs_solve_info* info) {
+  if (!c || (B > 0 && !angles)) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, j, ldj));
+  if (B == 0) return WCS_OK;
+  const int64_t chunk = c->opt.rhs_chunk, N = c->N;
+  TRY(ensure_work(c, std::min(B, chunk)));
+  DevBuf eb, hb, bb, ang;
+  const int64_t cmax = std::min(B, chunk);
+  TRY(eb.ensure(sizeof(zd) * N * cmax));
+  TRY(hb.ensure(sizeof(zd) * N * cmax));
+  TRY(bb.ensure(sizeof(zd) * N * cmax));
+  TRY(ang.ensure(sizeof(double) * B));
+  cudaMemcpyAsync(ang.p, angles, sizeof(double) * B, cudaMemcpyHostToDevice, c->s);
+  int steps = 0, status = WCS_OK;
+  double rr = 0;
+  for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+    const int64_t cc = std::min(chunk, B - c0);
+    TRY(planewave_rhs(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, N, c->h, c->k, ang.d() + c0,
+                      (int)cc, eb.z(), hb.z(), N, c->s));
+    TRY(precondition(c, eb.z(), hb.z(), N, bb.z(), N, cc));
+    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr);
+    if (r == WCS_ERR_NOT_CONVERGED) status = r;
+    else if (r) return r;
+  }
+  if (info) { info->refine_steps = steps; info->rel_residual = rr; }
+  if (status) set_error("iterative refinement did not reach refine_tol");
+  return status;
+}
+
+int wcs_solve_planewaves_host(wcs_ctx* c, int64_t B, const double* angles, double* j_host,
+                              int64_t ldj, wcs_solve_info* info) {
+  if (!c || (B > 0 && (!angles || !j_host)) || ldj < (c ? c->N : 0)) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (B == 0) return WCS_OK;
+  DevBuf jd;
+  TRY(jd.ensure(sizeof(zd) * c->N * B));
+  int r = wcs_solve_planewaves(c, B, angles, jd.d(), c->N, info);
+  if (r && r != WCS_ERR_NOT_CONVERGED) { jd.release(); return r; }
+  cudaMemcpy2DAsync(j_host, sizeof(zd) * ldj, jd.p, sizeof(zd) * c->N, sizeof(zd) * c->N, B,
+                    cudaMemcpyDeviceToHost, c->s);
+  int r2 = sync(c);
+  jd.release();
+  return r2 ? r2 : r;
+}
+
+int wcs_farfield(wcs_ctx* c, int64_t B, const double* j, int64_t ldj, int nphi, const double* phi,
+                 double* F, int64_t ldf) {
+  if (!c || nphi < 0 || (nphi > 0 && (!phi || !F)) || ldf < nphi) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_MESH) { set_error("mesh first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, j, ldj));
+  if (B == 0 || nphi == 0) return WCS_OK;
+  DevBuf E, ang;
+  TRY(E.ensure(sizeof(zd) * (int64_t)nphi * c->N));
+  TRY(ang.ensure(sizeof(double) * nphi));
+  cudaMemcpyAsync(ang.p, phi, sizeof(double) * nphi, cudaMemcpyHostToDevice, c->s);
+  TRY(farfield_matrix(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, c->N, c->h, c->k, ang.d(),
+                      nphi, E.z(), nphi, c->s));
+  TRY(zgemm(nphi, B, c->N, mkz(1.0), ZView{E.z(), 1, nphi, false}, blk((const zd*)j, ldj), mkz(0.0),
+            (zd*)F, ldf, c->s));
+  int r = sync(c);
+  E.release();
+  ang.release();
+  return r;
+}
+
+int wcs_quadrature_tables(int q, double* out) {
+  if (q < 2 || q > 16 || !out) { set_error("bad argument"); return WCS_ERR_ARG; }
+  QuadTables t;
+  t.q_near = q;
+  t.q_far = q;
+  build_quad_tables(t);
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < q * q; ++i) out[k * q * q + i] = t.wlog[k][i];
+  return WCS_OK;
+}
+
+}  // extern "C"

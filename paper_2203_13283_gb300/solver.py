@@ -1,0 +1,187 @@
+"""Python binding of the solver library: marshals torch/numpy buffers into the
+C ABI of include/wcs.h.  Every computation runs in libwcs.so on the GPU;
+torch only provides device memory and the stream."""
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import OPS, Info, Options, SolveInfo, check, load
+
+
+def default_options(**overrides):
+    o = Options()
+    check(load().wcs_default_options(C.byref(o)))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(C.c_void_p)
+
+
+class Solver:
+    """One contour, its mesh, operators, skeleton and factorisation (one CUDA device)."""
+
+    def __init__(self, device=None, stream=None, **options):
+        self.lib = load()
+        self.device = torch.device(device or "cuda")
+        if self.device.type != "cuda":
+            raise ValueError("the solver runs on a CUDA device only")
+        torch.cuda.set_device(self.device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.opt = default_options(**options)
+        h = C.c_void_p()
+        check(self.lib.wcs_create(C.byref(h), C.byref(self.opt), C.c_void_p(self.stream.cuda_stream)))
+        self.h = h
+        self.N = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.wcs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- contour and mesh
+    def contour(self, family, **p):
+        if family == "circle":
+            check(self.lib.wcs_contour_circle(self.h, float(p.get("a", 1.0))))
+        elif family == "ellipse":
+            check(self.lib.wcs_contour_ellipse(self.h, float(p["ax"]), float(p["ay"])))
+        elif family == "superellipse":
+            check(self.lib.wcs_contour_superellipse(self.h, float(p["ax"]), float(p["ay"]), float(p["p"])))
+        elif family == "fourier":
+            cc, pc = _host(p["cos"], np.float64)
+            ss, ps = _host(p.get("sin", np.zeros(len(cc))), np.float64)
+            check(self.lib.wcs_contour_fourier(self.h, len(cc), pc, ps))
+        else:
+            raise ValueError(family)
+        return self
+
+    def mesh(self, N, k=None):
+        check(self.lib.wcs_mesh(self.h, int(N), float(k) if k else 0.0))
+        self.N = int(N)
+        return self
+
+    def info(self):
+        i = Info()
+        check(self.lib.wcs_query(self.h, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in Info._fields_}
+
+    def geometry_sample(self, s):
+        s, ps = _host(s, np.float64)
+        out = np.empty(5 * len(s))
+        check(self.lib.wcs_geometry_sample(self.h, len(s), ps, out.ctypes.data_as(C.c_void_p)))
+        out = out.reshape(5, len(s))
+        return dict(zip(("x", "y", "nx", "ny", "kappa"), out))
+
+    # ---- setup
+    def assemble(self):
+        check(self.lib.wcs_assemble(self.h))
+        return self
+
+    def skeleton(self, tol, max_rank=0, seed=0, allow_cap=False):
+        r = C.c_int(0)
+        allow = (_lib.WCS_ERR_RANK_CAP,) if allow_cap else ()
+        check(self.lib.wcs_skeleton(self.h, float(tol), int(max_rank), int(seed), C.byref(r)), allow)
+        return r.value
+
+    def factor(self):
+        check(self.lib.wcs_factor(self.h))
+        return self
+
+    # ---- blocks: (N, B) views of column-major storage
+    def _block(self, B):
+        return torch.empty((B, self.N), dtype=torch.complex128, device=self.device)
+
+    def _as_cols(self, X):
+        X = torch.as_tensor(X, dtype=torch.complex128, device=self.device)
+        if X.dim() == 1:
+            X = X[:, None]
+        return X.t().contiguous()  # (B, N) row-major == N x B column-major
+
+    def apply(self, op, X):
+        Xc = self._as_cols(X)
+        B = Xc.shape[0]
+        Y = self._block(B)
+        check(self.lib.wcs_apply(self.h, OPS[op], B, _ptr(Xc), self.N, _ptr(Y), self.N))
+        return Y.t()
+
+    def circulant_eigs(self, op):
+        out = torch.empty(self.N, dtype=torch.complex128, device=self.device)
+        check(self.lib.wcs_circulant_eigs(self.h, OPS[op], _ptr(out)))
+        return out
+
+    def operator_entries(self, rows, cols):
+        r, pr = _host(rows, np.int64)
+        c, pc = _host(cols, np.int64)
+        out = np.empty(4 * len(r), dtype=np.complex128)
+        check(self.lib.wcs_operator_entries(self.h, len(r), pr, pc, out.ctypes.data_as(C.c_void_p)))
+        return dict(zip(("S", "D", "Dt", "N"), out.reshape(4, len(r))))
+
+    def planewave_rhs(self, angles):
+        a, pa = _host(angles, np.float64)
+        e, hv = self._block(len(a)), self._block(len(a))
+        check(self.lib.wcs_planewave_rhs(self.h, len(a), pa, _ptr(e), _ptr(hv), self.N))
+        return e.t(), hv.t()
+
+    def woodbury_apply(self, b):
+        bc = self._as_cols(b)
+        x = self._block(bc.shape[0])
+        check(self.lib.wcs_woodbury_apply(self.h, bc.shape[0], _ptr(bc), self.N, _ptr(x), self.N))
+        return x.t()
+
+    def solve_planewaves(self, angles, out=None, allow_unconverged=False):
+        a, pa = _host(angles, np.float64)
+        j = out if out is not None else self._block(len(a))
+        si = SolveInfo()
+        allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+        check(self.lib.wcs_solve_planewaves(self.h, len(a), pa, _ptr(j), self.N, C.byref(si)), allow)
+        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        return j.t()
+
+    def solve_planewaves_host(self, angles, allow_unconverged=False):
+        a, pa = _host(angles, np.float64)
+        j = np.empty((len(a), self.N), dtype=np.complex128)
+        si = SolveInfo()
+        allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+        check(self.lib.wcs_solve_planewaves_host(self.h, len(a), pa, j.ctypes.data_as(C.c_void_p),
+                                                 self.N, C.byref(si)), allow)
+        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        return j.T
+
+    def solve_rhs(self, e, hv, allow_unconverged=False):
+        ec, hc = self._as_cols(e), self._as_cols(hv)
+        j = self._block(ec.shape[0])
+        si = SolveInfo()
+        allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+        check(self.lib.wcs_solve_rhs(self.h, ec.shape[0], _ptr(ec), _ptr(hc), self.N, _ptr(j), self.N,
+                                     C.byref(si)), allow)
+        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        return j.t()
+
+    def farfield(self, j, phi):
+        jc = self._as_cols(j)
+        p, pp = _host(phi, np.float64)
+        F = torch.empty((jc.shape[0], len(p)), dtype=torch.complex128, device=self.device)
+        check(self.lib.wcs_farfield(self.h, jc.shape[0], _ptr(jc), self.N, len(p), pp, _ptr(F), len(p)))
+        return F.t()
+
+
+def quadrature_tables(q):
+    out = np.empty(3 * q * q)
+    check(load().wcs_quadrature_tables(int(q), out.ctypes.data_as(C.c_void_p)))
+    return out.reshape(3, q, q)

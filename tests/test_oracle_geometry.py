@@ -111,6 +111,6 @@ def test_log_integrals_numeric(kind):
                 ref = si.dblquad(g, 0, 1, 0, 1, epsabs=1e-11, epsrel=1e-11)[0]
             assert abs(I[a, b] - ref) < 1e-8
     if kind == "self":
-        assert abs(I1 + 1.5) < 1e-15
+        assert abs(I1 + 1.5) < 1e-14
     else:
-        assert abs(I1 - (2 * np.log(2) - 1.5)) < 1e-15
+        assert abs(I1 - (2 * np.log(2) - 1.5)) < 1e-14
