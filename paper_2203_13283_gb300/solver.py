@@ -36,6 +36,8 @@ class Solver:
         self.device = torch.device(device or "cuda")
         if self.device.type != "cuda":
             raise ValueError("the solver runs on a CUDA device only")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         torch.cuda.set_device(self.device)
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.opt = default_options(**options)
