@@ -200,6 +200,18 @@ int wcs_planewave_rhs(wcs_ctx* ctx, int64_t B, const double* angles_host, double
 int wcs_farfield(wcs_ctx* ctx, int64_t B, const double* j_dev, int64_t ldj, int nphi,
                  const double* phi_host, double* F_dev, int64_t ldf);
 
+/* Real contraction on the tensor cores (tcgen05, sm_103a) with split-bf16
+ * operands: D (M x Nc) = A (M x K) * B (Nc x K)^T, all FP64 row-major device
+ * arrays (lda, ldb >= K, ldd >= Nc).  Each operand is rounded to `planes`
+ * bf16 terms (1: bf16, 2: ~16 bits, 3: ~24 bits) and every product of
+ * combined order < planes is accumulated in FP32 in tensor memory.  This is
+ * the contraction behind the mixed-precision operator products of Eq. (5)-(7).
+ * Allocates its own staging buffers; ordered on `stream`; synchronises.
+ * Returns WCS_ERR_TIMEOUT if a bounded device wait expired. */
+int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
+                        const double* B_dev, int64_t ldb, int planes, double* D_dev, int64_t ldd,
+                        void* stream);
+
 /* Host-only: product-integration weights of the near-field rule with q points
  * (3 * q * q doubles: coincident, next-neighbour, previous-neighbour pairs). */
 int wcs_quadrature_tables(int q, double* out_host);

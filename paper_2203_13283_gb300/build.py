@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwcs.so")
-SOURCES = ["geometry.cu", "quad.cu", "assemble.cu", "fft.cu", "linalg.cu", "rhs.cu", "solver.cu"]
+SOURCES = ["geometry.cu", "quad.cu", "assemble.cu", "fft.cu", "linalg.cu", "rhs.cu", "gemm_tc.cu",
+           "mixed.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

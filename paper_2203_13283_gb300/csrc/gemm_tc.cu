@@ -1,0 +1,314 @@
+// Tensor-core contraction for the mixed-precision form: the sampling of the
+// skeleton (Eq. 7), the preconditioned right-hand side of Eq. (5) and the
+// operator applies of Eq. (6) are dense complex products with the assembled
+// Galerkin matrices, carried out here as real products on the 5th-generation
+// tensor cores of sm_103a.
+//
+//   D (M x Nc, FP32) = sum_p  A_{ia[p]} (M x K) * B_{ib[p]} (Nc x K)^T
+//
+// A and B are bf16 "planes" (split-bf16: x = hi + lo [+ lo2]), K-major (row
+// major with K contiguous).  Tiles of A (128 x 64) and B (NT x 64) are staged
+// by TMA (128-byte swizzle) into a multi-stage shared-memory ring guarded by
+// mbarriers; one thread issues tcgen05.mma (kind::f16, M = 128, N = NT,
+// K = 16) accumulating in TMEM; tcgen05.commit releases ring slots; the four
+// warps drain TMEM with tcgen05.ld in the epilogue, which applies a complex
+// combination (see Epi) and writes FP32 or FP64 output.
+//
+// Every wait on an mbarrier is bounded; on expiry the kernel records an error
+// code in *err, stops issuing work, waits (bounded) for its own copies and
+// MMAs, frees TMEM and returns, so the host sees WCS_ERR_TIMEOUT.
+#include <cuda.h>
+
+#include "gemm_tc.h"
+
+namespace wcs {
+
+// ----------------------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: gives up after `budget` SM clock cycles, or as soon as any CTA
+// of the launch has raised the global error flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget,
+                                          const volatile int* gerr) {
+  const long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 255u && (clock64() - t0 > budget || *gerr != 0)) return false;
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t sw128_desc(const void* tile) {
+  // tcgen05 shared-memory matrix descriptor: K-major, 128-byte swizzle,
+  // rows of 128 B, 8-row core groups 1024 B apart (SBO), version 1.
+  const uint64_t a = smem_u32(tile);
+  uint64_t d = 0;
+  d |= (a >> 4) & 0x3FFFull;            // start address
+  d |= (uint64_t)1 << 16;               // LBO (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;     // SBO
+  d |= (uint64_t)1 << 46;               // descriptor version
+  d |= (uint64_t)2 << 61;               // SWIZZLE_128B
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+          dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ----------------------------------------------------------------------------- kernel
+constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128;
+constexpr long long WAIT_LIMIT = 4000000000ll;  // SM cycles (~2 s) before a wait is declared stuck
+
+template <int NT, int PA, int PB, int STAGES>
+struct TcSmem {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;   // 16 KB
+  static constexpr int B_BYTES = NT * TC_BK * 2;      // 16 or 32 KB
+  static constexpr int STAGE_BYTES = PA * A_BYTES + PB * B_BYTES;
+  static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, flags*/;
+};
+
+template <int NT, int PA, int PB, int STAGES>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+              const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+              const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, TcArgs args) {
+  using L = TcSmem<NT, PA, PB, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * L::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tslot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TC_BM;
+  const int n0 = blockIdx.x * NT;
+  const int nk = (args.K + TC_BK - 1) / TC_BK;
+
+  if (*(volatile int*)args.err != 0) return;  // another CTA already gave up: do nothing
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"((uint32_t)NT));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+
+  const CUtensorMap* mapA[3] = {&mA0, &mA1, &mA2};
+  const CUtensorMap* mapB[3] = {&mB0, &mB1, &mB2};
+  // instruction descriptor: D f32, A bf16, B bf16, both K-major, N, M
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                         ((uint32_t)(TC_BM >> 4) << 24);
+
+  volatile int* issued = (volatile int*)(tslot + 2);     // k-blocks whose loads were issued
+  volatile int* consumed = (volatile int*)(tslot + 3);   // k-blocks the MMA thread waited for
+  if (threadIdx.x == 0) { *issued = 0; *consumed = 0; }
+  __syncthreads();
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES) {
+        if (!mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * L::STAGE_BYTES;
+      mbar_expect_tx(&full[s], L::STAGE_BYTES);
+      const int k0 = kb * TC_BK;
+#pragma unroll
+      for (int p = 0; p < PA; ++p) tma_load_2d(st + p * L::A_BYTES, mapA[p], &full[s], k0, m0);
+#pragma unroll
+      for (int p = 0; p < PB; ++p) tma_load_2d(st + PA * L::A_BYTES + p * L::B_BYTES, mapB[p], &full[s], k0, n0);
+      *issued = kb + 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+      *consumed = kb + 1;
+      if (*abort_flag) break;
+      tc_fence_after();
+      uint8_t* st = smem + s * L::STAGE_BYTES;
+      for (int p = 0; p < args.nprod; ++p) {
+        const uint8_t* ta = st + args.ia[p] * L::A_BYTES;
+        const uint8_t* tb = st + PA * L::A_BYTES + args.ib[p] * L::B_BYTES;
+        const uint64_t da = sw128_desc(ta), db = sw128_desc(tb);
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          // advance 16 bf16 = 32 bytes along K inside the swizzle atom
+          mma_bf16(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
+                   (kb > 0 || p > 0 || kk > 0) ? 1u : 0u);
+        }
+      }
+      mma_commit(&empty[s]);
+    }
+    mma_commit(done);   // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+  // ---------------- epilogue: all four warps
+  bool got = mbar_wait(done, 0, WAIT_LIMIT, args.err);
+  got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
+  tc_fence_after();
+  if (!got) {
+    if (threadIdx.x == 0) {
+      const int zero_flag = 0;
+      atomicExch(args.err, 1);
+      // let the loads already in flight land before the CTA's shared memory goes away
+      for (int kb = *consumed; kb < *issued; ++kb)
+        (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
+    }
+  } else {
+    const int row = m0 + warp * 32 + lane;   // TMEM lane = tile row
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      epilogue_store(args, row, n0 + c0, v);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)NT));
+  }
+}
+
+// ----------------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
+}
+
+// bf16 matrix rows x cols (K = cols contiguous), leading dimension ld elements
+static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) { set_error("cuTensorMapEncodeTiled unavailable"); return 3; }
+  if (((uintptr_t)base & 15) || ((ld * 2) & 15)) { set_error("tensor map: base or pitch not 16-byte aligned"); return 1; }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_error("cuTensorMapEncodeTiled failed"); return 3; }
+  return 0;
+}
+
+template <int NT, int PA, int PB, int STAGES>
+static int launch_tc(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaStream_t s) {
+  using L = TcSmem<NT, PA, PB, STAGES>;
+  CUtensorMap ma[3], mb[3];
+  std::memset(ma, 0, sizeof(ma));
+  std::memset(mb, 0, sizeof(mb));
+  for (int p = 0; p < PA; ++p) TRY_TC(make_map(&ma[p], A.plane[p], args.M, args.K, A.ld, TC_BM));
+  for (int p = 0; p < PB; ++p) TRY_TC(make_map(&mb[p], B.plane[p], args.Nc, args.K, B.ld, NT));
+  for (int p = PA; p < 3; ++p) ma[p] = ma[0];
+  for (int p = PB; p < 3; ++p) mb[p] = mb[0];
+  auto kern = k_gemm_tc<NT, PA, PB, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    attr = true;
+  }
+  dim3 grid((unsigned)((args.Nc + NT - 1) / NT), (unsigned)((args.M + TC_BM - 1) / TC_BM));
+  kern<<<grid, TC_THREADS, L::TOTAL, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], args);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("gemm_tc launch: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
+}
+
+int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s) {
+  if (args.M <= 0 || args.Nc <= 0 || args.K <= 0) return 0;
+  if (args.nprod < 1 || args.nprod > 6) { set_error("gemm_tc: 1..6 products"); return 1; }
+  if (A.planes < 1 || A.planes > 3 || B.planes < 1 || B.planes > 3) { set_error("gemm_tc: 1..3 planes"); return 1; }
+  for (int p = 0; p < args.nprod; ++p)
+    if (args.ia[p] >= A.planes || args.ib[p] >= B.planes) { set_error("gemm_tc: plane index"); return 1; }
+  if ((args.M + TC_BM - 1) / TC_BM > 65535) { set_error("gemm_tc: M too large"); return 1; }
+  const int key = A.planes * 10 + B.planes;
+  switch (key) {
+    case 11: return launch_tc<256, 1, 1, 4>(A, B, args, s);
+    case 22: return launch_tc<256, 2, 2, 2>(A, B, args, s);
+    case 33: return launch_tc<128, 3, 3, 2>(A, B, args, s);
+    default: set_error("gemm_tc: plane combination not built"); return 1;
+  }
+}
+
+}  // namespace wcs

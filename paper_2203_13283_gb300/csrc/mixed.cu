@@ -1,0 +1,81 @@
+// Staging of FP64 data into split-bf16 planes for the tensor-core contraction.
+// x = p0 + p1 (+ p2): p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1),
+// all with round-to-nearest, so each extra plane adds about 8 bits.
+#include <cuda_bf16.h>
+
+#include "gemm_tc.h"
+
+namespace wcs {
+
+__device__ __forceinline__ void split3(double x, int planes, uint16_t* o0, uint16_t* o1, uint16_t* o2) {
+  __nv_bfloat16 h0 = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(h0);
+  *o0 = __bfloat16_as_ushort(h0);
+  if (planes > 1) {
+    __nv_bfloat16 h1 = __double2bfloat16(r);
+    r -= (double)__bfloat162float(h1);
+    *o1 = __bfloat16_as_ushort(h1);
+    if (planes > 2) *o2 = __bfloat16_as_ushort(__double2bfloat16(r));
+  }
+}
+
+__global__ void k_split_real(const double* X, int64_t rows, int64_t cols, int64_t ld, int planes,
+                             uint16_t* p0, uint16_t* p1, uint16_t* p2, int64_t ldp) {
+  const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t r = blockIdx.y;
+  if (c >= cols) return;
+  const int64_t o = r * ldp + c;
+  uint16_t d1, d2;
+  split3(X[r * ld + c], planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
+}
+
+int split_real_f64(const double* X, int64_t rows, int64_t cols, int64_t ld, int planes, uint16_t* const* P,
+                   int64_t ldp, cudaStream_t s) {
+  for (int64_t r0 = 0; r0 < rows; r0 += 65535) {
+    const int64_t rr = std::min<int64_t>(65535, rows - r0);
+    dim3 g((unsigned)((cols + 255) / 256), (unsigned)rr);
+    k_split_real<<<g, 256, 0, s>>>(X + r0 * ld, rr, cols, ld, planes, P[0] + r0 * ldp,
+                                   planes > 1 ? P[1] + r0 * ldp : nullptr, planes > 2 ? P[2] + r0 * ldp : nullptr, ldp);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("split: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
+}
+
+int split_complex_rows(const zd* X, int64_t rows, int64_t cols, int64_t ld, int planes, uint16_t* const* P,
+                       int64_t ldp, cudaStream_t s) {
+  return split_real_f64((const double*)X, rows, 2 * cols, 2 * ld, planes, P, ldp, s);
+}
+
+__global__ void k_stage_rhs(const zd* X, int64_t n, int64_t B, int64_t ldx, int conj_in, int planes,
+                            uint16_t* p0, uint16_t* p1, uint16_t* p2, int64_t ldp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t j = blockIdx.y;
+  if (i >= n) return;
+  zd x = X[j * ldx + i];
+  if (conj_in) x.y = -x.y;
+  // row 2j: (Re x, -Im x); row 2j+1: (Im x, Re x)
+  const double v[4] = {x.x, -x.y, x.y, x.x};
+  const int64_t o[4] = {(2 * j) * ldp + 2 * i, (2 * j) * ldp + 2 * i + 1, (2 * j + 1) * ldp + 2 * i,
+                        (2 * j + 1) * ldp + 2 * i + 1};
+  uint16_t d1, d2;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    split3(v[t], planes, p0 + o[t], planes > 1 ? p1 + o[t] : &d1, planes > 2 ? p2 + o[t] : &d2);
+}
+
+int stage_rhs(const zd* X, int64_t n, int64_t B, int64_t ldx, int conj_in, int planes, uint16_t* const* P,
+              int64_t ldp, cudaStream_t s) {
+  for (int64_t b0 = 0; b0 < B; b0 += 32768) {
+    const int64_t bb = std::min<int64_t>(32768, B - b0);
+    dim3 g((unsigned)((n + 255) / 256), (unsigned)bb);
+    k_stage_rhs<<<g, 256, 0, s>>>(X + b0 * ldx, n, bb, ldx, conj_in, planes, P[0] + 2 * b0 * ldp,
+                                  planes > 1 ? P[1] + 2 * b0 * ldp : nullptr,
+                                  planes > 2 ? P[2] + 2 * b0 * ldp : nullptr, ldp);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("stage_rhs: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
+}
+
+}  // namespace wcs

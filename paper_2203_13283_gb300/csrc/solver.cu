@@ -13,6 +13,7 @@
 
 #include "../../include/wcs.h"
 #include "internal.h"
+#include "gemm_tc.h"
 
 namespace wcs {
 static thread_local std::string g_err;
@@ -819,6 +820,52 @@ int wcs_farfield(wcs_ctx* c, int64_t B, const double* j, int64_t ldj, int nphi, 
   E.release();
   ang.release();
   return r;
+}
+
+int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, int planes, double* D, int64_t ldd, void* stream) {
+  if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (!A || lda < K)) ||
+      (Nc > 0 && (!B || ldb < K)) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
+    set_error("bad argument");
+    return WCS_ERR_ARG;
+  }
+  if (M == 0 || Nc == 0) return WCS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t ldp = ((K + 63) / 64) * 64;
+  DevBuf pa, pb, err;
+  TRY(pa.ensure(sizeof(uint16_t) * ldp * M * planes));
+  TRY(pb.ensure(sizeof(uint16_t) * ldp * Nc * planes));
+  TRY(err.ensure(sizeof(int)));
+  cudaMemsetAsync(pa.p, 0, pa.bytes, s);
+  cudaMemsetAsync(pb.p, 0, pb.bytes, s);
+  cudaMemsetAsync(err.p, 0, sizeof(int), s);
+  uint16_t* PA[3];
+  uint16_t* PB[3];
+  for (int p = 0; p < 3; ++p) {
+    PA[p] = (uint16_t*)pa.p + (int64_t)p * ldp * M;
+    PB[p] = (uint16_t*)pb.p + (int64_t)p * ldp * Nc;
+  }
+  TRY(split_real_f64(A, M, K, lda, planes, PA, ldp, s));
+  TRY(split_real_f64(B, Nc, K, ldb, planes, PB, ldp, s));
+  TcOperand oa, ob;
+  oa.planes = ob.planes = planes;
+  oa.ld = ob.ld = ldp;
+  for (int p = 0; p < planes; ++p) { oa.plane[p] = PA[p]; ob.plane[p] = PB[p]; }
+  TcArgs t;
+  t.M = (int)M; t.Nc = (int)Nc; t.K = (int)K;
+  tc_products(planes, t);
+  t.epi = EPI_RAW_F64;
+  t.out = D;
+  t.ldo = ldd;
+  t.err = (int*)err.p;
+  TRY(gemm_tc(oa, ob, t, s));
+  int errh = 0;
+  cudaMemcpyAsync(&errh, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  pa.release(); pb.release(); err.release();
+  if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  if (errh) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
+  return WCS_OK;
 }
 
 int wcs_quadrature_tables(int q, double* out) {

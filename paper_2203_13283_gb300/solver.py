@@ -187,3 +187,16 @@ def quadrature_tables(q):
     out = np.empty(3 * q * q)
     check(load().wcs_quadrature_tables(int(q), out.ctypes.data_as(C.c_void_p)))
     return out.reshape(3, q, q)
+
+
+def gemm_split_bf16(A, B, planes=2):
+    """D = A @ B.T on the tensor cores with split-bf16 operands (FP64 in/out, cuda)."""
+    A = torch.as_tensor(A, dtype=torch.float64, device="cuda").contiguous()
+    B = torch.as_tensor(B, dtype=torch.float64, device="cuda").contiguous()
+    M, K = A.shape
+    Nc = B.shape[0]
+    D = torch.empty((M, Nc), dtype=torch.float64, device=A.device)
+    st = torch.cuda.current_stream(A.device)
+    check(load().wcs_gemm_split_bf16(M, Nc, K, _ptr(A), K, _ptr(B), K, int(planes), _ptr(D), Nc,
+                                     C.c_void_p(st.cuda_stream)))
+    return D

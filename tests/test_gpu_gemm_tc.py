@@ -1,0 +1,26 @@
+"""Tensor-core (tcgen05) split-bf16 contraction against an FP64 matmul."""
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("M,Nc,K", [(128, 256, 64), (256, 512, 1024), (200, 100, 300), (1000, 700, 4096),
+                                    (130, 260, 70)])
+@pytest.mark.parametrize("planes", [1, 2, 3])
+def test_split_bf16_gemm(M, Nc, K, planes):
+    built()
+    from paper_2203_13283_gb300.solver import gemm_split_bf16
+    g = torch.Generator(device="cpu").manual_seed(M * 7 + Nc + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(Nc, K, generator=g, dtype=torch.float64).cuda()
+    D = gemm_split_bf16(A, B, planes)
+    ref = A @ B.T
+    err = ((D - ref).abs().max() / (A.abs() @ B.abs().T).max()).item()
+    # bound: input rounding 2^-(8 planes) plus FP32 accumulation over K
+    bound = {1: 1e-2, 2: 6e-5, 3: 1e-5}[planes]   # 3 planes: FP32 accumulation floor
+    assert err < bound, err
