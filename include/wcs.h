@@ -47,20 +47,27 @@ typedef enum wcs_status {
 
 typedef enum wcs_precision {
   WCS_PREC_FP64 = 0,        /* every stage in complex FP64 */
-  WCS_PREC_MIXED = 1        /* reserved for the tensor-core form */
+  WCS_PREC_MIXED = 1        /* operator products on the tensor cores (split-bf16, FP32
+                               accumulation), far-field kernels in FP32 with FP64 phase;
+                               FP64 singular quadrature, circulant eigenvalues,
+                               capacitance matrix and refinement vectors */
 } wcs_precision;
 
 /* Tunables.  Obtain defaults with wcs_default_options, then override. */
 typedef struct wcs_options {
   int precision;      /* wcs_precision */
-  int q_far;          /* Gauss points per element for element pairs farther than near_band (default 6) */
+  int q_far;          /* Gauss points per element for element pairs farther than near_band
+                         (default 0 = automatic: 6 in the FP64 form, 4 in the mixed form) */
   int q_near;         /* Gauss points per element for near and singular pairs (default 12, max 16) */
   int near_band;      /* periodic element distance treated as near (default 4) */
   int block;          /* randomized sampling block width (default 32, max 64) */
   int max_refine;     /* maximum iterative-refinement steps per solve (default 12) */
   double refine_tol;  /* target relative residual ||b - C x|| / ||b|| per column (default 1e-12) */
   int rhs_chunk;      /* right-hand sides processed per pass (default 256) */
-  int reserved[7];
+  int mixed_planes;   /* mixed form: bf16 planes per operator entry (default 2, max 3) */
+  int rhs_planes;     /* mixed form: bf16 planes per staged vector entry (= mixed_planes) */
+  double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h use the FP32 path (default 14) */
+  int reserved[2];
 } wcs_options;
 
 typedef struct wcs_info {
@@ -211,6 +218,20 @@ int wcs_farfield(wcs_ctx* ctx, int64_t B, const double* j_dev, int64_t ldj, int 
 int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
                         const double* B_dev, int64_t ldb, int planes, double* D_dev, int64_t ldd,
                         void* stream);
+
+/* Number of CUDA kernel launches the library has issued in this process. */
+uint64_t wcs_launch_count(void);
+
+/* Per-kernel timing with CUDA events recorded on the context stream around
+ * each instrumented launch (enable != 0 turns it on; off by default). */
+int wcs_profile(wcs_ctx* ctx, int enable);
+
+/* Sum the recorded launches by category (synchronises): out_host gets 7 x 4
+ * doubles {launches, total ms, algorithmic work, bytes} for the categories
+ * tensor-core contraction (work = useful real flops 2 M Nc K of the complex
+ * product), assembly (work = far point pairs), FFT circulant applies (bytes),
+ * FP64 GEMM, skeleton, factor, solve.  reset != 0 clears the records. */
+int wcs_profile_read(wcs_ctx* ctx, int reset, double* out_host);
 
 /* Host-only: product-integration weights of the near-field rule with q points
  * (3 * q * q doubles: coincident, next-neighbour, previous-neighbour pairs). */

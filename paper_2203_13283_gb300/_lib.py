@@ -19,7 +19,8 @@ OPS = {"C": 0, "CH": 1, "CC": 2, "CCH": 3, "CC_INV": 4, "S": 5, "D": 6, "DT": 7,
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("q_far", C.c_int), ("q_near", C.c_int),
                 ("near_band", C.c_int), ("block", C.c_int), ("max_refine", C.c_int),
-                ("refine_tol", C.c_double), ("rhs_chunk", C.c_int), ("reserved", C.c_int * 7)]
+                ("refine_tol", C.c_double), ("rhs_chunk", C.c_int), ("mixed_planes", C.c_int),
+                ("rhs_planes", C.c_int), ("zfast", C.c_double), ("reserved", C.c_int * 2)]
 
 
 class Info(C.Structure):
@@ -60,6 +61,9 @@ SIGNATURES = {
     "wcs_planewave_rhs": (I, [P, I64, P, P, P, I64]),
     "wcs_farfield": (I, [P, I64, P, I64, I, P, P, I64]),
     "wcs_gemm_split_bf16": (I, [I64, I64, I64, P, I64, P, I64, I, P, I64, P]),
+    "wcs_launch_count": (U64, []),
+    "wcs_profile": (I, [P, I]),
+    "wcs_profile_read": (I, [P, I, P]),
     "wcs_quadrature_tables": (I, [I, P]),
 }
 

@@ -15,6 +15,8 @@
 // (q_far); 2 <= d <= near_band tensor Gauss (q_near); d <= 1 the same q_near
 // grid with the log|s - s'| part of each kernel integrated by product
 // weights (split K = A log|s - s'| + B, A = -(1/2pi) J0 or -(kappa/2pi) J1 g).
+#include <cuda_bf16.h>
+
 #include "hankel.cuh"
 #include "internal.h"
 
@@ -168,13 +170,163 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
     for (int j = 0; j < 4; ++j) o.v[op][j] = h2 * o.v[op][j];
 }
 
+
+// ---------------------------------------------------------------------------
+// Far element pairs in the mixed form.  With element centres c_e, c_f and
+// point offsets o = r - c (|o| < h), R = |d0 + o_p - o_r| with d0 = c_e - c_f:
+// R0 = |d0| and the phase k R0 mod 2 pi are formed in FP64 once per pair;
+// R - R0 = (2 d0.(o_p - o_r) + |o_p - o_r|^2) / (R + R0) is small and
+// accurate in FP32, so the phase k R = (k R0 mod 2 pi) + k (R - R0) keeps
+// ~1e-7 absolute accuracy even for k R ~ 1e4.  The Hankel functions use the
+// large-argument expansion (DLMF 10.17.5) with eight terms (z >= 12 gives
+// < 1e-7), for k and for k~ = k + i beta (exp(i k~ R) = exp(i k R - beta R)).
+// ---------------------------------------------------------------------------
+__constant__ float c_a0[8], c_a1[8];   // a_k(0), a_k(1) of the Hankel expansion
+
+struct cf {
+  float x, y;
+};
+__device__ __forceinline__ cf cmul(cf a, cf b) { return {fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
+__device__ __forceinline__ cf cscale(cf a, float s) { return {a.x * s, a.y * s}; }
+
+struct PairOutF {
+  cf v[4][4];
+};
+
+__device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& out);
+
+__device__ void pair_fast(const AsmArgs& A, int64_t e, int64_t f, PairOut& out) {
+  PairOutF o;
+  pair_fast_f(A, e, f, o);
+#pragma unroll
+  for (int op = 0; op < 4; ++op)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out.v[op][j] = mkz((double)o.v[op][j].x, (double)o.v[op][j].y);
+}
+
+__device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& out) {
+  const int q = A.q_far;
+  const double dx0 = A.cx[e] - A.cx[f], dy0 = A.cy[e] - A.cy[f];
+  const double R0 = sqrt(dx0 * dx0 + dy0 * dy0);
+  const double kR0 = A.k * R0;
+  const double twopi_hi = 6.283185307179586, twopi_lo = 2.4492935982947064e-16;
+  const double nrev = rint(kR0 * (1.0 / twopi_hi));
+  const float ph0 = (float)fma(-nrev, twopi_lo, fma(-nrev, twopi_hi, kR0));
+  const float fdx0 = (float)dx0, fdy0 = (float)dy0, fR0 = (float)R0;
+  const float k = (float)A.k, beta = (float)A.kt.y;
+  // sqrt(2/(pi k~)) and i/k~ for the complex wavenumber
+  const zd ckd = zsqrt((2.0 / WCS_PI) * zrecip(A.kt));
+  const zd ikd = zrecip(A.kt);
+  const cf ck = {(float)ckd.x, (float)ckd.y};
+  const cf ik = {(float)(-ikd.y), (float)ikd.x};           // i / k~
+  const cf kt4 = {(float)(-0.25 * A.kt.y), (float)(0.25 * A.kt.x)};  // i k~ / 4
+  const float ampk = sqrtf((float)(2.0 / (WCS_PI * A.k)));
+  const float kk2h2 = (float)(A.k * A.k * A.h * A.h);
+  cf v[4][4];
+#pragma unroll
+  for (int op = 0; op < 4; ++op)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[op][j] = {0.f, 0.f};
+  for (int p = 0; p < q; ++p) {
+    const int64_t ip = e * q + p;
+    const float oxp = A.ox[ip], oyp = A.oy[ip], nxt = A.nxf[ip], nyt = A.nyf[ip];
+    const float xip = (float)c_xf[p], wp = (float)c_wf[p];
+    for (int r = 0; r < q; ++r) {
+      const int64_t ir = f * q + r;
+      const float dx = oxp - A.ox[ir], dy = oyp - A.oy[ir];
+      const float nxs = A.nxf[ir], nys = A.nyf[ir];
+      const float a = 2.f * (fdx0 * dx + fdy0 * dy) + dx * dx + dy * dy;
+      const float R = sqrtf(fR0 * fR0 + a);
+      const float dR = a / (fR0 + R);
+      const float iR = 1.f / R;
+      const float gg = ((fdx0 + dx) * nxs + (fdy0 + dy) * nys) * iR;
+      const float nd = nxt * nxs + nyt * nys;
+      float sn, cs;
+      sincosf(ph0 + k * dR - 0.78539816339744831f, &sn, &cs);   // e^{i(kR - pi/4)}
+      const cf E = {cs, sn};
+      // real wavenumber: P + iQ = sum (i t)^k a_k, t = 1/(kR)
+      const float t = iR / k, t2 = t * t;
+      float P0 = c_a0[6], Q0 = c_a0[7], P1 = c_a1[6], Q1 = c_a1[7];
+#pragma unroll
+      for (int m = 2; m >= 0; --m) {
+        P0 = fmaf(-t2, P0, c_a0[2 * m]);
+        Q0 = fmaf(-t2, Q0, c_a0[2 * m + 1]);
+        P1 = fmaf(-t2, P1, c_a1[2 * m]);
+        Q1 = fmaf(-t2, Q1, c_a1[2 * m + 1]);
+      }
+      Q0 *= t;
+      Q1 *= t;
+      const float amp = ampk * sqrtf(iR);
+      const cf AE = cscale(E, amp);
+      const cf H0 = cmul(AE, {P0, Q0});
+      const cf H1 = cmul(AE, {Q1, -P1});                        // e^{-i pi/2} (P1 + i Q1)
+      const cf gk = {-0.25f * H0.y, 0.25f * H0.x};               // (i/4) H0
+      const cf dgk = cscale({-0.25f * H1.y, 0.25f * H1.x}, k * gg);
+      // complex wavenumber: w = i/(k~ R)
+      const cf w = cscale(ik, iR);
+      cf s0 = {c_a0[7], 0.f}, s1 = {c_a1[7], 0.f};
+#pragma unroll
+      for (int m = 6; m >= 0; --m) {
+        s0 = cmul(s0, w); s0.x += c_a0[m];
+        s1 = cmul(s1, w); s1.x += c_a1[m];
+      }
+      const cf Et = cscale(cmul(E, ck), sqrtf(iR) * __expf(-beta * R));
+      const cf Ht0 = cmul(Et, s0);
+      const cf Ht1 = cmul(Et, {s1.y, -s1.x});
+      const cf gt = {-0.25f * Ht0.y, 0.25f * Ht0.x};
+      const cf dgt = cscale(cmul(kt4, Ht1), gg);
+      const float ph[2] = {1.f - xip, xip};
+      const float xir = (float)c_xf[r];
+      const float ps[2] = {1.f - xir, xir};
+      const float w2 = wp * (float)c_wf[r];
+#pragma unroll
+      for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb) {
+          const float c = w2 * ph[aa] * ps[bb];
+          const float cn = w2 * ((aa == bb) ? 1.f : -1.f) - kk2h2 * nd * c;
+          cf* o = &v[0][aa * 2 + bb];
+          v[0][aa * 2 + bb].x = fmaf(c, gt.x, v[0][aa * 2 + bb].x);
+          v[0][aa * 2 + bb].y = fmaf(c, gt.y, v[0][aa * 2 + bb].y);
+          v[1][aa * 2 + bb].x = fmaf(c, dgk.x, v[1][aa * 2 + bb].x);
+          v[1][aa * 2 + bb].y = fmaf(c, dgk.y, v[1][aa * 2 + bb].y);
+          v[2][aa * 2 + bb].x = fmaf(c, dgt.x, v[2][aa * 2 + bb].x);
+          v[2][aa * 2 + bb].y = fmaf(c, dgt.y, v[2][aa * 2 + bb].y);
+          v[3][aa * 2 + bb].x = fmaf(cn, gk.x, v[3][aa * 2 + bb].x);
+          v[3][aa * 2 + bb].y = fmaf(cn, gk.y, v[3][aa * 2 + bb].y);
+          (void)o;
+        }
+    }
+  }
+  const float h2 = (float)(A.h * A.h);
+#pragma unroll
+  for (int op = 0; op < 4; ++op)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out.v[op][j] = (op < 3) ? cscale(v[op][j], h2) : v[op][j];
+}
+
+__device__ __forceinline__ bool fast_ok(const AsmArgs& A, int64_t e, int64_t f) {
+  if (periodic_dist(e, f, A.N) <= A.near_band) return false;
+  const double dx0 = A.cx[e] - A.cx[f], dy0 = A.cy[e] - A.cy[f];
+  return A.k * sqrt(dx0 * dx0 + dy0 * dy0) >= A.zfast;
+}
+
+__device__ __forceinline__ void pair_any(const AsmArgs& A, int64_t e, int64_t f, PairOut& o) {
+  if (A.mixed && fast_ok(A, e, f)) { pair_fast(A, e, f, o); return; }
+  pair_integrals(A, e, f, o);
+}
+
+__device__ __forceinline__ void split_store(double x, int planes, uint16_t* const* P, int64_t off);
+
 constexpr int TILE = 32;
 constexpr int ASM_THREADS = 256;
 
+template <int MIXED>
 __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs A) {
   extern __shared__ zd acc[];  // [4][TILE][TILE]
   const int64_t N = A.N;
   const int64_t i0 = (int64_t)blockIdx.y * TILE, j0 = (int64_t)blockIdx.x * TILE;
+  if (MIXED && A.tile_flags && !A.tile_flags[(int64_t)blockIdx.y * gridDim.x + blockIdx.x]) return;
   for (int t = threadIdx.x; t < 4 * TILE * TILE; t += blockDim.x) acc[t] = mkz(0.0);
   __syncthreads();
   const int span = TILE + 1;
@@ -191,7 +343,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs A) {
     if (rowok && colok) {
       const int64_t e = ((i0 - 1 + el) % N + N) % N;
       const int64_t f = ((j0 - 1 + fl) % N + N) % N;
-      pair_integrals(A, e, f, o);
+      if (MIXED) pair_any(A, e, f, o); else pair_integrals(A, e, f, o);
     }
 #pragma unroll
     for (int ph = 0; ph < 4; ++ph) {
@@ -206,11 +358,38 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs A) {
       __syncthreads();
     }
   }
-  zd* outs[4] = {A.S, A.D, A.Dt, A.Nk};
-  for (int t = threadIdx.x; t < 4 * TILE * TILE; t += blockDim.x) {
-    const int op = t / (TILE * TILE), rem = t - op * TILE * TILE;
+  if constexpr (!MIXED) {
+    zd* outs[4] = {A.S, A.D, A.Dt, A.Nk};
+    for (int t = threadIdx.x; t < 4 * TILE * TILE; t += blockDim.x) {
+      const int op = t / (TILE * TILE), rem = t - op * TILE * TILE;
+      const int li = rem / TILE, lj = rem - (rem / TILE) * TILE;
+      if (i0 + li < N && j0 + lj < N) outs[op][(i0 + li) * A.ld + j0 + lj] = acc[t];
+    }
+  } else {
+  // planes: layout 0 row i0+li holds (re, im) of column j0+lj at 2(j0+lj);
+  // layout 1 (transpose) row j0+lj holds entry (i0+li, j0+lj) at 2(i0+li)
+  for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
+    const int comp = t & 1;
+    const int u = t >> 1;
+    const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
     const int li = rem / TILE, lj = rem - (rem / TILE) * TILE;
-    if (i0 + li < N && j0 + lj < N) outs[op][(i0 + li) * A.ld + j0 + lj] = acc[t];
+    if (i0 + li < N && j0 + lj < N) {
+      const zd v = acc[(op * TILE + li) * TILE + lj];
+      const double x = comp ? v.y : v.x;
+      split_store(x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
+    }
+  }
+  for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
+    const int comp = t & 1;
+    const int u = t >> 1;
+    const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
+    const int lj = rem / TILE, li = rem - (rem / TILE) * TILE;   // consecutive threads walk i
+    if (i0 + li < N && j0 + lj < N) {
+      const zd v = acc[(op * TILE + li) * TILE + lj];
+      const double x = comp ? v.y : v.x;
+      split_store(x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
+    }
+  }
   }
 }
 
@@ -268,18 +447,171 @@ static int upload_rules(const AsmArgs& A) {
 int assemble_dense(const AsmArgs& A, cudaStream_t s) {
   if (upload_rules(A)) { set_error("uploading quadrature rules failed"); return 3; }
   const size_t smem = sizeof(zd) * 4 * TILE * TILE;
-  cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k_assemble<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int64_t nt = (A.N + TILE - 1) / TILE;
   dim3 grid((unsigned)nt, (unsigned)nt);
-  k_assemble<<<grid, ASM_THREADS, smem, s>>>(A);
+  k_assemble<0><<<grid, ASM_THREADS, smem, s>>>(A);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("assemble: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+__device__ __forceinline__ void split_store(double x, int planes, uint16_t* const* P, int64_t off) {
+  __nv_bfloat16 h0 = __double2bfloat16(x);
+  double r = x - (double)__bfloat162float(h0);
+  P[0][off] = __bfloat16_as_ushort(h0);
+  if (planes > 1) {
+    __nv_bfloat16 h1 = __double2bfloat16(r);
+    r -= (double)__bfloat162float(h1);
+    P[1][off] = __bfloat16_as_ushort(h1);
+    if (planes > 2) P[2][off] = __bfloat16_as_ushort(__double2bfloat16(r));
+  }
+}
+
+static int upload_hankel_coefficients() {
+  float a0[8], a1[8];
+  double t0 = 1.0, t1 = 1.0;
+  a0[0] = 1.f;
+  a1[0] = 1.f;
+  for (int kk = 1; kk < 8; ++kk) {
+    const double o = 2.0 * kk - 1.0;
+    t0 *= (0.0 - o * o) / (8.0 * kk);
+    t1 *= (4.0 - o * o) / (8.0 * kk);
+    a0[kk] = (float)t0;
+    a1[kk] = (float)t1;
+  }
+  if (cudaMemcpyToSymbol(c_a0, a0, sizeof(a0)) != cudaSuccess) return 3;
+  if (cudaMemcpyToSymbol(c_a1, a1, sizeof(a1)) != cudaSuccess) return 3;
+  return 0;
+}
+
+// flag[t] = 1 when tile t holds an element pair outside the FP32 fast path
+__global__ void k_tile_flags(AsmArgs A, int64_t nt, uint8_t* flag) {
+  const int64_t t = blockIdx.x;
+  const int64_t ti = t / nt, tj = t - (t / nt) * nt;
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  const int span = TILE + 1;
+  for (int u = threadIdx.x; u < span * span; u += blockDim.x) {
+    const int el = u / span, fl = u - (u / span) * span;
+    const int64_t e = ((ti * TILE - 1 + el) % A.N + A.N) % A.N;
+    const int64_t f = ((tj * TILE - 1 + fl) % A.N + A.N) % A.N;
+    if (!fast_ok(A, e, f)) any = 1;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) flag[t] = (uint8_t)any;
+}
+
+// Tiles whose element pairs all take the FP32 path: FP32 accumulation in
+// shared memory, same four conflict-free phases, planes written directly.
+__global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_t nt, const uint8_t* flag) {
+  const int64_t ti = blockIdx.y, tj = blockIdx.x;
+  if (flag[ti * nt + tj]) return;
+  __shared__ cf acc[4 * TILE * TILE];
+  const int64_t N = A.N;
+  const int64_t i0 = ti * TILE, j0 = tj * TILE;
+  for (int t = threadIdx.x; t < 4 * TILE * TILE; t += blockDim.x) acc[t] = {0.f, 0.f};
+  __syncthreads();
+  const int span = TILE + 1;
+  const int npairs = span * span;
+  for (int base = 0; base < npairs; base += blockDim.x) {
+    const int idx = base + threadIdx.x;
+    const int el = idx / span, fl = idx - (idx / span) * span;
+    const bool valid = idx < npairs;
+    const bool rowok = valid && ((el >= 1 && i0 + el - 1 < N) || (el < TILE && i0 + el < N));
+    const bool colok = valid && ((fl >= 1 && j0 + fl - 1 < N) || (fl < TILE && j0 + fl < N));
+    PairOutF o;
+    if (rowok && colok) {
+      const int64_t e = ((i0 - 1 + el) % N + N) % N;
+      const int64_t f = ((j0 - 1 + fl) % N + N) % N;
+      pair_fast_f(A, e, f, o);
+    }
+#pragma unroll
+    for (int ph = 0; ph < 4; ++ph) {
+      const int a = ph >> 1, b = ph & 1;
+      if (rowok && colok) {
+        const int li = el - 1 + a, lj = fl - 1 + b;
+        if (li >= 0 && li < TILE && lj >= 0 && lj < TILE && i0 + li < N && j0 + lj < N) {
+#pragma unroll
+          for (int op = 0; op < 4; ++op) {
+            cf& d = acc[(op * TILE + li) * TILE + lj];
+            d.x += o.v[op][ph].x;
+            d.y += o.v[op][ph].y;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
+    const int comp = t & 1, u = t >> 1;
+    const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
+    const int li = rem / TILE, lj = rem - (rem / TILE) * TILE;
+    if (i0 + li < N && j0 + lj < N) {
+      const cf v = acc[(op * TILE + li) * TILE + lj];
+      split_store(comp ? v.y : v.x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
+    }
+  }
+  for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
+    const int comp = t & 1, u = t >> 1;
+    const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
+    const int lj = rem / TILE, li = rem - (rem / TILE) * TILE;
+    if (i0 + li < N && j0 + lj < N) {
+      const cf v = acc[(op * TILE + li) * TILE + lj];
+      split_store(comp ? v.y : v.x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
+    }
+  }
+}
+
+int assemble_planes(const AsmArgs& A, cudaStream_t s) {
+  if (upload_rules(A) || upload_hankel_coefficients()) { set_error("uploading quadrature rules failed"); return 3; }
+  const size_t smem = sizeof(zd) * 4 * TILE * TILE;
+  cudaFuncSetAttribute(k_assemble<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int64_t nt = (A.N + TILE - 1) / TILE;
+  uint8_t* flag = nullptr;
+  if (cudaMalloc(&flag, nt * nt) != cudaSuccess) { set_error("oom (tile flags)"); return 4; }
+  k_tile_flags<<<(unsigned)(nt * nt), 256, 0, s>>>(A, nt, flag);
+  note_launch();
+  dim3 grid((unsigned)nt, (unsigned)nt);
+  k_assemble_fast<<<grid, ASM_THREADS, 0, s>>>(A, nt, flag);
+  note_launch();
+  AsmArgs B = A;
+  B.tile_flags = flag;
+  k_assemble<1><<<grid, ASM_THREADS, smem, s>>>(B);
+  note_launch();
+  cudaStreamSynchronize(s);
+  cudaFree(flag);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("assemble (planes): ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+__global__ void k_far_offsets(Points far, const double* cx, const double* cy, int64_t N, int q, float* ox,
+                              float* oy, float* nxf, float* nyf) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N * q) return;
+  const int64_t e = t / q;
+  ox[t] = (float)(far.x[t] - cx[e]);
+  oy[t] = (float)(far.y[t] - cy[e]);
+  nxf[t] = (float)far.nx[t];
+  nyf[t] = (float)far.ny[t];
+}
+
+int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
+                float* oy, float* nxf, float* nyf, cudaStream_t s) {
+  k_far_offsets<<<(unsigned)((N * q + 255) / 256), 256, 0, s>>>(far, cx, cy, N, q, ox, oy, nxf, nyf);
+  note_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("far offsets: ") + cudaGetErrorString(err)); return 3; }
   return 0;
 }
 
 int assemble_circle_row(const AsmArgs& A, cudaStream_t s) {
   if (upload_rules(A)) { set_error("uploading quadrature rules failed"); return 3; }
   k_circle_row<<<(unsigned)((A.N + 63) / 64), 64, 0, s>>>(A);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("circle row: ") + cudaGetErrorString(err)); return 3; }
   return 0;
@@ -290,6 +622,7 @@ int assemble_entries(const AsmArgs& A, int64_t count, const int64_t* rows, const
   if (count <= 0) return 0;
   if (upload_rules(A)) { set_error("uploading quadrature rules failed"); return 3; }
   k_entries<<<(unsigned)((count + 63) / 64), 64, 0, s>>>(A, count, rows, cols, out4);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("entries: ") + cudaGetErrorString(err)); return 3; }
   return 0;

@@ -68,6 +68,9 @@ __host__ __device__ __forceinline__ void zfmas(zd& acc, double s, zd b) {
 #include <string>
 namespace wcs {
 void set_error(const std::string& msg);
+// host-side count of kernel launches issued by the library
+extern unsigned long long g_launches;
+inline void note_launch() { ++g_launches; }
 }
 #define WCS_CUDA_TRY(expr)                                                        \
   do {                                                                            \

@@ -188,6 +188,7 @@ static int launch_tile(const zd* in, int64_t in_es, int64_t in_ss, int64_t in_cs
     k_fft_tile<<<grid, threads, smem, s>>>(in + c0 * in_cs, in_es, in_ss, in_cs, out + c0 * out_cs,
                                            out_es, out_ss, out_cs, (int)L, ilog2(L), nseq,
                                            nseq_total, tw, Ltw, sign, twn, npost);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("fft: ") + cudaGetErrorString(err)); return 3; }
@@ -233,6 +234,7 @@ int fft_plan_create(FFTPlan& p, int64_t n, cudaStream_t s) {
   }
   if (cudaMalloc(&p.twiddle, sizeof(zd) * len) != cudaSuccess) { set_error("oom (fft)"); return 4; }
   k_twiddles<<<(unsigned)((len + 255) / 256), 256, 0, s>>>(p.twiddle, len);
+  note_launch();
   p.work_cols = std::max<int64_t>(1, std::min<int64_t>(256, (int64_t(1) << 27) / len));
   if (cudaMalloc(&p.work, sizeof(zd) * len * p.work_cols * (p.pow2 ? 1 : 2)) != cudaSuccess) {
     set_error("oom (fft work)");
@@ -246,7 +248,9 @@ int fft_plan_create(FFTPlan& p, int64_t n, cudaStream_t s) {
       return 4;
     }
     k_chirp<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p.chirp, n);
+    note_launch();
     k_bluestein_filter<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(p.chirp, n, m, p.chirp_hat);
+    note_launch();
     Pow2 P{m, p.twiddle, p.work + m * p.work_cols, p.work_cols};
     int r = pow2_transform(P, p.chirp_hat, m, 1, -1, s);
     if (r) return r;
@@ -277,13 +281,16 @@ int fft_columns(FFTPlan& p, zd* x, int64_t ld, int64_t cols, int sign, cudaStrea
     int64_t cc = std::min(p.work_cols, cols - c0);
     dim3 gm((unsigned)((m + 255) / 256), (unsigned)cc), gn((unsigned)((n + 255) / 256), (unsigned)cc);
     k_bluestein_pre<<<gm, 256, 0, s>>>(x + c0 * ld, ld, n, m, p.chirp, sign, work);
+    note_launch();
     Pow2 P{m, p.twiddle, scratch, p.work_cols};
     int r = pow2_transform(P, work, m, cc, -1, s);
     if (r) return r;
     k_pointwise<<<gm, 256, 0, s>>>(work, m, p.chirp_hat, 0);
+    note_launch();
     r = pow2_transform(P, work, m, cc, +1, s);
     if (r) return r;
     k_bluestein_post<<<gn, 256, 0, s>>>(work, n, m, p.chirp, sign, x + c0 * ld, ld);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
@@ -296,6 +303,7 @@ int scale_columns(zd* x, int64_t n, int64_t ld, int64_t cols, const zd* mu, bool
     int64_t cc = std::min<int64_t>(65535, cols - c0);
     dim3 g((unsigned)((n + 255) / 256), (unsigned)cc);
     k_scale_columns<<<g, 256, 0, s>>>(x + c0 * ld, n, ld, mu, divide, conj_mu, extra);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }

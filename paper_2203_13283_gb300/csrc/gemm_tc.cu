@@ -290,6 +290,7 @@ static int launch_tc(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaS
   }
   dim3 grid((unsigned)((args.Nc + NT - 1) / NT), (unsigned)((args.M + TC_BM - 1) / TC_BM));
   kern<<<grid, TC_THREADS, L::TOTAL, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], args);
+  note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error(std::string("gemm_tc launch: ") + cudaGetErrorString(e)); return 3; }
   return 0;

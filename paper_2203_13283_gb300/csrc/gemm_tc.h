@@ -99,4 +99,9 @@ int split_complex_rows(const zd* X, int64_t rows, int64_t cols, int64_t ld, int 
 int stage_rhs(const zd* X, int64_t n, int64_t B, int64_t ldx, int conj_in, int planes, uint16_t* const* P,
               int64_t ldp, cudaStream_t s);
 
+// Stage a strided complex matrix view (element (i, j) at X[i*rs + j*cs],
+// optionally conjugated) as real rows x 2cols bf16 planes (K-major A operand).
+int stage_view(const zd* X, int64_t rows, int64_t cols, int64_t rs, int64_t cs, int conj, int planes,
+               uint16_t* const* P, int64_t ldp, cudaStream_t s);
+
 }  // namespace wcs

@@ -193,7 +193,9 @@ int arc_table_build(const Contour& c, ArcTable& t, cudaStream_t s) {
     return 4;
   }
   k_panel_lengths<<<(t.P + 127) / 128, 128, 0, s>>>(c, t.P, len);
+  note_launch();
   k_prefix_kahan<<<1, 32, 0, s>>>(len, t.P, t.cum);
+  note_launch();
   double L = 0.0;
   cudaMemcpyAsync(&L, t.cum + t.P, sizeof(double), cudaMemcpyDeviceToHost, s);
   cudaError_t err = cudaStreamSynchronize(s);
@@ -207,6 +209,7 @@ int points_build(const Contour& c, const ArcTable& t, int64_t N, double h, const
                  int nq, Points& out, cudaStream_t s) {
   int64_t n = N * nq;
   k_points<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(c, t.cum, t.P, t.L, N, h, xi_dev, nq, out);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
   return 0;
@@ -218,6 +221,7 @@ int min_curvature(const Contour& c, const ArcTable& t, int64_t samples, double* 
   double* d = nullptr;
   if (cudaMalloc(&d, sizeof(double) * blocks) != cudaSuccess) { set_error("oom"); return 4; }
   k_min_curv<<<blocks, 256, 0, s>>>(c, t.cum, t.P, t.L, samples, d);
+  note_launch();
   double h[blocks];
   cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
   cudaError_t err = cudaStreamSynchronize(s);

@@ -64,8 +64,26 @@ struct AsmArgs {
   const double* wlog;              // 3 * q_near^2 product weights (device)
   zd *S, *D, *Dt, *Nk;             // outputs
   int64_t ld;                      // row-major leading dimension
+  // mixed-precision form: far pairs with k R >= zfast are integrated in FP32
+  // around the FP64 element-centre distance; output written as split-bf16
+  // planes [op][layout][plane] (layout 0: X, layout 1: X^T; each row-major
+  // complex as real N x 2N, leading dimension ldp).
+  int mixed = 0;
+  int planes = 0;
+  uint16_t* P[4][2][3];
+  int64_t ldp = 0;
+  const double *cx = nullptr, *cy = nullptr;     // element centres (xi = 1/2)
+  const float *ox = nullptr, *oy = nullptr;      // far points minus their element centre
+  const float *nxf = nullptr, *nyf = nullptr;    // far-point normals (FP32)
+  double zfast = 1e300;
+  const uint8_t* tile_flags = nullptr;           // mixed tile kernel: only flagged tiles
 };
 int assemble_dense(const AsmArgs& a, cudaStream_t s);
+// Mixed form: the same operators written as split-bf16 planes (see AsmArgs).
+int assemble_planes(const AsmArgs& a, cudaStream_t s);
+// FP32 offset tables of the far points relative to element centres.
+int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
+                float* oy, float* nxf, float* nyf, cudaStream_t s);
 // First row of the four circulant operators on the circle (row 0, N entries each).
 int assemble_circle_row(const AsmArgs& a, cudaStream_t s);
 // Sampled entries (row, col) of the four operators, computed point-wise.

@@ -84,6 +84,7 @@ int zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A, ZView B, zd beta, 
   dim3 grid((unsigned)((n + GB_N - 1) / GB_N), (unsigned)((m + GB_M - 1) / GB_M));
   if (grid.y > 65535) { set_error("zgemm: m too large"); return 1; }
   k_zgemm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, B, beta, C, ldc);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("zgemm: ") + cudaGetErrorString(err)); return 3; }
   return 0;
@@ -152,7 +153,9 @@ int gram_inverse(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_
   const int64_t tasks = ((n + GI_CH - 1) / GI_CH) * cols;
   const unsigned blocks = (unsigned)((tasks + 127) / 128);
   k_gram_fwd<<<blocks, 128, 0, s>>>(X, ldx, g_gram_work, n, cols, rho);
+  note_launch();
   k_gram_bwd<<<blocks, 128, 0, s>>>(g_gram_work, Y, ldy, n, cols, rho, -rho * 6.0 / h);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("gram: ") + cudaGetErrorString(err)); return 3; }
   return 0;
@@ -178,6 +181,7 @@ int gram_apply(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t 
     dim3 g((unsigned)((n + 255) / 256), (unsigned)cc);
     k_gram_apply<<<g, 256, 0, s>>>(X + c0 * ldx, ldx, Y + c0 * ldy, ldy, n, alpha * h / 6.0,
                                    alpha * 4.0 * h / 6.0, beta);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("gram_apply: ") + cudaGetErrorString(err)); return 3; }
@@ -202,6 +206,7 @@ __global__ void k_colnorm(const zd* X, int64_t ld, int64_t m, double* out) {
 int column_norms(const zd* X, int64_t ld, int64_t m, int64_t n, double* out, cudaStream_t s) {
   if (n <= 0) return 0;
   k_colnorm<<<(unsigned)n, 256, 0, s>>>(X, ld, m, out);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
   return 0;
@@ -246,6 +251,7 @@ int gaussian_fill(zd* X, int64_t ld, int64_t m, int64_t n, uint64_t seed, uint64
   const int64_t tot = m * n;
   if (tot <= 0) return 0;
   k_gauss<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(X, ld, m, n, seed, offset);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
   return 0;
@@ -266,6 +272,7 @@ int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int
     int64_t cc = std::min<int64_t>(65535, n - c0);
     dim3 g((unsigned)((m + 255) / 256), (unsigned)cc);
     k_axpby<<<g, 256, 0, s>>>(m, a, X + c0 * ldx, ldx, b, Y + c0 * ldy, ldy);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
@@ -333,6 +340,7 @@ __global__ void k_pchol(zd* Gm, int b, double rel_tol, int* perm, int* rank_out)
 
 int pivoted_cholesky(zd* Gm, int b, double rel_tol, int* perm, int* rank_dev, cudaStream_t s) {
   k_pchol<<<1, 512, 0, s>>>(Gm, b, rel_tol, perm, rank_dev);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
   return 0;
@@ -365,6 +373,7 @@ int trsm_right_upper(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, co
   const size_t smem = sizeof(zd) * rank_host * rank_host;
   cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
   k_trsm_rows<<<(unsigned)((m + 127) / 128), 128, smem, s>>>(X, ldx, m, R, b, perm, rank_dev, Y, ldy);
+  note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("trsm: ") + cudaGetErrorString(err)); return 3; }
   return 0;
@@ -436,15 +445,18 @@ int lu_inverse(zd* A, int64_t n, zd* Ainv, int* piv, int* info_dev, double* minp
   cudaMemcpy2DAsync(M, sizeof(zd) * n, A, sizeof(zd) * n, sizeof(zd) * n, n, cudaMemcpyDeviceToDevice, s);
   cudaMemsetAsync(M + n * n, 0, sizeof(zd) * n * n, s);
   k_identity<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M + n * n, n);
+  note_launch();
   const double big = 1e300;
   cudaMemcpyAsync(minpiv_dev, &big, sizeof(double), cudaMemcpyHostToDevice, s);
   cudaMemsetAsync(info_dev, 0, sizeof(int), s);
   for (int64_t j = 0; j < n; ++j) {
     k_gj_pivot<<<1, 512, 0, s>>>(M, n, j, colj, rowj, info_dev, minpiv_dev);
+    note_launch();
     const int64_t ncols = 2 * n - j;
     for (int64_t c0 = 0; c0 < ncols; c0 += 65535) {
       dim3 g((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(65535, ncols - c0));
       k_gj_update<<<g, 256, 0, s>>>(M, n, j, j + c0, colj, rowj);
+      note_launch();
     }
   }
   cudaMemcpy2DAsync(Ainv, sizeof(zd) * n, M + n * n, sizeof(zd) * n, sizeof(zd) * n, n,

@@ -36,6 +36,7 @@ int split_real_f64(const double* X, int64_t rows, int64_t cols, int64_t ld, int 
     dim3 g((unsigned)((cols + 255) / 256), (unsigned)rr);
     k_split_real<<<g, 256, 0, s>>>(X + r0 * ld, rr, cols, ld, planes, P[0] + r0 * ldp,
                                    planes > 1 ? P[1] + r0 * ldp : nullptr, planes > 2 ? P[2] + r0 * ldp : nullptr, ldp);
+    note_launch();
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error(std::string("split: ") + cudaGetErrorString(e)); return 3; }
@@ -72,9 +73,38 @@ int stage_rhs(const zd* X, int64_t n, int64_t B, int64_t ldx, int conj_in, int p
     k_stage_rhs<<<g, 256, 0, s>>>(X + b0 * ldx, n, bb, ldx, conj_in, planes, P[0] + 2 * b0 * ldp,
                                   planes > 1 ? P[1] + 2 * b0 * ldp : nullptr,
                                   planes > 2 ? P[2] + 2 * b0 * ldp : nullptr, ldp);
+    note_launch();
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error(std::string("stage_rhs: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
+}
+
+__global__ void k_stage_view(const zd* X, int64_t rows, int64_t cols, int64_t rs, int64_t cs, int conj,
+                             int planes, uint16_t* p0, uint16_t* p1, uint16_t* p2, int64_t ldp) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = blockIdx.y;
+  if (j >= cols) return;
+  zd x = X[i * rs + j * cs];
+  if (conj) x.y = -x.y;
+  const int64_t o = i * ldp + 2 * j;
+  uint16_t d1, d2;
+  split3(x.x, planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
+  split3(x.y, planes, p0 + o + 1, planes > 1 ? p1 + o + 1 : &d1, planes > 2 ? p2 + o + 1 : &d2);
+}
+
+int stage_view(const zd* X, int64_t rows, int64_t cols, int64_t rs, int64_t cs, int conj, int planes,
+               uint16_t* const* P, int64_t ldp, cudaStream_t s) {
+  for (int64_t r0 = 0; r0 < rows; r0 += 65535) {
+    const int64_t rr = std::min<int64_t>(65535, rows - r0);
+    dim3 g((unsigned)((cols + 255) / 256), (unsigned)rr);
+    k_stage_view<<<g, 256, 0, s>>>(X + r0 * rs, rr, cols, rs, cs, conj, planes, P[0] + r0 * ldp,
+                                   planes > 1 ? P[1] + r0 * ldp : nullptr, planes > 2 ? P[2] + r0 * ldp : nullptr,
+                                   ldp);
+    note_launch();
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("stage_view: ") + cudaGetErrorString(e)); return 3; }
   return 0;
 }
 

@@ -78,6 +78,7 @@ int planewave_rhs(const Points& near, const double* wn, const double* xn, int q,
     dim3 g((unsigned)((N + 127) / 128), (unsigned)bb);
     k_planewave<<<g, 128, 0, s>>>(near, q, N, h, k, angles + b0, bb, e + (int64_t)b0 * ld,
                                   hv + (int64_t)b0 * ld, ld);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("rhs: ") + cudaGetErrorString(err)); return 3; }
@@ -92,6 +93,7 @@ int farfield_matrix(const Points& near, const double* wn, const double* xn, int 
     int oo = std::min(65535, nphi - o0);
     dim3 g((unsigned)((N + 127) / 128), (unsigned)oo);
     k_farfield_matrix<<<g, 128, 0, s>>>(near, q, N, h, k, phi + o0, oo, E + o0, lde);
+    note_launch();
   }
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("farfield: ") + cudaGetErrorString(err)); return 3; }

@@ -16,6 +16,7 @@
 #include "gemm_tc.h"
 
 namespace wcs {
+unsigned long long g_launches = 0;
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 }  // namespace wcs
@@ -64,7 +65,47 @@ struct wcs_ctx {
   DevBuf U, Vw, Wt;                       // N x rank each
   DevBuf w1, w2, w3, w4, w5;              // N x chunk scratch
   DevBuf small;                           // small scratch
+  // mixed-precision form
+  bool mixed = false;
+  int planes = 2, rhs_planes = 2;
+  int64_t ldp = 0;                        // plane leading dimension (bf16 elements)
+  DevBuf opplanes;                        // [op][layout][plane] N x ldp bf16
+  DevBuf centres, offs;                   // element centres (FP64), far offsets (FP32)
+  DevBuf stage0, stage1, stage2;          // staged right-hand blocks (bf16 planes)
+  int64_t stage_cols = 0;
+  DevBuf tcerr;
+  DevBuf gA, gB;                          // staging for general complex tensor products
+  // optional per-kernel timing: CUDA events on the context stream
+  bool profile = false;
+  struct Rec { int cat; cudaEvent_t a, b; double flops, bytes; };
+  std::vector<Rec> recs;
 };
+
+enum StatCat { CAT_GEMM_TC = 0, CAT_ASSEMBLY = 1, CAT_FFT = 2, CAT_ZGEMM = 3, CAT_SKELETON = 4,
+               CAT_FACTOR = 5, CAT_SOLVE = 6, CAT_COUNT = 7 };
+
+struct ProfScope {
+  wcs_ctx* c;
+  int cat;
+  double flops, bytes;
+  cudaEvent_t a = nullptr, b = nullptr;
+  ProfScope(wcs_ctx* c_, int cat_, double f, double by) : c(c_), cat(cat_), flops(f), bytes(by) {
+    if (!c->profile) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, c->s);
+  }
+  ~ProfScope() {
+    if (!c->profile) return;
+    cudaEventRecord(b, c->s);
+    c->recs.push_back({cat, a, b, flops, bytes});
+  }
+};
+
+static uint16_t* plane_ptr(wcs_ctx* c, int op, int layout, int plane) {
+  const int64_t per = c->N * c->ldp;
+  return (uint16_t*)c->opplanes.p + (((int64_t)op * 2 + layout) * c->planes + plane) * per;
+}
 
 static zd* mu_ptr(wcs_ctx* c, int which) { return c->mu.z() + (int64_t)which * c->N; }
 enum { MU_G = 0, MU_S = 1, MU_D = 2, MU_DT = 3, MU_N = 4, MU_C = 5 };
@@ -93,8 +134,136 @@ static int ensure_work(wcs_ctx* c, int64_t cols) {
   return 0;
 }
 
+static int ensure_stage(wcs_ctx* c, int64_t cols) {
+  if (cols <= c->stage_cols) return 0;
+  const size_t b = sizeof(uint16_t) * (size_t)(2 * cols) * c->ldp * c->rhs_planes;
+  TRY(c->stage0.ensure(b));
+  TRY(c->stage1.ensure(b));
+  TRY(c->stage2.ensure(b));
+  TRY(c->tcerr.ensure(sizeof(int)));
+  cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), c->s);
+  c->stage_cols = cols;
+  return 0;
+}
+
+static int stage(wcs_ctx* c, DevBuf& buf, const zd* X, int64_t ldx, int64_t cols, int conj) {
+  uint16_t* P[3];
+  const int64_t per = 2 * c->stage_cols * c->ldp;
+  for (int p = 0; p < 3; ++p) P[p] = (uint16_t*)buf.p + p * per;
+  return stage_rhs(X, c->N, cols, ldx, conj, c->rhs_planes, P, c->ldp, c->s);
+}
+
+// Y = alpha * op(X) + beta * Y on the tensor cores, op one of the assembled
+// operators (0 S~, 1 D, 2 D~, 3 N), X already staged in `buf`.  adjoint uses
+// the transposed planes: A^H x = conj(A^T conj(x)) (buf staged with conj).
+static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols, zd alpha, zd beta, zd* Y,
+                    int64_t ldy) {
+  TcOperand A, B;
+  A.planes = c->planes;
+  A.ld = c->ldp;
+  for (int p = 0; p < c->planes; ++p) A.plane[p] = plane_ptr(c, op, adjoint ? 1 : 0, p);
+  B.planes = c->rhs_planes;
+  B.ld = c->ldp;
+  const int64_t per = 2 * c->stage_cols * c->ldp;
+  for (int p = 0; p < c->rhs_planes; ++p) B.plane[p] = (uint16_t*)buf.p + p * per;
+  TcArgs t;
+  t.M = (int)c->N;
+  t.Nc = (int)(2 * cols);
+  t.K = (int)(2 * c->N);
+  tc_products(std::min(c->planes, c->rhs_planes), t);
+  t.epi = EPI_CPLX_F64;
+  t.conj_out = adjoint ? 1 : 0;
+  t.out = Y;
+  t.ldo = ldy;
+  t.alpha = alpha;
+  t.beta = beta;
+  t.err = (int*)c->tcerr.p;
+  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  return gemm_tc(A, B, t, c->s);
+}
+
+static int check_tc(wcs_ctx* c) {
+  int e = 0;
+  cudaMemcpyAsync(&e, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+  cudaError_t r = cudaStreamSynchronize(c->s);
+  if (r != cudaSuccess) { set_error(std::string("device: ") + cudaGetErrorString(r)); return WCS_ERR_CUDA; }
+  if (e) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
+  return 0;
+}
+
+// C (m x n, column-major ldc) = alpha * A (m x k view) * X (k x n, column-major) + beta * C.
+// Mixed form: on the tensor cores through staged split-bf16 planes; FP64 form: zgemm.
+static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A, const zd* X, int64_t ldx,
+                 zd beta, zd* C, int64_t ldc) {
+  if (m <= 0 || n <= 0) return 0;
+  if (!c->mixed || k < 64) return zgemm(m, n, k, alpha, A, blk(X, ldx), beta, C, ldc, c->s);
+  const int P = c->rhs_planes;
+  const int64_t ldk = ((2 * k + 63) / 64) * 64;
+  // grow the staging buffers geometrically: the skeleton calls this with a
+  // basis that widens block by block
+  const size_t needA = sizeof(uint16_t) * (size_t)m * ldk * P, needB = sizeof(uint16_t) * (size_t)(2 * n) * ldk * P;
+  if (needA > c->gA.bytes) TRY(c->gA.ensure(std::max(needA, c->gA.bytes + c->gA.bytes / 2)));
+  if (needB > c->gB.bytes) TRY(c->gB.ensure(std::max(needB, c->gB.bytes + c->gB.bytes / 2)));
+  TRY(c->tcerr.ensure(sizeof(int)));
+  uint16_t *pa[3], *pb[3];
+  for (int p = 0; p < 3; ++p) {
+    pa[p] = (uint16_t*)c->gA.p + (int64_t)p * m * ldk;
+    pb[p] = (uint16_t*)c->gB.p + (int64_t)p * 2 * n * ldk;
+  }
+  if (ldk != 2 * k) {   // zero the padding of the K dimension
+    cudaMemsetAsync(c->gA.p, 0, sizeof(uint16_t) * (size_t)m * ldk * P, c->s);
+    cudaMemsetAsync(c->gB.p, 0, sizeof(uint16_t) * (size_t)(2 * n) * ldk * P, c->s);
+  }
+  TRY(stage_view(A.p, m, k, A.rs, A.cs, A.conj ? 1 : 0, P, pa, ldk, c->s));
+  TRY(stage_rhs(X, k, n, ldx, 0, P, pb, ldk, c->s));
+  TcOperand oa, ob;
+  oa.planes = ob.planes = P;
+  oa.ld = ob.ld = ldk;
+  for (int p = 0; p < P; ++p) { oa.plane[p] = pa[p]; ob.plane[p] = pb[p]; }
+  TcArgs t;
+  t.M = (int)m; t.Nc = (int)(2 * n); t.K = (int)(2 * k);
+  tc_products(P, t);
+  t.epi = EPI_CPLX_F64;
+  t.out = C; t.ldo = ldc; t.alpha = alpha; t.beta = beta;
+  t.err = (int*)c->tcerr.p;
+  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  return gemm_tc(oa, ob, t, c->s);
+}
+
+static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj) {
+  const int64_t N = c->N;
+  zd* T1 = c->w1.z();
+  zd* T2 = c->w2.z();
+  const zd one = mkz(1.0), zero = mkz(0.0), mone = mkz(-1.0);
+  TRY(ensure_stage(c, cols));
+  const int cj = adj ? 1 : 0;
+  TRY(stage(c, c->stage0, X, ldx, cols, cj));
+  if (!adj) {
+    TRY(tc_apply(c, 1, false, c->stage0, cols, mone, zero, T1, N));   // -D X
+    TRY(tc_apply(c, 3, false, c->stage0, cols, one, zero, T2, N));    // N X
+  } else {
+    TRY(tc_apply(c, 2, true, c->stage0, cols, one, zero, T1, N));     // D~^H X
+    TRY(tc_apply(c, 0, true, c->stage0, cols, one, zero, T2, N));     // S~^H X
+  }
+  TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
+  TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
+  TRY(gram_inverse(T2, N, T2, N, N, cols, c->h, c->s));
+  TRY(stage(c, c->stage1, T1, N, cols, cj));
+  TRY(stage(c, c->stage2, T2, N, cols, cj));
+  if (!adj) {
+    TRY(tc_apply(c, 2, false, c->stage1, cols, one, zero, Y, ldy));   // D~ T1
+    TRY(tc_apply(c, 0, false, c->stage2, cols, one, one, Y, ldy));    // + S~ T2
+  } else {
+    TRY(tc_apply(c, 1, true, c->stage1, cols, mone, zero, Y, ldy));   // -D^H T1
+    TRY(tc_apply(c, 3, true, c->stage2, cols, one, one, Y, ldy));     // + N^H T2
+  }
+  TRY(gram_apply(T1, N, Y, ldy, N, cols, c->h, 0.5, 1.0, c->s));
+  return 0;
+}
+
 // Y = C X (adjoint: C^H X); uses w1, w2 as temporaries.  Y must not alias X.
 static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj) {
+  if (c->mixed) return apply_C_mixed(c, X, ldx, Y, ldy, cols, adj);
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -132,6 +301,7 @@ static int apply_Cc(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, in
                                       cudaMemcpyDeviceToDevice, c->s);
     if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return WCS_ERR_CUDA; }
   }
+  ProfScope ps(c, CAT_FFT, 0.0, 4.0 * 16.0 * (double)N * cols);
   TRY(fft_columns(c->fft, Y, ldy, cols, -1, c->s));
   TRY(scale_columns(Y, N, ldy, cols, mu_ptr(c, MU_C), mode == 2, mode == 1, 1.0 / (double)N, c->s));
   TRY(fft_columns(c->fft, Y, ldy, cols, +1, c->s));
@@ -157,8 +327,8 @@ static int woodbury(wcs_ctx* c, const zd* B, int64_t ldb, zd* X, int64_t ldx, in
   TRY(c->small.ensure(sizeof(zd) * r * cols));
   zd* Z = c->small.z();
   // Z = V^T Y = Vw^H Y ; X = Y - Wt Z
-  TRY(zgemm(r, cols, N, mkz(1.0), blkH(c->Vw.z(), N), blk(X, ldx), mkz(0.0), Z, r, c->s));
-  TRY(zgemm(N, cols, r, mkz(-1.0), blk(c->Wt.z(), N), blk(Z, r), mkz(1.0), X, ldx, c->s));
+  TRY(cgemm(c, r, cols, N, mkz(1.0), blkH(c->Vw.z(), N), X, ldx, mkz(0.0), Z, r));
+  TRY(cgemm(c, N, cols, r, mkz(-1.0), blk(c->Wt.z(), N), Z, r, mkz(1.0), X, ldx));
   return 0;
 }
 
@@ -225,13 +395,16 @@ int wcs_default_options(wcs_options* o) {
   if (!o) { set_error("null options"); return WCS_ERR_ARG; }
   std::memset(o, 0, sizeof(*o));
   o->precision = WCS_PREC_FP64;
-  o->q_far = 6;
+  o->q_far = 0;   // automatic: 6 (FP64 form) or 4 (mixed form)
   o->q_near = 12;
   o->near_band = 4;
   o->block = 32;
   o->max_refine = 12;
   o->refine_tol = 1e-12;
   o->rhs_chunk = 256;
+  o->mixed_planes = 2;
+  o->rhs_planes = 2;
+  o->zfast = 14.0;
   return WCS_OK;
 }
 
@@ -239,7 +412,12 @@ int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream) {
   if (!out) { set_error("null output pointer"); return WCS_ERR_ARG; }
   wcs_options o;
   if (opt) o = *opt; else wcs_default_options(&o);
-  if (o.precision != WCS_PREC_FP64) { set_error("only the FP64 precision mode is built"); return WCS_ERR_UNSUPPORTED; }
+  if (o.precision != WCS_PREC_FP64 && o.precision != WCS_PREC_MIXED) { set_error("unknown precision mode"); return WCS_ERR_ARG; }
+  if (o.precision == WCS_PREC_MIXED && (o.mixed_planes < 1 || o.mixed_planes > 3 || o.rhs_planes != o.mixed_planes)) {
+    set_error("mixed form: 1 <= mixed_planes <= 3 and rhs_planes == mixed_planes");
+    return WCS_ERR_ARG;
+  }
+  if (o.q_far == 0) o.q_far = (o.precision == WCS_PREC_MIXED) ? 4 : 6;
   if (o.q_far < 2 || o.q_far > 16 || o.q_near < 4 || o.q_near > 16 || o.near_band < 1 ||
       o.block < 1 || o.block > 64 || o.rhs_chunk < 1 || o.max_refine < 0) {
     set_error("option out of range");
@@ -248,6 +426,9 @@ int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream) {
   wcs_ctx* c = new wcs_ctx();
   c->opt = o;
   c->s = (cudaStream_t)stream;
+  c->mixed = (o.precision == WCS_PREC_MIXED);
+  c->planes = o.mixed_planes;
+  c->rhs_planes = o.rhs_planes;
   c->quad.q_far = o.q_far;
   c->quad.q_near = o.q_near;
   c->quad.near_band = o.near_band;
@@ -261,6 +442,9 @@ static void free_mesh(wcs_ctx* c) {
   cudaFree(c->arc_c.cum); c->arc_c.cum = nullptr;
   c->pts_far.release(); c->pts_near.release(); c->pts_far_c.release(); c->pts_near_c.release();
   c->ops.release(); c->mu.release();
+  c->opplanes.release(); c->centres.release(); c->offs.release();
+  c->stage0.release(); c->stage1.release(); c->stage2.release(); c->stage_cols = 0;
+  c->gA.release(); c->gB.release();
   c->U.release(); c->Vw.release(); c->Wt.release();
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
   c->rank = -1;
@@ -431,11 +615,42 @@ int wcs_assemble(wcs_ctx* c) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
   if (c->stage < ST_MESH) { set_error("mesh first"); return WCS_ERR_STATE; }
   const int64_t N = c->N, ld = c->ld;
-  TRY(c->ops.ensure(sizeof(zd) * 4 * N * ld));
-  c->S = c->ops.z(); c->D = c->S + N * ld; c->Dt = c->D + N * ld; c->Nk = c->Dt + N * ld;
-  AsmArgs A = asm_args(c, false);
-  A.S = c->S; A.D = c->D; A.Dt = c->Dt; A.Nk = c->Nk;
-  TRY(assemble_dense(A, c->s));
+  if (!c->mixed) {
+    TRY(c->ops.ensure(sizeof(zd) * 4 * N * ld));
+    c->S = c->ops.z(); c->D = c->S + N * ld; c->Dt = c->D + N * ld; c->Nk = c->Dt + N * ld;
+    AsmArgs A = asm_args(c, false);
+    A.S = c->S; A.D = c->D; A.Dt = c->Dt; A.Nk = c->Nk;
+    ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * c->opt.q_far * c->opt.q_far, 0.0);
+    TRY(assemble_dense(A, c->s));
+  } else {
+    c->ldp = ((2 * N + 63) / 64) * 64;
+    TRY(c->opplanes.ensure(sizeof(uint16_t) * (size_t)8 * c->planes * N * c->ldp));
+    cudaMemsetAsync(c->opplanes.p, 0, c->opplanes.bytes, c->s);   // zero the padding columns
+    // element centres (xi = 1/2) and FP32 offsets of the far points
+    const int qf = c->opt.q_far;
+    TRY(c->centres.ensure(sizeof(double) * 6 * N));
+    double* half = c->centres.d() + 5 * N;
+    const double hv = 0.5;
+    cudaMemcpyAsync(half, &hv, sizeof(double), cudaMemcpyHostToDevice, c->s);
+    Points cp;
+    cp.x = c->centres.d(); cp.y = cp.x + N; cp.nx = cp.y + N; cp.ny = cp.nx + N; cp.kappa = nullptr; cp.n = N;
+    TRY(points_build(c->contour, c->arc, N, c->h, half, 1, cp, c->s));
+    TRY(c->offs.ensure(sizeof(float) * 4 * N * qf));
+    float* of = (float*)c->offs.p;
+    TRY(far_offsets(c->far, cp.x, cp.y, N, qf, of, of + N * qf, of + 2 * N * qf, of + 3 * N * qf, c->s));
+    AsmArgs A = asm_args(c, false);
+    A.mixed = 1;
+    A.planes = c->planes;
+    A.ldp = c->ldp;
+    for (int op = 0; op < 4; ++op)
+      for (int l = 0; l < 2; ++l)
+        for (int p = 0; p < 3; ++p) A.P[op][l][p] = (p < c->planes) ? plane_ptr(c, op, l, p) : nullptr;
+    A.cx = cp.x; A.cy = cp.y;
+    A.ox = of; A.oy = of + N * qf; A.nxf = of + 2 * N * qf; A.nyf = of + 3 * N * qf;
+    A.zfast = c->opt.zfast + 2.0 * c->k * c->h;
+    ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * qf * qf, 0.0);   // units: far point pairs
+    TRY(assemble_planes(A, c->s));
+  }
   // circle: first rows -> eigenvalues
   TRY(c->mu.ensure(sizeof(zd) * 6 * N));
   AsmArgs B = asm_args(c, true);
@@ -444,8 +659,10 @@ int wcs_assemble(wcs_ctx* c) {
   // mu_X(m) = sum_j X_0j e^{+2 pi i m j / N}
   TRY(fft_columns(c->fft, mu_ptr(c, MU_S), N, 4, +1, c->s));
   k_mu_finish<<<(unsigned)((N + 255) / 256), 256, 0, c->s>>>(c->mu.z(), N, c->h);
+  note_launch();
   TRY(c->small.ensure(sizeof(double) * 8));
   k_absmax<<<1, 256, 0, c->s>>>(mu_ptr(c, MU_C), N, c->small.d());
+  note_launch();
   cudaMemcpyAsync(&c->norm_cc, c->small.p, sizeof(double), cudaMemcpyDeviceToHost, c->s);
   TRY(sync(c));
   c->U.release(); c->Vw.release(); c->Wt.release();
@@ -521,10 +738,24 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
       case WCS_OP_CC: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 0)); break;
       case WCS_OP_CCH: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 1)); break;
       case WCS_OP_CC_INV: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 2)); break;
-      case WCS_OP_S: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->S, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
-      case WCS_OP_D: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->D, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
-      case WCS_OP_DT: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Dt, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
-      case WCS_OP_N: TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Nk, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
+      case WCS_OP_S:
+      case WCS_OP_D:
+      case WCS_OP_DT:
+      case WCS_OP_N:
+        if (c->mixed) {
+          const int which = op - WCS_OP_S;
+          TRY(ensure_stage(c, cc));
+          TRY(stage(c, c->stage0, xc, ldx, cc, 0));
+          TRY(tc_apply(c, which, false, c->stage0, cc, mkz(1.0), mkz(0.0), yc, ldy));
+          break;
+        }
+        if (op != WCS_OP_S) goto fp64_ops;
+        TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->S, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break;
+      fp64_ops:
+        if (op == WCS_OP_D) { TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->D, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break; }
+        if (op == WCS_OP_DT) { TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Dt, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s)); break; }
+        TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Nk, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s));
+        break;
       case WCS_OP_G: TRY(gram_apply(xc, ldx, yc, ldy, N, cc, c->h, 1.0, 0.0, c->s)); break;
       case WCS_OP_SKEL: {
         if (c->stage < ST_SKELETON) { set_error("skeleton first"); return WCS_ERR_STATE; }
@@ -532,13 +763,14 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
         if (r == 0) { TRY(axpby(N, cc, mkz(0.0), xc, ldx, mkz(0.0), yc, ldy, c->s)); break; }
         TRY(c->small.ensure(sizeof(zd) * r * cc));
         // U V^T x = Q (Vw^H x)
-        TRY(zgemm(r, cc, N, mkz(1.0), blkH(c->Vw.z(), N), blk(xc, ldx), mkz(0.0), c->small.z(), r, c->s));
-        TRY(zgemm(N, cc, r, mkz(1.0), blk(c->U.z(), N), blk(c->small.z(), r), mkz(0.0), yc, ldy, c->s));
+        TRY(cgemm(c, r, cc, N, mkz(1.0), blkH(c->Vw.z(), N), xc, ldx, mkz(0.0), c->small.z(), r));
+        TRY(cgemm(c, N, cc, r, mkz(1.0), blk(c->U.z(), N), c->small.z(), r, mkz(0.0), yc, ldy));
         break;
       }
       default: set_error("unknown operator"); return WCS_ERR_ARG;
     }
   }
+  if (c->mixed) TRY(check_tc(c));
   return WCS_OK;
 }
 
@@ -572,8 +804,8 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
     offset += (uint64_t)N * b;
     TRY(apply_remainder(c, Om, N, Y, N, b, false));
     for (int pass = 0; pass < 2 && ell > 0; ++pass) {
-      TRY(zgemm(ell, b, N, one, blkH(Q, N), blk(Y, N), zero, Zb.z(), ell, c->s));
-      TRY(zgemm(N, b, ell, mone, blk(Q, N), blk(Zb.z(), ell), one, Y, N, c->s));
+      TRY(cgemm(c, ell, b, N, one, blkH(Q, N), Y, N, zero, Zb.z(), ell));
+      TRY(cgemm(c, N, b, ell, mone, blk(Q, N), Zb.z(), ell, one, Y, N));
     }
     TRY(column_norms(Y, N, N, b, Nb.d(), c->s));
     cudaMemcpyAsync(norms.data(), Nb.p, sizeof(double) * b, cudaMemcpyDeviceToHost, c->s);
@@ -598,8 +830,8 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
       if (pass == 0) {
         // re-orthogonalise against the accepted basis before the second pass
         if (ell > 0) {
-          TRY(zgemm(ell, rk, N, one, blkH(Q, N), blk(c->w3.z(), N), zero, Zb.z(), ell, c->s));
-          TRY(zgemm(N, rk, ell, mone, blk(Q, N), blk(Zb.z(), ell), one, c->w3.z(), N, c->s));
+          TRY(cgemm(c, ell, rk, N, one, blkH(Q, N), c->w3.z(), N, zero, Zb.z(), ell));
+          TRY(cgemm(c, N, rk, ell, mone, blk(Q, N), Zb.z(), ell, one, c->w3.z(), N));
         }
         src = c->w3.z();
       }
@@ -611,8 +843,10 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   c->rank = (int)ell;
   // V^T = Q^H (C - C_c)  <=>  Vw = (C - C_c)^H Q  (V = conj(Vw))
   TRY(c->Vw.ensure(sizeof(zd) * N * std::max<int64_t>(ell, 1)));
-  for (int64_t c0 = 0; c0 < ell; c0 += b) {
-    const int64_t cc = std::min<int64_t>(b, ell - c0);
+  const int64_t wide = std::max<int64_t>(b, std::min<int64_t>(c->opt.rhs_chunk, 1024));
+  TRY(ensure_work(c, wide));
+  for (int64_t c0 = 0; c0 < ell; c0 += wide) {
+    const int64_t cc = std::min<int64_t>(wide, ell - c0);
     TRY(apply_remainder(c, Q + c0 * N, N, c->Vw.z() + c0 * N, N, cc, true));
   }
   TRY(sync(c));
@@ -635,8 +869,9 @@ int wcs_factor(wcs_ctx* c) {
     // K = I + V^T W = I + Vw^H W
     TRY(Kb.ensure(sizeof(zd) * r * r));
     TRY(Kinv.ensure(sizeof(zd) * r * r));
-    TRY(zgemm(r, r, N, mkz(1.0), blkH(c->Vw.z(), N), blk(Wb.z(), N), mkz(0.0), Kb.z(), r, c->s));
+    TRY(cgemm(c, r, r, N, mkz(1.0), blkH(c->Vw.z(), N), Wb.z(), N, mkz(0.0), Kb.z(), r));
     k_add_identity<<<(unsigned)((r + 255) / 256), 256, 0, c->s>>>(Kb.z(), r);
+    note_launch();
     TRY(info.ensure(sizeof(int) + sizeof(double) * 2));
     int* infod = (int*)info.p;
     double* minpiv = (double*)((char*)info.p + 8);
@@ -648,7 +883,7 @@ int wcs_factor(wcs_ctx* c) {
     TRY(sync(c));
     if (infoh != 0 || !(mp > 1e-14)) { set_error("capacitance matrix is singular"); return WCS_ERR_SINGULAR; }
     // Wt = W K^{-1}
-    TRY(zgemm(N, r, r, mkz(1.0), blk(Wb.z(), N), blk(Kinv.z(), r), mkz(0.0), c->Wt.z(), N, c->s));
+    TRY(cgemm(c, N, r, r, mkz(1.0), blk(Wb.z(), N), Kinv.z(), r, mkz(0.0), c->Wt.z(), N));
     TRY(sync(c));
   }
   c->stage = ST_FACTORED;
@@ -692,8 +927,16 @@ static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b
   zd* T2 = c->w2.z();
   TRY(gram_inverse(e, ld, T1, N, N, cc, c->h, c->s));
   TRY(gram_inverse(hv, ld, T2, N, N, cc, c->h, c->s));
-  TRY(zgemm(N, cc, N, mkz(0.0, -c->k), op_view(c->S, c->ld, false), blk(T1, N), mkz(0.0), b, ldb, c->s));
-  TRY(zgemm(N, cc, N, mkz(-1.0), op_view(c->Dt, c->ld, false), blk(T2, N), mkz(1.0), b, ldb, c->s));
+  if (c->mixed) {
+    TRY(ensure_stage(c, cc));
+    TRY(stage(c, c->stage1, T1, N, cc, 0));
+    TRY(stage(c, c->stage2, T2, N, cc, 0));
+    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb));
+    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb));
+  } else {
+    TRY(zgemm(N, cc, N, mkz(0.0, -c->k), op_view(c->S, c->ld, false), blk(T1, N), mkz(0.0), b, ldb, c->s));
+    TRY(zgemm(N, cc, N, mkz(-1.0), op_view(c->Dt, c->ld, false), blk(T2, N), mkz(1.0), b, ldb, c->s));
+  }
   TRY(gram_apply(T2, N, b, ldb, N, cc, c->h, -0.5, 1.0, c->s));
   return 0;
 }
@@ -865,6 +1108,33 @@ int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A, int64
   pa.release(); pb.release(); err.release();
   if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
   if (errh) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
+  return WCS_OK;
+}
+
+uint64_t wcs_launch_count(void) { return (uint64_t)g_launches; }
+
+int wcs_profile(wcs_ctx* c, int enable) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  c->profile = enable != 0;
+  return WCS_OK;
+}
+
+int wcs_profile_read(wcs_ctx* c, int reset, double* out_host) {
+  if (!c || !out_host) { set_error("bad argument"); return WCS_ERR_ARG; }
+  TRY(sync(c));
+  for (int k = 0; k < 4 * CAT_COUNT; ++k) out_host[k] = 0.0;
+  for (auto& r : c->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    out_host[4 * r.cat + 0] += 1.0;
+    out_host[4 * r.cat + 1] += ms;
+    out_host[4 * r.cat + 2] += r.flops;
+    out_host[4 * r.cat + 3] += r.bytes;
+  }
+  if (reset) {
+    for (auto& r : c->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    c->recs.clear();
+  }
   return WCS_OK;
 }
 

@@ -175,6 +175,18 @@ class Solver:
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
         return j.t()
 
+    PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve")
+
+    def profile(self, enable=True):
+        check(self.lib.wcs_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, reset=True):
+        out = np.zeros(4 * len(self.PROFILE_CATS))
+        check(self.lib.wcs_profile_read(self.h, 1 if reset else 0, out.ctypes.data_as(C.c_void_p)))
+        out = out.reshape(-1, 4)
+        return {c: {"launches": int(r[0]), "ms": r[1], "work": r[2], "bytes": r[3]}
+                for c, r in zip(self.PROFILE_CATS, out)}
+
     def farfield(self, j, phi):
         jc = self._as_cols(j)
         p, pp = _host(phi, np.float64)
