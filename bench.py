@@ -144,7 +144,8 @@ def main():
     ap.add_argument("--workload", default="superellipse_n32768")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=None, help="skeleton tolerance")
-    ap.add_argument("--max-rank", type=int, default=0)
+    ap.add_argument("--max-rank", type=int, default=None,
+                    help="skeleton rank cap (default N/8 in the mixed form, none in FP64)")
     ap.add_argument("--refine-tol", type=float, default=None)
     ap.add_argument("--rhs", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -172,7 +173,8 @@ def main():
     from paper_2203_13283_gb300 import Solver
 
     mixed = args.form == "mixed"
-    tol = args.tol if args.tol is not None else (3e-2 if mixed else 1e-2)
+    tol = args.tol if args.tol is not None else (1e-6 if mixed else 1e-2)
+    max_rank = args.max_rank if args.max_rank is not None else (w["N"] // 8 if mixed else 0)
     rtol = args.refine_tol if args.refine_tol is not None else (1e-7 if mixed else 1e-12)
     S = Solver(device=f"cuda:{local}", precision=1 if mixed else 0, refine_tol=rtol, max_refine=12,
                rhs_chunk=1024 if mixed else 256, block=64)
@@ -192,7 +194,7 @@ def main():
         S.contour(w["family"], **w["params"])
         S.mesh(w["N"], w["k"])
         S.assemble()
-        rank_ = S.skeleton(tol, max_rank=args.max_rank, seed=1, allow_cap=True)
+        rank_ = S.skeleton(tol, max_rank=max_rank, seed=1, allow_cap=True)
         S.factor()
         e1.record(stream)
         S.solve_planewaves(angles, out=j, allow_unconverged=True)
