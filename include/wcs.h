@@ -219,6 +219,23 @@ int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, i
                         const double* B_dev, int64_t ldb, int planes, double* D_dev, int64_t ldd,
                         void* stream);
 
+/* The contraction of wcs_gemm_split_bf16 without any device allocation.  The
+ * paper has no counterpart: this is a service for callers that cannot call
+ * cudaMalloc (a real-time loop running on a frozen memory pool, a plug-in
+ * whose host application owns all device memory, code between two
+ * synchronisation points that must not allocate).  Same arguments and result
+ * as wcs_gemm_split_bf16; the staging planes and the error flag live in one
+ * file-scope device array of 32 MiB that every GPU loading the library holds
+ * until the process exits.  Sizes with (M + Nc) * ceil64(K) * planes * 2 bytes
+ * above that limit are rejected with WCS_ERR_ARG.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  All calls share the array: calls whose GPU
+ * work overlaps (other streams, other host threads) race on it.  Each call
+ * clears the parts that must start at zero.  Synchronises `stream`. */
+int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
+                                const double* B_dev, int64_t ldb, int planes, double* D_dev,
+                                int64_t ldd, void* stream);
+
 /* Number of CUDA kernel launches the library has issued in this process. */
 uint64_t wcs_launch_count(void);
 
