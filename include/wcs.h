@@ -64,7 +64,7 @@ typedef struct wcs_options {
   int max_refine;     /* maximum iterative-refinement steps per solve (default 12) */
   double refine_tol;  /* target relative residual ||b - C x|| / ||b|| per column (default 1e-12) */
   int rhs_chunk;      /* right-hand sides processed per pass (default 256) */
-  int mixed_planes;   /* mixed form: bf16 planes per operator entry (default 2, max 3) */
+  int mixed_planes;   /* mixed form: bf16 planes per operator entry (default 3, max 3) */
   int rhs_planes;     /* mixed form: bf16 planes per staged vector entry (= mixed_planes) */
   double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h use the FP32 path (default 14) */
   int reserved[2];
@@ -218,6 +218,14 @@ int wcs_farfield(wcs_ctx* ctx, int64_t B, const double* j_dev, int64_t ldj, int 
 int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
                         const double* B_dev, int64_t ldb, int planes, double* D_dev, int64_t ldd,
                         void* stream);
+
+/* wcs_gemm_split_bf16 with a choice of accumulation: accurate != 0 drains the
+ * tensor-memory accumulator into compensated FP32 registers after every
+ * K = 16 step (the accumulator of the MMA truncates, so its error grows with
+ * the number of steps it spans); planes must then be 2 or 3. */
+int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
+                           const double* B_dev, int64_t ldb, int planes, int accurate, double* D_dev,
+                           int64_t ldd, void* stream);
 
 /* The contraction of wcs_gemm_split_bf16 without any device allocation.  The
  * paper has no counterpart: this is a service for callers that cannot call

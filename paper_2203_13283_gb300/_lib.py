@@ -61,6 +61,7 @@ SIGNATURES = {
     "wcs_planewave_rhs": (I, [P, I64, P, P, P, I64]),
     "wcs_farfield": (I, [P, I64, P, I64, I, P, P, I64]),
     "wcs_gemm_split_bf16": (I, [I64, I64, I64, P, I64, P, I64, I, P, I64, P]),
+    "wcs_gemm_split_bf16_ex": (I, [I64, I64, I64, P, I64, P, I64, I, I, P, I64, P]),
     "wcs_gemm_split_bf16_noalloc": (I, [I64, I64, I64, P, I64, P, I64, I, P, I64, P]),
     "wcs_launch_count": (U64, []),
     "wcs_profile": (I, [P, I]),

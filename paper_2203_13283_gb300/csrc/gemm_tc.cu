@@ -296,6 +296,210 @@ static int launch_tc(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaS
   return 0;
 }
 
+
+// ----------------------------------------------------------------------------- accurate variant
+// The tensor-core accumulator truncates: its relative error grows with the
+// number of accumulation steps (measured ~3e-8 per step).  This variant keeps
+// each K = 16 step's result in its own TMEM buffer (two buffers, ping-pong),
+// and eight drain warps move it into FP32 registers before the next use, so no
+// TMEM sum spans more than one step.  Register sums are two-level (an inner
+// sum over 64 steps folded into an outer sum), which keeps the FP32 rounding
+// of ~K/16 additions near 1e-7 at a quarter of the cost of compensated
+// summation.  Tile 128 x 128; warps 0-7 drain (warp w: TMEM lanes 32 (w % 4),
+// columns 64 (w / 4)), warp 8 loads (TMA), warp 9 issues the MMAs.
+constexpr int ACC_NT = 128, ACC_THREADS = 320, ACC_FOLD = 64;
+
+template <int PA, int PB, int STAGES>
+struct AccSmem {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;        // 16 KB
+  static constexpr int B_BYTES = ACC_NT * TC_BK * 2;       // 16 KB
+  static constexpr int STAGE_BYTES = PA * A_BYTES + PB * B_BYTES;
+  static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int PA, int PB, int STAGES>
+__global__ void __launch_bounds__(ACC_THREADS, 1)
+    k_gemm_tc_acc(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                  const __grid_constant__ CUtensorMap mA2, const __grid_constant__ CUtensorMap mB0,
+                  const __grid_constant__ CUtensorMap mB1, const __grid_constant__ CUtensorMap mB2, TcArgs args) {
+  using L = AccSmem<PA, PB, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  if (*(volatile int*)args.err != 0) return;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * L::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;      // [2] MMA -> drain
+  uint64_t* tempty = tfull + 2;          // [2] drain -> MMA
+  uint32_t* tslot = (uint32_t*)(tempty + 2);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+  volatile int* issued = (volatile int*)(tslot + 2);
+  volatile int* consumed = (volatile int*)(tslot + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TC_BM;
+  const int n0 = blockIdx.x * ACC_NT;
+  const int nk = (args.K + TC_BK - 1) / TC_BK;
+  const int nsteps = nk * (TC_BK / 16);
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+    for (int q = 0; q < 2; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], 8); }
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"((uint32_t)(2 * ACC_NT)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const CUtensorMap* mapA[3] = {&mA0, &mA1, &mA2};
+  const CUtensorMap* mapB[3] = {&mB0, &mB1, &mB2};
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ACC_NT >> 3) << 17) |
+                         ((uint32_t)(TC_BM >> 4) << 24);
+
+  float inner[64], outer[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) { inner[i] = 0.f; outer[i] = 0.f; }
+
+  if (warp == 8) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nk; ++kb) {
+        const int st = kb % STAGES;
+        if (kb >= STAGES) {
+          if (!mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+        }
+        if (*abort_flag) break;
+        uint8_t* sp = smem + st * L::STAGE_BYTES;
+        mbar_expect_tx(&full[st], L::STAGE_BYTES);
+        const int k0 = kb * TC_BK;
+#pragma unroll
+        for (int p = 0; p < PA; ++p) tma_load_2d(sp + p * L::A_BYTES, mapA[p], &full[st], k0, m0);
+#pragma unroll
+        for (int p = 0; p < PB; ++p) tma_load_2d(sp + PA * L::A_BYTES + p * L::B_BYTES, mapB[p], &full[st], k0, n0);
+        *issued = kb + 1;
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int kb = 0; kb < nk && ok; ++kb) {
+        const int st = kb % STAGES;
+        if (!mbar_wait(&full[st], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+        *consumed = kb + 1;
+        if (*abort_flag) break;
+        tc_fence_after();
+        uint8_t* sp = smem + st * L::STAGE_BYTES;
+        for (int kk = 0; kk < TC_BK / 16; ++kk, ++g) {
+          const int b = g & 1;
+          if (g >= 2 && !mbar_wait(&tempty[b], ((g >> 1) - 1) & 1, WAIT_LIMIT, args.err)) {
+            *abort_flag = 1; ok = false; break;
+          }
+          tc_fence_after();
+          const uint32_t dt = tmem + (uint32_t)(b * ACC_NT);
+          for (int p = 0; p < args.nprod; ++p) {
+            const uint64_t da = sw128_desc(sp + args.ia[p] * L::A_BYTES);
+            const uint64_t db = sw128_desc(sp + PA * L::A_BYTES + args.ib[p] * L::B_BYTES);
+            mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, p > 0 ? 1u : 0u);
+          }
+          mma_commit(&tfull[b]);
+        }
+        mma_commit(&empty[st]);
+      }
+    }
+  } else {
+    // drain warps
+    const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
+    for (int g = 0; g < nsteps; ++g) {
+      const int b = g & 1;
+      bool got = mbar_wait(&tfull[b], (g >> 1) & 1, WAIT_LIMIT, args.err);
+      got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
+      if (!got) { if (lane == 0) *abort_flag = 1; break; }
+      tc_fence_after();
+      float v[32];
+      const uint32_t ta = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colhalf);
+      tmem_ld32(ta, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) inner[i] += v[i];
+      tmem_ld32(ta + 32, v);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) inner[32 + i] += v[i];
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
+      if ((g % ACC_FOLD) == ACC_FOLD - 1) {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) { outer[i] += inner[i]; inner[i] = 0.f; }
+      }
+    }
+  }
+  __syncthreads();
+  const bool ok = (*abort_flag == 0);
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      const int zero_flag = 0;
+      atomicExch(args.err, 1);
+      for (int kb = *consumed; kb < *issued; ++kb)
+        (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
+    }
+  } else if (warp < 8) {
+    float out[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) out[i] = outer[i] + inner[i];
+    epilogue_store(args, m0 + 32 * (warp & 3) + lane, n0 + 64 * (warp >> 2), out);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) out[i] = outer[32 + i] + inner[32 + i];
+    epilogue_store(args, m0 + 32 * (warp & 3) + lane, n0 + 64 * (warp >> 2) + 32, out);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * ACC_NT)));
+  }
+}
+
+template <int PA, int PB, int STAGES>
+static int launch_tc_acc(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaStream_t s) {
+  using L = AccSmem<PA, PB, STAGES>;
+  CUtensorMap ma[3], mb[3];
+  std::memset(ma, 0, sizeof(ma));
+  std::memset(mb, 0, sizeof(mb));
+  for (int p = 0; p < PA; ++p) TRY_TC(make_map(&ma[p], A.plane[p], args.M, args.K, A.ld, TC_BM));
+  for (int p = 0; p < PB; ++p) TRY_TC(make_map(&mb[p], B.plane[p], args.Nc, args.K, B.ld, ACC_NT));
+  for (int p = PA; p < 3; ++p) ma[p] = ma[0];
+  for (int p = PB; p < 3; ++p) mb[p] = mb[0];
+  auto kern = k_gemm_tc_acc<PA, PB, STAGES>;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    attr = true;
+  }
+  dim3 grid((unsigned)((args.Nc + ACC_NT - 1) / ACC_NT), (unsigned)((args.M + TC_BM - 1) / TC_BM));
+  kern<<<grid, ACC_THREADS, L::TOTAL, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], args);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("gemm_tc_acc launch: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
+}
+
+int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s) {
+  if (args.M <= 0 || args.Nc <= 0 || args.K <= 0) return 0;
+  if (args.nprod < 1 || args.nprod > 6) { set_error("gemm_tc: 1..6 products"); return 1; }
+  for (int p = 0; p < args.nprod; ++p)
+    if (args.ia[p] >= A.planes || args.ib[p] >= B.planes) { set_error("gemm_tc: plane index"); return 1; }
+  if ((args.M + TC_BM - 1) / TC_BM > 65535) { set_error("gemm_tc: M too large"); return 1; }
+  if (A.planes == 3 && B.planes == 3) return launch_tc_acc<3, 3, 2>(A, B, args, s);
+  if (A.planes == 2 && B.planes == 2) return launch_tc_acc<2, 2, 3>(A, B, args, s);
+  set_error("gemm_tc_accurate: plane combination not built");
+  return 1;
+}
+
 int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s) {
   if (args.M <= 0 || args.Nc <= 0 || args.K <= 0) return 0;
   if (args.nprod < 1 || args.nprod > 6) { set_error("gemm_tc: 1..6 products"); return 1; }

@@ -71,17 +71,22 @@ __device__ __forceinline__ void epilogue_store(const TcArgs& a, int row, int col
 }
 
 int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s);
+// Same contraction with the accumulator drained every K = 16 step into
+// compensated FP32 registers (accuracy ~1e-7 independent of K).
+int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s);
 
-// Product lists for 1, 2 or 3 planes per operand (terms of order <= planes-1).
+// Product lists for 1, 2 or 3 planes per operand (terms of order <= planes-1),
+// smallest first: the accumulator truncates each addition relative to its
+// current magnitude, so the dominant hi*hi term is added last.
 inline void tc_products(int planes, TcArgs& a) {
   if (planes == 1) { a.nprod = 1; a.ia[0] = 0; a.ib[0] = 0; return; }
   if (planes == 2) {
-    const int ia[3] = {0, 0, 1}, ib[3] = {0, 1, 0};
+    const int ia[3] = {1, 0, 0}, ib[3] = {0, 1, 0};
     a.nprod = 3;
     for (int i = 0; i < 3; ++i) { a.ia[i] = ia[i]; a.ib[i] = ib[i]; }
     return;
   }
-  const int ia[6] = {0, 0, 1, 0, 1, 2}, ib[6] = {0, 1, 0, 2, 1, 0};
+  const int ia[6] = {2, 1, 0, 1, 0, 0}, ib[6] = {0, 1, 2, 0, 1, 0};
   a.nprod = 6;
   for (int i = 0; i < 6; ++i) { a.ia[i] = ia[i]; a.ib[i] = ib[i]; }
 }

@@ -134,6 +134,9 @@ int gaussian_fill(zd* X, int64_t ld, int64_t m, int64_t n, uint64_t seed, uint64
 // Y(:, c) = a X(:, c) + b Y(:, c)
 int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int64_t ldy,
           cudaStream_t s);
+// G (b x b, column-major) = X^H X for X m x b (b <= 64); work holds
+// ceil(m/256) * b * b partial sums.
+int gram_matrix(const zd* X, int64_t ld, int64_t m, int b, zd* G, zd* work, cudaStream_t s);
 // Pivoted Cholesky of a Hermitian b x b Gram (device, column-major ld = b): returns
 // numerical rank r (pivots >= tol^2 * max) and writes R (upper, r x b in permuted order)
 // and the pivot permutation.  Runs in one thread block.

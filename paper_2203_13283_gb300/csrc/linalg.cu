@@ -279,6 +279,61 @@ int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int
   return 0;
 }
 
+// =========================================================================== Gram matrix X^H X
+// Tall-skinny X (m x b, b <= 64): CTAs take row chunks and write partial
+// b x b Grams, a second kernel sums the partials (fixed order: deterministic).
+constexpr int GRAM_ROWS = 256;
+
+__global__ void k_gram_partial(const zd* X, int64_t ld, int64_t m, int b, zd* part) {
+  __shared__ zd xs[64][65];
+  const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
+  const int tid = threadIdx.x;                  // 256 threads: (i, j) pairs
+  zd acc[16];
+#pragma unroll
+  for (int t = 0; t < 16; ++t) acc[t] = mkz(0.0);
+  for (int64_t rr = r0; rr < min(m, r0 + GRAM_ROWS); rr += 64) {
+    __syncthreads();
+    for (int u = tid; u < 64 * b; u += blockDim.x) {
+      const int c = u / 64, r = u % 64;
+      xs[c][r] = (rr + r < m) ? X[(int64_t)c * ld + rr + r] : mkz(0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const int pidx = tid + 256 * t;
+      const int i = pidx / 64, j = pidx % 64;
+      if (i < b && j < b)
+        for (int r = 0; r < 64; ++r) zfma(acc[t], conj(xs[i][r]), xs[j][r]);
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 16; ++t) {
+    const int pidx = tid + 256 * t;
+    const int i = pidx / 64, j = pidx % 64;
+    if (i < b && j < b) part[(int64_t)blockIdx.x * b * b + j * b + i] = acc[t];
+  }
+}
+
+__global__ void k_gram_reduce(const zd* part, int nparts, int b, zd* G) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= b * b) return;
+  zd s = mkz(0.0);
+  for (int p = 0; p < nparts; ++p) s += part[(int64_t)p * b * b + t];
+  G[t] = s;
+}
+
+int gram_matrix(const zd* X, int64_t ld, int64_t m, int b, zd* G, zd* work, cudaStream_t s) {
+  if (b > 64) { set_error("gram_matrix: b <= 64"); return 1; }
+  const int nparts = (int)((m + GRAM_ROWS - 1) / GRAM_ROWS);
+  k_gram_partial<<<nparts, 256, 0, s>>>(X, ld, m, b, work);
+  note_launch();
+  k_gram_reduce<<<(b * b + 255) / 256, 256, 0, s>>>(work, nparts, b, G);
+  note_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("gram: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
 // =========================================================================== pivoted Cholesky
 // In-place on a Hermitian b x b matrix (column-major, ld = b), one CTA.
 // After return: rank r, perm[0:b], and R (upper, row j holds R[j, j..b-1]

@@ -82,7 +82,8 @@ struct wcs_ctx {
 };
 
 enum StatCat { CAT_GEMM_TC = 0, CAT_ASSEMBLY = 1, CAT_FFT = 2, CAT_ZGEMM = 3, CAT_SKELETON = 4,
-               CAT_FACTOR = 5, CAT_SOLVE = 6, CAT_COUNT = 7 };
+               CAT_FACTOR = 5, CAT_SOLVE = 6, CAT_GEMM_ACC = 7, CAT_SAMPLE = 8, CAT_PROJECT = 9,
+               CAT_ORTH = 10, CAT_VW = 11, CAT_INVERSE = 12, CAT_COUNT = 13 };
 
 struct ProfScope {
   wcs_ctx* c;
@@ -157,20 +158,24 @@ static int stage(wcs_ctx* c, DevBuf& buf, const zd* X, int64_t ldx, int64_t cols
 // operators (0 S~, 1 D, 2 D~, 3 N), X already staged in `buf`.  adjoint uses
 // the transposed planes: A^H x = conj(A^T conj(x)) (buf staged with conj).
 static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols, zd alpha, zd beta, zd* Y,
-                    int64_t ldy) {
+                    int64_t ldy, bool accurate = false) {
+  // accurate: all stored planes, accumulator drained every K step (refinement
+  // residual, preconditioned right-hand side); otherwise the two leading
+  // planes with one TMEM accumulator (skeleton sampling, Woodbury products)
+  const int P = accurate ? std::min(c->planes, c->rhs_planes) : std::min(2, std::min(c->planes, c->rhs_planes));
   TcOperand A, B;
-  A.planes = c->planes;
+  A.planes = P;
   A.ld = c->ldp;
-  for (int p = 0; p < c->planes; ++p) A.plane[p] = plane_ptr(c, op, adjoint ? 1 : 0, p);
-  B.planes = c->rhs_planes;
+  for (int p = 0; p < P; ++p) A.plane[p] = plane_ptr(c, op, adjoint ? 1 : 0, p);
+  B.planes = P;
   B.ld = c->ldp;
   const int64_t per = 2 * c->stage_cols * c->ldp;
-  for (int p = 0; p < c->rhs_planes; ++p) B.plane[p] = (uint16_t*)buf.p + p * per;
+  for (int p = 0; p < P; ++p) B.plane[p] = (uint16_t*)buf.p + p * per;
   TcArgs t;
   t.M = (int)c->N;
   t.Nc = (int)(2 * cols);
   t.K = (int)(2 * c->N);
-  tc_products(std::min(c->planes, c->rhs_planes), t);
+  tc_products(P, t);
   t.epi = EPI_CPLX_F64;
   t.conj_out = adjoint ? 1 : 0;
   t.out = Y;
@@ -178,8 +183,8 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.alpha = alpha;
   t.beta = beta;
   t.err = (int*)c->tcerr.p;
-  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
-  return gemm_tc(A, B, t, c->s);
+  ProfScope ps(c, accurate ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  return accurate ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s);
 }
 
 static int check_tc(wcs_ctx* c) {
@@ -197,7 +202,7 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
                  zd beta, zd* C, int64_t ldc) {
   if (m <= 0 || n <= 0) return 0;
   if (!c->mixed || k < 64) return zgemm(m, n, k, alpha, A, blk(X, ldx), beta, C, ldc, c->s);
-  const int P = c->rhs_planes;
+  const int P = 2;
   const int64_t ldk = ((2 * k + 63) / 64) * 64;
   // grow the staging buffers geometrically: the skeleton calls this with a
   // basis that widens block by block
@@ -230,7 +235,8 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
   return gemm_tc(oa, ob, t, c->s);
 }
 
-static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj) {
+static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj,
+                         bool acc) {
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -239,11 +245,11 @@ static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ld
   const int cj = adj ? 1 : 0;
   TRY(stage(c, c->stage0, X, ldx, cols, cj));
   if (!adj) {
-    TRY(tc_apply(c, 1, false, c->stage0, cols, mone, zero, T1, N));   // -D X
-    TRY(tc_apply(c, 3, false, c->stage0, cols, one, zero, T2, N));    // N X
+    TRY(tc_apply(c, 1, false, c->stage0, cols, mone, zero, T1, N, acc));   // -D X
+    TRY(tc_apply(c, 3, false, c->stage0, cols, one, zero, T2, N, acc));    // N X
   } else {
-    TRY(tc_apply(c, 2, true, c->stage0, cols, one, zero, T1, N));     // D~^H X
-    TRY(tc_apply(c, 0, true, c->stage0, cols, one, zero, T2, N));     // S~^H X
+    TRY(tc_apply(c, 2, true, c->stage0, cols, one, zero, T1, N, acc));     // D~^H X
+    TRY(tc_apply(c, 0, true, c->stage0, cols, one, zero, T2, N, acc));     // S~^H X
   }
   TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
   TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
@@ -251,19 +257,20 @@ static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ld
   TRY(stage(c, c->stage1, T1, N, cols, cj));
   TRY(stage(c, c->stage2, T2, N, cols, cj));
   if (!adj) {
-    TRY(tc_apply(c, 2, false, c->stage1, cols, one, zero, Y, ldy));   // D~ T1
-    TRY(tc_apply(c, 0, false, c->stage2, cols, one, one, Y, ldy));    // + S~ T2
+    TRY(tc_apply(c, 2, false, c->stage1, cols, one, zero, Y, ldy, acc));   // D~ T1
+    TRY(tc_apply(c, 0, false, c->stage2, cols, one, one, Y, ldy, acc));    // + S~ T2
   } else {
-    TRY(tc_apply(c, 1, true, c->stage1, cols, mone, zero, Y, ldy));   // -D^H T1
-    TRY(tc_apply(c, 3, true, c->stage2, cols, one, one, Y, ldy));     // + N^H T2
+    TRY(tc_apply(c, 1, true, c->stage1, cols, mone, zero, Y, ldy, acc));   // -D^H T1
+    TRY(tc_apply(c, 3, true, c->stage2, cols, one, one, Y, ldy, acc));     // + N^H T2
   }
   TRY(gram_apply(T1, N, Y, ldy, N, cols, c->h, 0.5, 1.0, c->s));
   return 0;
 }
 
 // Y = C X (adjoint: C^H X); uses w1, w2 as temporaries.  Y must not alias X.
-static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj) {
-  if (c->mixed) return apply_C_mixed(c, X, ldx, Y, ldy, cols, adj);
+static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj,
+                   bool accurate = false) {
+  if (c->mixed) return apply_C_mixed(c, X, ldx, Y, ldy, cols, adj, accurate);
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -402,8 +409,8 @@ int wcs_default_options(wcs_options* o) {
   o->max_refine = 12;
   o->refine_tol = 1e-12;
   o->rhs_chunk = 256;
-  o->mixed_planes = 2;
-  o->rhs_planes = 2;
+  o->mixed_planes = 3;
+  o->rhs_planes = 3;
   o->zfast = 14.0;
   return WCS_OK;
 }
@@ -733,8 +740,8 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
     const zd* xc = x + c0 * ldx;
     zd* yc = y + c0 * ldy;
     switch (op) {
-      case WCS_OP_C: TRY(apply_C(c, xc, ldx, yc, ldy, cc, false)); break;
-      case WCS_OP_CH: TRY(apply_C(c, xc, ldx, yc, ldy, cc, true)); break;
+      case WCS_OP_C: TRY(apply_C(c, xc, ldx, yc, ldy, cc, false, true)); break;
+      case WCS_OP_CH: TRY(apply_C(c, xc, ldx, yc, ldy, cc, true, true)); break;
       case WCS_OP_CC: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 0)); break;
       case WCS_OP_CCH: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 1)); break;
       case WCS_OP_CC_INV: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 2)); break;
@@ -746,7 +753,7 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
           const int which = op - WCS_OP_S;
           TRY(ensure_stage(c, cc));
           TRY(stage(c, c->stage0, xc, ldx, cc, 0));
-          TRY(tc_apply(c, which, false, c->stage0, cc, mkz(1.0), mkz(0.0), yc, ldy));
+          TRY(tc_apply(c, which, false, c->stage0, cc, mkz(1.0), mkz(0.0), yc, ldy, true));
           break;
         }
         if (op != WCS_OP_S) goto fp64_ops;
@@ -781,12 +788,14 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   const int64_t N = c->N;
   const int64_t cap = (max_rank <= 0 || max_rank > N) ? N : max_rank;
   const int b = c->opt.block;
+  ProfScope whole(c, CAT_SKELETON, 0.0, 0.0);
   TRY(ensure_work(c, b));
   TRY(c->U.ensure(sizeof(zd) * N * (cap + b)));
   zd* Q = c->U.z();
   const double thr = tol * c->norm_cc / (10.0 * std::sqrt(2.0 / WCS_PI));
   // small scratch: Z (cap x b), Gram (b x b), perm, rank, norms
-  DevBuf Zb, Gb, Ib, Nb;
+  DevBuf Zb, Gb, Ib, Nb, GW;
+  TRY(GW.ensure(sizeof(zd) * ((N + 255) / 256) * b * b));
   TRY(Zb.ensure(sizeof(zd) * (cap + b) * b));
   TRY(Gb.ensure(sizeof(zd) * b * b));
   TRY(Ib.ensure(sizeof(int) * (b + 1)));
@@ -800,9 +809,13 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   const zd one = mkz(1.0), mone = mkz(-1.0), zero = mkz(0.0);
   while (true) {
     if (ell >= cap) { status = (ell < N) ? WCS_ERR_RANK_CAP : WCS_OK; break; }
-    TRY(gaussian_fill(Om, N, N, b, seed, offset, c->s));
-    offset += (uint64_t)N * b;
-    TRY(apply_remainder(c, Om, N, Y, N, b, false));
+    {
+      ProfScope ps(c, CAT_SAMPLE, 0.0, 0.0);
+      TRY(gaussian_fill(Om, N, N, b, seed, offset, c->s));
+      offset += (uint64_t)N * b;
+      TRY(apply_remainder(c, Om, N, Y, N, b, false));
+    }
+    ProfScope ps_proj(c, CAT_PROJECT, 0.0, 0.0);
     for (int pass = 0; pass < 2 && ell > 0; ++pass) {
       TRY(cgemm(c, ell, b, N, one, blkH(Q, N), Y, N, zero, Zb.z(), ell));
       TRY(cgemm(c, N, b, ell, mone, blk(Q, N), Zb.z(), ell, one, Y, N));
@@ -814,11 +827,12 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
     for (int j = 0; j < b; ++j) mx = std::max(mx, norms[j]);
     if (mx <= thr) break;
     // orthonormalise the block twice (pivoted CholeskyQR)
+    ProfScope ps_orth(c, CAT_ORTH, 0.0, 0.0);
     int rk = b;
     const zd* src = Y;
     for (int pass = 0; pass < 2; ++pass) {
       const int cols = (pass == 0) ? b : rk;
-      TRY(zgemm(cols, cols, N, one, blkH(src, N), blk(src, N), zero, Gb.z(), cols, c->s));
+      TRY(gram_matrix(src, N, N, cols, Gb.z(), GW.z(), c->s));
       TRY(pivoted_cholesky(Gb.z(), cols, 1e-7, (int*)Ib.p, (int*)Ib.p + b, c->s));
       int rk_new = 0;
       cudaMemcpyAsync(&rk_new, (int*)Ib.p + b, sizeof(int), cudaMemcpyDeviceToHost, c->s);
@@ -843,6 +857,7 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   c->rank = (int)ell;
   // V^T = Q^H (C - C_c)  <=>  Vw = (C - C_c)^H Q  (V = conj(Vw))
   TRY(c->Vw.ensure(sizeof(zd) * N * std::max<int64_t>(ell, 1)));
+  ProfScope ps_vw(c, CAT_VW, 0.0, 0.0);
   const int64_t wide = std::max<int64_t>(b, std::min<int64_t>(c->opt.rhs_chunk, 1024));
   TRY(ensure_work(c, wide));
   for (int64_t c0 = 0; c0 < ell; c0 += wide) {
@@ -860,6 +875,7 @@ int wcs_factor(wcs_ctx* c) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
   if (c->stage < ST_SKELETON) { set_error("skeleton first"); return WCS_ERR_STATE; }
   const int64_t N = c->N, r = c->rank;
+  ProfScope whole(c, CAT_FACTOR, 8.0 / 3.0 * r * (double)r * r, 0.0);
   if (r > 0) {
     TRY(c->Wt.ensure(sizeof(zd) * N * r));
     // W = C_c^{-1} U  (held in Wt until the inverse is applied)
@@ -875,7 +891,10 @@ int wcs_factor(wcs_ctx* c) {
     TRY(info.ensure(sizeof(int) + sizeof(double) * 2));
     int* infod = (int*)info.p;
     double* minpiv = (double*)((char*)info.p + 8);
-    TRY(lu_inverse(Kb.z(), r, Kinv.z(), nullptr, infod, minpiv, c->s));
+    {
+      ProfScope ps(c, CAT_INVERSE, 8.0 * r * (double)r * r, 0.0);
+      TRY(lu_inverse(Kb.z(), r, Kinv.z(), nullptr, infod, minpiv, c->s));
+    }
     int infoh = 0;
     double mp = 0;
     cudaMemcpyAsync(&infoh, infod, sizeof(int), cudaMemcpyDeviceToHost, c->s);
@@ -931,8 +950,8 @@ static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b
     TRY(ensure_stage(c, cc));
     TRY(stage(c, c->stage1, T1, N, cc, 0));
     TRY(stage(c, c->stage2, T2, N, cc, 0));
-    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb));
-    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb));
+    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb, true));
+    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb, true));
   } else {
     TRY(zgemm(N, cc, N, mkz(0.0, -c->k), op_view(c->S, c->ld, false), blk(T1, N), mkz(0.0), b, ldb, c->s));
     TRY(zgemm(N, cc, N, mkz(-1.0), op_view(c->Dt, c->ld, false), blk(T2, N), mkz(1.0), b, ldb, c->s));
@@ -954,16 +973,33 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
   zd* R = c->w4.z();
   zd* dx = c->w5.z();
   int it = 0;
-  double worst = 0;
+  double worst = 0, prev = 1e300;
+  bool accurate = !c->mixed;   // mixed form: fast residuals while the error is large
   for (;; ++it) {
-    TRY(apply_C(c, x, ldx, R, N, cc, false));
+    TRY(apply_C(c, x, ldx, R, N, cc, false, accurate || !c->mixed));
     TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));   // R = b - C x
     TRY(column_norms(R, N, N, cc, nb.d() + cc, c->s));
     cudaMemcpyAsync(rn.data(), nb.d() + cc, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
     TRY(sync(c));
     worst = 0;
     for (int64_t j = 0; j < cc; ++j) worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
-    if (worst <= c->opt.refine_tol || it >= c->opt.max_refine) break;
+    if (!accurate && (worst < 3e-3 || it >= c->opt.max_refine / 2)) {
+      // the fast contraction's own error (~1e-4 at large K) is now comparable
+      // with the residual: recompute it with the drained accumulation
+      accurate = true;
+      TRY(apply_C(c, x, ldx, R, N, cc, false, true));
+      TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));
+      TRY(column_norms(R, N, N, cc, nb.d() + cc, c->s));
+      cudaMemcpyAsync(rn.data(), nb.d() + cc, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
+      TRY(sync(c));
+      worst = 0;
+      for (int64_t j = 0; j < cc; ++j) worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
+    }
+    if ((accurate && worst <= c->opt.refine_tol) || it >= c->opt.max_refine) break;
+    // stagnation: the residual no longer decreases (its floor is the
+    // contraction's rounding); further steps cannot improve the solution
+    if (accurate && c->mixed && worst > 0.7 * prev) break;
+    if (accurate) prev = worst;
     TRY(woodbury(c, R, N, dx, N, cc));
     TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
   }
@@ -1065,8 +1101,22 @@ int wcs_farfield(wcs_ctx* c, int64_t B, const double* j, int64_t ldj, int nphi, 
   return r;
 }
 
+static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, int planes, int accurate, double* D, int64_t ldd, void* stream);
+
 int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
                         int64_t ldb, int planes, double* D, int64_t ldd, void* stream) {
+  return gemm_split_impl(M, Nc, K, A, lda, B, ldb, planes, 0, D, ldd, stream);
+}
+
+int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, int planes, int accurate, double* D, int64_t ldd, void* stream) {
+  return gemm_split_impl(M, Nc, K, A, lda, B, ldb, planes, accurate, D, ldd, stream);
+}
+
+static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
+                           int64_t ldb, int planes, int accurate, double* D, int64_t ldd, void* stream) {
+  if (accurate && planes < 2) { set_error("accurate contraction needs 2 or 3 planes"); return WCS_ERR_ARG; }
   if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (!A || lda < K)) ||
       (Nc > 0 && (!B || ldb < K)) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
     set_error("bad argument");
@@ -1101,7 +1151,7 @@ int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A, int64
   t.out = D;
   t.ldo = ldd;
   t.err = (int*)err.p;
-  TRY(gemm_tc(oa, ob, t, s));
+  TRY(accurate ? gemm_tc_accurate(oa, ob, t, s) : gemm_tc(oa, ob, t, s));
   int errh = 0;
   cudaMemcpyAsync(&errh, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);

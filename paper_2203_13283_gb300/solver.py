@@ -175,7 +175,8 @@ class Solver:
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
         return j.t()
 
-    PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve")
+    PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
+                    "sample", "project", "orth", "vw", "inverse")
 
     def profile(self, enable=True):
         check(self.lib.wcs_profile(self.h, 1 if enable else 0))
@@ -201,7 +202,7 @@ def quadrature_tables(q):
     return out.reshape(3, q, q)
 
 
-def gemm_split_bf16(A, B, planes=2):
+def gemm_split_bf16(A, B, planes=2, accurate=False):
     """D = A @ B.T on the tensor cores with split-bf16 operands (FP64 in/out, cuda)."""
     A = torch.as_tensor(A, dtype=torch.float64, device="cuda").contiguous()
     B = torch.as_tensor(B, dtype=torch.float64, device="cuda").contiguous()
@@ -209,6 +210,6 @@ def gemm_split_bf16(A, B, planes=2):
     Nc = B.shape[0]
     D = torch.empty((M, Nc), dtype=torch.float64, device=A.device)
     st = torch.cuda.current_stream(A.device)
-    check(load().wcs_gemm_split_bf16(M, Nc, K, _ptr(A), K, _ptr(B), K, int(planes), _ptr(D), Nc,
-                                     C.c_void_p(st.cuda_stream)))
+    check(load().wcs_gemm_split_bf16_ex(M, Nc, K, _ptr(A), K, _ptr(B), K, int(planes), int(bool(accurate)),
+                                        _ptr(D), Nc, C.c_void_p(st.cuda_stream)))
     return D

@@ -24,3 +24,19 @@ def test_split_bf16_gemm(M, Nc, K, planes):
     # bound: input rounding 2^-(8 planes) plus FP32 accumulation over K
     bound = {1: 1e-2, 2: 6e-5, 3: 1e-5}[planes]   # 3 planes: FP32 accumulation floor
     assert err < bound, err
+
+
+@pytest.mark.parametrize("M,Nc,K", [(128, 64, 64), (300, 200, 1000), (256, 128, 65536), (130, 70, 300)])
+@pytest.mark.parametrize("planes", [2, 3])
+def test_split_bf16_gemm_accurate(M, Nc, K, planes):
+    """Accumulator drained every K step: error independent of K."""
+    built()
+    from paper_2203_13283_gb300.solver import gemm_split_bf16
+    g = torch.Generator(device="cpu").manual_seed(M + 3 * Nc + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(Nc, K, generator=g, dtype=torch.float64).cuda()
+    D = gemm_split_bf16(A, B, planes, accurate=True)
+    ref = A @ B.T
+    err = ((D - ref).norm() / ref.norm()).item()
+    bound = {2: 3e-5, 3: 5e-7}[planes]
+    assert err < bound, err
