@@ -6,6 +6,7 @@
 // circulant; its eigenvalues mu_C come from the FFT of the first rows of the
 // circle operators.  Eq. (7): C - C_c = U V^T by randomized range finding;
 // Eq. (8)/(9): Woodbury with the capacitance K = I + V^T C_c^{-1} U.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -369,6 +370,64 @@ __global__ void k_absmax(const zd* x, int64_t n, double* out) {
     __syncthreads();
   }
   if (threadIdx.x == 0) *out = red[0];
+}
+
+// X0 = K^H / (||K||_1 ||K||_inf): column/row absolute sums
+__global__ void k_abs_sums(const zd* K, int64_t r, double* colsum, double* rowsum) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= r) return;
+  double cs = 0.0, rs = 0.0;
+  for (int64_t j = 0; j < r; ++j) {
+    cs += zabs(K[i * r + j]);   // column i
+    rs += zabs(K[j * r + i]);   // row i
+  }
+  colsum[i] = cs;
+  rowsum[i] = rs;
+}
+
+__global__ void k_scaled_adjoint(const zd* K, int64_t r, const double* colsum, const double* rowsum, zd* X) {
+  __shared__ double n1, ninf;
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int64_t i = 0; i < r; ++i) { a = fmax(a, colsum[i]); b = fmax(b, rowsum[i]); }
+    n1 = a;
+    ninf = b;
+  }
+  __syncthreads();
+  const double sc = 1.0 / (n1 * ninf);
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < r * r; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % r, j = t / r;   // X(i, j) = conj(K(j, i)) * sc
+    X[j * r + i] = sc * conj(K[i * r + j]);
+  }
+}
+
+// T = 2I - T (in place)
+__global__ void k_two_minus(zd* T, int64_t r) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= r * r) return;
+  const int64_t i = t % r, j = t / r;
+  zd v = -T[t];
+  if (i == j) v.x += 2.0;
+  T[t] = v;
+}
+
+// ||I - T||_F^2 partial sums (one block)
+__global__ void k_eye_residual(const zd* T, int64_t r, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t t = threadIdx.x; t < r * r; t += blockDim.x) {
+    const int64_t i = t % r, j = t / r;
+    zd v = T[t];
+    if (i == j) v.x -= 1.0;
+    s += abs2(v);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sqrt(red[0]);
 }
 
 __global__ void k_add_identity(zd* K, int64_t r) {
@@ -891,16 +950,56 @@ int wcs_factor(wcs_ctx* c) {
     TRY(info.ensure(sizeof(int) + sizeof(double) * 2));
     int* infod = (int*)info.p;
     double* minpiv = (double*)((char*)info.p + 8);
-    {
+    if (!c->mixed || r < 256) {
       ProfScope ps(c, CAT_INVERSE, 8.0 * r * (double)r * r, 0.0);
       TRY(lu_inverse(Kb.z(), r, Kinv.z(), nullptr, infod, minpiv, c->s));
+      int infoh = 0;
+      double mp = 0;
+      cudaMemcpyAsync(&infoh, infod, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+      cudaMemcpyAsync(&mp, minpiv, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+      TRY(sync(c));
+      if (infoh != 0 || !(mp > 1e-14)) { set_error("capacitance matrix is singular"); return WCS_ERR_SINGULAR; }
+    } else {
+      // Newton-Schulz: X <- X (2I - K X) from X0 = K^H / (||K||_1 ||K||_inf),
+      // which converges for any nonsingular K; products on the tensor cores
+      ProfScope ps(c, CAT_INVERSE, 16.0 * r * (double)r * r, 0.0);
+      DevBuf T, sums;
+      TRY(T.ensure(sizeof(zd) * r * r));
+      TRY(sums.ensure(sizeof(double) * (2 * r + 2)));
+      double* cs = sums.d();
+      k_abs_sums<<<(unsigned)((r + 127) / 128), 128, 0, c->s>>>(Kb.z(), r, cs, cs + r);
+      note_launch();
+      k_scaled_adjoint<<<1024, 256, 0, c->s>>>(Kb.z(), r, cs, cs + r, Kinv.z());
+      note_launch();
+      DevBuf X2;
+      TRY(X2.ensure(sizeof(zd) * r * r));
+      zd* X = Kinv.z();
+      zd* Xn = X2.z();
+      double res = 1e300, prev = 1e300;
+      const double target = 1e-4 * std::sqrt((double)r);   // ||I - K X||_F, i.e. ~1e-4 per direction
+      for (int it = 0; it < 120; ++it) {
+        // T = K X
+        TRY(cgemm(c, r, r, r, mkz(1.0), blk(Kb.z(), r), X, r, mkz(0.0), T.z(), r));
+        if ((it & 3) == 3) {
+          k_eye_residual<<<1, 256, 0, c->s>>>(T.z(), r, cs + 2 * r);
+          note_launch();
+          cudaMemcpyAsync(&res, cs + 2 * r, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+          TRY(sync(c));
+          if (!(res == res)) { set_error("capacitance iteration diverged"); return WCS_ERR_SINGULAR; }
+          // converged, or stalled at the contraction's rounding level
+          if (res < target || (res < 0.1 * std::sqrt((double)r) && res > 0.8 * prev)) break;
+          prev = res;
+        }
+        // X <- X (2I - T)
+        k_two_minus<<<(unsigned)((r * r + 255) / 256), 256, 0, c->s>>>(T.z(), r);
+        note_launch();
+        TRY(cgemm(c, r, r, r, mkz(1.0), blk(X, r), T.z(), r, mkz(0.0), Xn, r));
+        std::swap(X, Xn);
+      }
+      if (!(res < 0.1 * std::sqrt((double)r))) { set_error("capacitance iteration did not converge"); return WCS_ERR_SINGULAR; }
+      if (X != Kinv.z())
+        cudaMemcpyAsync(Kinv.p, X, sizeof(zd) * r * r, cudaMemcpyDeviceToDevice, c->s);
     }
-    int infoh = 0;
-    double mp = 0;
-    cudaMemcpyAsync(&infoh, infod, sizeof(int), cudaMemcpyDeviceToHost, c->s);
-    cudaMemcpyAsync(&mp, minpiv, sizeof(double), cudaMemcpyDeviceToHost, c->s);
-    TRY(sync(c));
-    if (infoh != 0 || !(mp > 1e-14)) { set_error("capacitance matrix is singular"); return WCS_ERR_SINGULAR; }
     // Wt = W K^{-1}
     TRY(cgemm(c, N, r, r, mkz(1.0), blk(Wb.z(), N), Kinv.z(), r, mkz(0.0), c->Wt.z(), N));
     TRY(sync(c));
