@@ -66,7 +66,7 @@ typedef struct wcs_options {
   int rhs_chunk;      /* right-hand sides processed per pass (default 256) */
   int mixed_planes;   /* mixed form: bf16 planes per operator entry (default 3, max 3) */
   int rhs_planes;     /* mixed form: bf16 planes per staged vector entry (= mixed_planes) */
-  double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h use the FP32 path (default 14) */
+  double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h use the FP32 path (default 9) */
   int reserved[2];
 } wcs_options;
 

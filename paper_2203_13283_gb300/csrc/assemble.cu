@@ -178,10 +178,10 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
 // R - R0 = (2 d0.(o_p - o_r) + |o_p - o_r|^2) / (R + R0) is small and
 // accurate in FP32, so the phase k R = (k R0 mod 2 pi) + k (R - R0) keeps
 // ~1e-7 absolute accuracy even for k R ~ 1e4.  The Hankel functions use the
-// large-argument expansion (DLMF 10.17.5) with eight terms (z >= 12 gives
+// large-argument expansion (DLMF 10.17.5) with ten terms (z >= 9 gives
 // < 1e-7), for k and for k~ = k + i beta (exp(i k~ R) = exp(i k R - beta R)).
 // ---------------------------------------------------------------------------
-__constant__ float c_a0[8], c_a1[8];   // a_k(0), a_k(1) of the Hankel expansion
+__constant__ float c_a0[10], c_a1[10];   // a_k(0), a_k(1) of the Hankel expansion
 
 struct cf {
   float x, y;
@@ -246,9 +246,9 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
       const cf E = {cs, sn};
       // real wavenumber: P + iQ = sum (i t)^k a_k, t = 1/(kR)
       const float t = iR / k, t2 = t * t;
-      float P0 = c_a0[6], Q0 = c_a0[7], P1 = c_a1[6], Q1 = c_a1[7];
+      float P0 = c_a0[8], Q0 = c_a0[9], P1 = c_a1[8], Q1 = c_a1[9];
 #pragma unroll
-      for (int m = 2; m >= 0; --m) {
+      for (int m = 3; m >= 0; --m) {
         P0 = fmaf(-t2, P0, c_a0[2 * m]);
         Q0 = fmaf(-t2, Q0, c_a0[2 * m + 1]);
         P1 = fmaf(-t2, P1, c_a1[2 * m]);
@@ -264,9 +264,9 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
       const cf dgk = cscale({-0.25f * H1.y, 0.25f * H1.x}, k * gg);
       // complex wavenumber: w = i/(k~ R)
       const cf w = cscale(ik, iR);
-      cf s0 = {c_a0[7], 0.f}, s1 = {c_a1[7], 0.f};
+      cf s0 = {c_a0[9], 0.f}, s1 = {c_a1[9], 0.f};
 #pragma unroll
-      for (int m = 6; m >= 0; --m) {
+      for (int m = 8; m >= 0; --m) {
         s0 = cmul(s0, w); s0.x += c_a0[m];
         s1 = cmul(s1, w); s1.x += c_a1[m];
       }
@@ -393,27 +393,33 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble(AsmArgs A) {
   }
 }
 
-// Row 0 of the four operators: thread per column j; node 0 gets element
-// N-1 (a = 1) and element 0 (a = 0); column j gets elements j-1 (b = 1), j (b = 0).
-__global__ void k_circle_row(AsmArgs A) {
+// Row 0 of the four operators: node 0 gets element N-1 (a = 1) and element 0
+// (a = 0); column j gets elements j-1 (b = 1) and j (b = 0).  One thread per
+// (column, element pair); the four partial values are summed in fixed order.
+__global__ void k_circle_row_part(AsmArgs A, zd* part) {
+  const int64_t N = A.N;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 4 * N) return;
+  const int64_t j = t >> 2;
+  const int u = (int)((t >> 1) & 1), v = (int)(t & 1);
+  const int64_t e = u ? 0 : N - 1;
+  const int a = u ? 0 : 1;
+  const int64_t f = v ? j : (j - 1 + N) % N;
+  const int b = v ? 0 : 1;
+  PairOut o;
+  pair_integrals(A, e, f, o);
+  for (int op = 0; op < 4; ++op) part[(int64_t)op * 4 * N + t] = o.v[op][a * 2 + b];
+}
+
+__global__ void k_circle_row_sum(AsmArgs A, const zd* part) {
   const int64_t N = A.N;
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= N) return;
-  zd sum[4] = {mkz(0.0), mkz(0.0), mkz(0.0), mkz(0.0)};
-  const int64_t es[2] = {N - 1, 0};
-  const int as_[2] = {1, 0};
-  const int64_t fs[2] = {(j - 1 + N) % N, j};
-  const int bs[2] = {1, 0};
-  for (int u = 0; u < 2; ++u)
-    for (int v = 0; v < 2; ++v) {
-      PairOut o;
-      pair_integrals(A, es[u], fs[v], o);
-      for (int op = 0; op < 4; ++op) sum[op] += o.v[op][as_[u] * 2 + bs[v]];
-    }
-  A.S[j] = sum[0];
-  A.D[j] = sum[1];
-  A.Dt[j] = sum[2];
-  A.Nk[j] = sum[3];
+  zd* outs[4] = {A.S, A.D, A.Dt, A.Nk};
+  for (int op = 0; op < 4; ++op) {
+    const zd* p = part + (int64_t)op * 4 * N + 4 * j;
+    outs[op][j] = ((p[0] + p[1]) + p[2]) + p[3];
+  }
 }
 
 // Entries (row i, col j): sum of the four element pairs (i-1|i) x (j-1|j).
@@ -470,11 +476,11 @@ __device__ __forceinline__ void split_store(double x, int planes, uint16_t* cons
 }
 
 static int upload_hankel_coefficients() {
-  float a0[8], a1[8];
+  float a0[10], a1[10];
   double t0 = 1.0, t1 = 1.0;
   a0[0] = 1.f;
   a1[0] = 1.f;
-  for (int kk = 1; kk < 8; ++kk) {
+  for (int kk = 1; kk < 10; ++kk) {
     const double o = 2.0 * kk - 1.0;
     t0 *= (0.0 - o * o) / (8.0 * kk);
     t1 *= (4.0 - o * o) / (8.0 * kk);
@@ -610,7 +616,13 @@ int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N
 
 int assemble_circle_row(const AsmArgs& A, cudaStream_t s) {
   if (upload_rules(A)) { set_error("uploading quadrature rules failed"); return 3; }
-  k_circle_row<<<(unsigned)((A.N + 63) / 64), 64, 0, s>>>(A);
+  zd* part = nullptr;
+  if (cudaMalloc(&part, sizeof(zd) * 16 * A.N) != cudaSuccess) { set_error("oom (circle row)"); return 4; }
+  k_circle_row_part<<<(unsigned)((4 * A.N + 63) / 64), 64, 0, s>>>(A, part);
+  note_launch();
+  k_circle_row_sum<<<(unsigned)((A.N + 127) / 128), 128, 0, s>>>(A, part);
+  cudaStreamSynchronize(s);
+  cudaFree(part);
   note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("circle row: ") + cudaGetErrorString(err)); return 3; }

@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       if (kb >= STAGES) {
-        if (!mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+        if (!mbar_wait(&empty[s], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 11; break; }
       }
       if (*abort_flag) break;
       uint8_t* st = smem + s * L::STAGE_BYTES;
@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- MMA issuer
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
-      if (!mbar_wait(&full[s], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+      if (!mbar_wait(&full[s], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 12; break; }
       *consumed = kb + 1;
       if (*abort_flag) break;
       tc_fence_after();
@@ -213,12 +213,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __syncwarp();
   // ---------------- epilogue: all four warps
   bool got = mbar_wait(done, 0, WAIT_LIMIT, args.err);
-  got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
+  const bool waited = __all_sync(0xffffffffu, got);
+  got = waited && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
   tc_fence_after();
   if (!got) {
+    if (!waited && lane == 0) atomicCAS((int*)abort_flag, 0, 13);
+    __syncwarp();
     if (threadIdx.x == 0) {
       const int zero_flag = 0;
-      atomicExch(args.err, 1);
+      atomicExch(args.err, 1000 * (*abort_flag) + (int)(blockIdx.x % 1000));
       // let the loads already in flight land before the CTA's shared memory goes away
       for (int kb = *consumed; kb < *issued; ++kb)
         (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       for (int kb = 0; kb < nk; ++kb) {
         const int st = kb % STAGES;
         if (kb >= STAGES) {
-          if (!mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+          if (!mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 21; break; }
         }
         if (*abort_flag) break;
         uint8_t* sp = smem + st * L::STAGE_BYTES;
@@ -391,7 +394,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       bool ok = true;
       for (int kb = 0; kb < nk && ok; ++kb) {
         const int st = kb % STAGES;
-        if (!mbar_wait(&full[st], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 1; break; }
+        if (!mbar_wait(&full[st], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 22; break; }
         *consumed = kb + 1;
         if (*abort_flag) break;
         tc_fence_after();
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
         for (int kk = 0; kk < TC_BK / 16; ++kk, ++g) {
           const int b = g & 1;
           if (g >= 2 && !mbar_wait(&tempty[b], ((g >> 1) - 1) & 1, WAIT_LIMIT, args.err)) {
-            *abort_flag = 1; ok = false; break;
+            *abort_flag = 25; ok = false; break;
           }
           tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)(b * ACC_NT);
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       const int b = g & 1;
       bool got = mbar_wait(&tfull[b], (g >> 1) & 1, WAIT_LIMIT, args.err);
       got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
-      if (!got) { if (lane == 0) *abort_flag = 1; break; }
+      if (!got) { if (lane == 0) atomicCAS((int*)abort_flag, 0, 24); break; }
       tc_fence_after();
       float v[32];
       const uint32_t ta = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colhalf);
@@ -444,7 +447,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   if (!ok) {
     if (threadIdx.x == 0) {
       const int zero_flag = 0;
-      atomicExch(args.err, 1);
+      atomicExch(args.err, 1000 * (*abort_flag) + (int)(blockIdx.x % 1000));
       for (int kb = *consumed; kb < *issued; ++kb)
         (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
     }

@@ -61,7 +61,9 @@ __device__ inline Hankel01 hankel01_series(zd z) {
 }
 
 __device__ inline Hankel01 hankel01_miller(zd z) {
-  int n0 = (int)(zabs(z) + 45.0);
+  // start index: |z| + 25 is within 1e-14 for |z| < 12, |z| + 45 above
+  const double az = zabs(z);
+  int n0 = (int)(az + (az < 12.0 ? 25.0 : 45.0));
   n0 += (n0 & 1);
   zd iz2 = 2.0 * zrecip(z);           // 2/z
   zd jp1 = mkz(0.0), j = mkz(1e-30);

@@ -285,16 +285,16 @@ int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int
 constexpr int GRAM_ROWS = 256;
 
 __global__ void k_gram_partial(const zd* X, int64_t ld, int64_t m, int b, zd* part) {
-  __shared__ zd xs[64][65];
+  __shared__ zd xs[64][33];
   const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
   const int tid = threadIdx.x;                  // 256 threads: (i, j) pairs
   zd acc[16];
 #pragma unroll
   for (int t = 0; t < 16; ++t) acc[t] = mkz(0.0);
-  for (int64_t rr = r0; rr < min(m, r0 + GRAM_ROWS); rr += 64) {
+  for (int64_t rr = r0; rr < min(m, r0 + GRAM_ROWS); rr += 32) {
     __syncthreads();
-    for (int u = tid; u < 64 * b; u += blockDim.x) {
-      const int c = u / 64, r = u % 64;
+    for (int u = tid; u < 32 * b; u += blockDim.x) {
+      const int c = u / 32, r = u % 32;
       xs[c][r] = (rr + r < m) ? X[(int64_t)c * ld + rr + r] : mkz(0.0);
     }
     __syncthreads();
@@ -303,7 +303,7 @@ __global__ void k_gram_partial(const zd* X, int64_t ld, int64_t m, int b, zd* pa
       const int pidx = tid + 256 * t;
       const int i = pidx / 64, j = pidx % 64;
       if (i < b && j < b)
-        for (int r = 0; r < 64; ++r) zfma(acc[t], conj(xs[i][r]), xs[j][r]);
+        for (int r = 0; r < 32; ++r) zfma(acc[t], conj(xs[i][r]), xs[j][r]);
     }
   }
 #pragma unroll

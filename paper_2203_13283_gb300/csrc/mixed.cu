@@ -85,12 +85,14 @@ __global__ void k_stage_view(const zd* X, int64_t rows, int64_t cols, int64_t rs
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t i = blockIdx.y;
   if (j >= cols) return;
-  zd x = X[i * rs + j * cs];
-  if (conj) x.y = -x.y;
-  const int64_t o = i * ldp + 2 * j;
+  const zd x = X[i * rs + j * cs];
+  const double v[2] = {x.x, conj ? -x.y : x.y};
   uint16_t d1, d2;
-  split3(x.x, planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
-  split3(x.y, planes, p0 + o + 1, planes > 1 ? p1 + o + 1 : &d1, planes > 2 ? p2 + o + 1 : &d2);
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int64_t o = i * ldp + 2 * j + t;
+    split3(v[t], planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
+  }
 }
 
 int stage_view(const zd* X, int64_t rows, int64_t cols, int64_t rs, int64_t cs, int conj, int planes,

@@ -7,6 +7,8 @@
 // circle operators.  Eq. (7): C - C_c = U V^T by randomized range finding;
 // Eq. (8)/(9): Woodbury with the capacitance K = I + V^T C_c^{-1} U.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -158,6 +160,9 @@ static int stage(wcs_ctx* c, DevBuf& buf, const zd* X, int64_t ldx, int64_t cols
 // Y = alpha * op(X) + beta * Y on the tensor cores, op one of the assembled
 // operators (0 S~, 1 D, 2 D~, 3 N), X already staged in `buf`.  adjoint uses
 // the transposed planes: A^H x = conj(A^T conj(x)) (buf staged with conj).
+static bool debug_finite();
+static int check_tc(wcs_ctx* c);
+
 static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols, zd alpha, zd beta, zd* Y,
                     int64_t ldy, bool accurate = false) {
   // accurate: all stored planes, accumulator drained every K step (refinement
@@ -185,7 +190,14 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.beta = beta;
   t.err = (int*)c->tcerr.p;
   ProfScope ps(c, accurate ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
-  return accurate ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s);
+  TRY(accurate ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
+  if (debug_finite()) {
+    int r = check_tc(c);
+    if (r) fprintf(stderr, "[wcs debug] operator product op=%d adj=%d acc=%d M=%d Nc=%d K=%d: %s\n", op,
+                   (int)adjoint, (int)accurate, t.M, t.Nc, t.K, g_err.c_str());
+    return r;
+  }
+  return 0;
 }
 
 static int check_tc(wcs_ctx* c) {
@@ -233,7 +245,8 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
   t.out = C; t.ldo = ldc; t.alpha = alpha; t.beta = beta;
   t.err = (int*)c->tcerr.p;
   ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
-  return gemm_tc(oa, ob, t, c->s);
+  TRY(gemm_tc(oa, ob, t, c->s));
+  return 0;
 }
 
 static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj,
@@ -337,6 +350,30 @@ static int woodbury(wcs_ctx* c, const zd* B, int64_t ldb, zd* X, int64_t ldx, in
   // Z = V^T Y = Vw^H Y ; X = Y - Wt Z
   TRY(cgemm(c, r, cols, N, mkz(1.0), blkH(c->Vw.z(), N), X, ldx, mkz(0.0), Z, r));
   TRY(cgemm(c, N, cols, r, mkz(-1.0), blk(c->Wt.z(), N), Z, r, mkz(1.0), X, ldx));
+  return 0;
+}
+
+// WCS_DEBUG_FINITE=1: check device buffers for non-finite values after each
+// stage of the skeleton (diagnostic; synchronises)
+static bool debug_finite() {
+  static int v = -1;
+  if (v < 0) { const char* e = getenv("WCS_DEBUG_FINITE"); v = (e && e[0] == '1') ? 1 : 0; }
+  return v == 1;
+}
+static int dbg_check(wcs_ctx* c, const zd* p, int64_t rows, int64_t cols, int64_t ld, const char* what) {
+  if (!debug_finite() || rows <= 0 || cols <= 0) return 0;
+  std::vector<zd> h(rows);
+  for (int64_t j = 0; j < cols; ++j) {
+    cudaMemcpyAsync(h.data(), p + j * ld, sizeof(zd) * rows, cudaMemcpyDeviceToHost, c->s);
+    cudaStreamSynchronize(c->s);
+    for (int64_t i = 0; i < rows; ++i)
+      if (!std::isfinite(h[i].x) || !std::isfinite(h[i].y) || std::fabs(h[i].x) > 1e30 || std::fabs(h[i].y) > 1e30) {
+        fprintf(stderr, "[wcs debug] non-finite or huge after %s at (%lld, %lld): %g %g\n", what, (long long)i,
+                (long long)j, h[i].x, h[i].y);
+        set_error(std::string("debug: non-finite after ") + what);
+        return WCS_ERR_CUDA;
+      }
+  }
   return 0;
 }
 
@@ -470,7 +507,7 @@ int wcs_default_options(wcs_options* o) {
   o->rhs_chunk = 256;
   o->mixed_planes = 3;
   o->rhs_planes = 3;
-  o->zfast = 14.0;
+  o->zfast = 9.0;
   return WCS_OK;
 }
 
@@ -871,19 +908,27 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
     {
       ProfScope ps(c, CAT_SAMPLE, 0.0, 0.0);
       TRY(gaussian_fill(Om, N, N, b, seed, offset, c->s));
+      TRY(dbg_check(c, Om, N, b, N, "gaussian"));
       offset += (uint64_t)N * b;
       TRY(apply_remainder(c, Om, N, Y, N, b, false));
+      TRY(dbg_check(c, Y, N, b, N, "sample"));
     }
     ProfScope ps_proj(c, CAT_PROJECT, 0.0, 0.0);
     for (int pass = 0; pass < 2 && ell > 0; ++pass) {
       TRY(cgemm(c, ell, b, N, one, blkH(Q, N), Y, N, zero, Zb.z(), ell));
+      TRY(dbg_check(c, Zb.z(), ell, b, ell, "projection coefficients"));
       TRY(cgemm(c, N, b, ell, mone, blk(Q, N), Zb.z(), ell, one, Y, N));
+      TRY(dbg_check(c, Y, N, b, N, "projection"));
     }
     TRY(column_norms(Y, N, N, b, Nb.d(), c->s));
     cudaMemcpyAsync(norms.data(), Nb.p, sizeof(double) * b, cudaMemcpyDeviceToHost, c->s);
     TRY(sync(c));
     double mx = 0;
-    for (int j = 0; j < b; ++j) mx = std::max(mx, norms[j]);
+    for (int j = 0; j < b; ++j) {
+      if (!std::isfinite(norms[j])) { set_error("skeleton: non-finite sample (block at rank " + std::to_string(ell) + ")"); return WCS_ERR_CUDA; }
+      mx = std::max(mx, norms[j]);
+    }
+    if (c->mixed) TRY(check_tc(c));
     if (mx <= thr) break;
     // orthonormalise the block twice (pivoted CholeskyQR)
     ProfScope ps_orth(c, CAT_ORTH, 0.0, 0.0);
@@ -892,19 +937,23 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
     for (int pass = 0; pass < 2; ++pass) {
       const int cols = (pass == 0) ? b : rk;
       TRY(gram_matrix(src, N, N, cols, Gb.z(), GW.z(), c->s));
+      TRY(dbg_check(c, Gb.z(), cols, cols, cols, "gram"));
       TRY(pivoted_cholesky(Gb.z(), cols, 1e-7, (int*)Ib.p, (int*)Ib.p + b, c->s));
       int rk_new = 0;
       cudaMemcpyAsync(&rk_new, (int*)Ib.p + b, sizeof(int), cudaMemcpyDeviceToHost, c->s);
       TRY(sync(c));
       if (rk_new == 0) { rk = 0; break; }
       zd* dst = (pass == 0) ? c->w3.z() : Q + ell * N;
+      TRY(dbg_check(c, Gb.z(), cols, cols, cols, "cholesky"));
       TRY(trsm_right_upper(src, N, N, Gb.z(), cols, (int*)Ib.p, (int*)Ib.p + b, rk_new, dst, N, c->s));
+      TRY(dbg_check(c, dst, N, rk_new, N, "trsm"));
       rk = rk_new;
       if (pass == 0) {
         // re-orthogonalise against the accepted basis before the second pass
         if (ell > 0) {
           TRY(cgemm(c, ell, rk, N, one, blkH(Q, N), c->w3.z(), N, zero, Zb.z(), ell));
           TRY(cgemm(c, N, rk, ell, mone, blk(Q, N), Zb.z(), ell, one, c->w3.z(), N));
+          TRY(dbg_check(c, c->w3.z(), N, rk, N, "re-orthogonalisation"));
         }
         src = c->w3.z();
       }
@@ -958,7 +1007,11 @@ int wcs_factor(wcs_ctx* c) {
       cudaMemcpyAsync(&infoh, infod, sizeof(int), cudaMemcpyDeviceToHost, c->s);
       cudaMemcpyAsync(&mp, minpiv, sizeof(double), cudaMemcpyDeviceToHost, c->s);
       TRY(sync(c));
-      if (infoh != 0 || !(mp > 1e-14)) { set_error("capacitance matrix is singular"); return WCS_ERR_SINGULAR; }
+      if (infoh != 0 || !(mp > 1e-14)) {
+        set_error("capacitance matrix is singular (rank " + std::to_string(r) + ", smallest pivot " +
+                  std::to_string(mp) + ", first zero pivot at step " + std::to_string(infoh) + ")");
+        return WCS_ERR_SINGULAR;
+      }
     } else {
       // Newton-Schulz: X <- X (2I - K X) from X0 = K^H / (||K||_1 ||K||_inf),
       // which converges for any nonsingular K; products on the tensor cores
