@@ -213,8 +213,11 @@ int wcs_farfield(wcs_ctx* ctx, int64_t B, const double* j_dev, int64_t ldj, int 
  * bf16 terms (1: bf16, 2: ~16 bits, 3: ~24 bits) and every product of
  * combined order < planes is accumulated in FP32 in tensor memory.  This is
  * the contraction behind the mixed-precision operator products of Eq. (5)-(7).
- * Allocates its own staging buffers; ordered on `stream`; synchronises.
- * Returns WCS_ERR_TIMEOUT if a bounded device wait expired. */
+ * When the output tiles cannot fill the GPU (few rows and columns, long K)
+ * and accurate == 0, K is split over the grid and the FP32 partials are summed
+ * in FP64 in a fixed order; the split depends on the shape alone, so results
+ * are reproducible.  Allocates its own staging buffers; ordered on `stream`;
+ * synchronises.  Returns WCS_ERR_TIMEOUT if a bounded device wait expired. */
 int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
                         const double* B_dev, int64_t ldb, int planes, double* D_dev, int64_t ldd,
                         void* stream);
@@ -232,10 +235,11 @@ int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A_dev
  * cudaMalloc (a real-time loop running on a frozen memory pool, a plug-in
  * whose host application owns all device memory, code between two
  * synchronisation points that must not allocate).  Same arguments and result
- * as wcs_gemm_split_bf16; the staging planes and the error flag live in one
- * file-scope device array of 32 MiB that every GPU loading the library holds
- * until the process exits.  Sizes with (M + Nc) * ceil64(K) * planes * 2 bytes
- * above that limit are rejected with WCS_ERR_ARG.  The first call on a device
+ * as wcs_gemm_split_bf16; the staging planes, the split-K partials and the
+ * error flag live in one file-scope device array of 32 MiB that every GPU
+ * loading the library holds until the process exits.  Sizes whose
+ * (M + Nc) * ceil64(K) * planes * 2 bytes plus split-K partials exceed that
+ * limit are rejected with WCS_ERR_ARG.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress); make that first
  * call before any stream capture.  All calls share the array: calls whose GPU
  * work overlaps (other streams, other host threads) race on it.  Each call

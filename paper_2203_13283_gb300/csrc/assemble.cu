@@ -38,6 +38,16 @@ __device__ __forceinline__ int periodic_dist(int64_t e, int64_t f, int64_t N) {
 // i/4 * H
 __device__ __forceinline__ zd i4(zd H) { return mkz(-0.25 * H.y, 0.25 * H.x); }
 
+// Hankel functions at k R and k~ R
+__device__ __forceinline__ void hankel_k_kt(const AsmArgs& A, double R, Hankel01& Hk, Hankel01& Ht) {
+  if (A.kt_pair) {
+    hankel01_pair(A.k * R, A.ktp, Hk, Ht);
+  } else {
+    Hk = hankel01(mkz(A.k * R));
+    Ht = hankel01(A.kt * R);
+  }
+}
+
 __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& o) {
 #pragma unroll
   for (int op = 0; op < 4; ++op)
@@ -60,8 +70,8 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
         const double R = sqrt(dx * dx + dy * dy);
         const double gg = (dx * nxs + dy * nys) / R;
         const double nd = nxt * nxs + nyt * nys;
-        Hankel01 Hk = hankel01(mkz(k * R));
-        Hankel01 Ht = hankel01(kt * R);
+        Hankel01 Hk, Ht;
+        hankel_k_kt(A, R, Hk, Ht);
         const zd gk = i4(Hk.H0);
         const zd gt = i4(Ht.H0);
         const zd dgk = (k * gg) * i4(Hk.H1);
@@ -118,8 +128,8 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
         } else {
           const double R = sqrt(dx * dx + dy * dy);
           const double gg = (dx * nxs + dy * nys) / R;
-          Hankel01 Hk = hankel01(mkz(k * R));
-          Hankel01 Ht = hankel01(kt * R);
+          Hankel01 Hk, Ht;
+          hankel_k_kt(A, R, Hk, Ht);
           kN = i4(Hk.H0);
           kS = i4(Ht.H0);
           kD = (k * gg) * i4(Hk.H1);
@@ -207,21 +217,24 @@ __device__ void pair_fast(const AsmArgs& A, int64_t e, int64_t f, PairOut& out) 
 __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& out) {
   const int q = A.q_far;
   const double dx0 = A.cx[e] - A.cx[f], dy0 = A.cy[e] - A.cy[f];
-  const double R0 = sqrt(dx0 * dx0 + dy0 * dy0);
+  // R0 from an FP32 square root and one Newton step in FP64 (relative error
+  // ~1e-15, enough for the phase k R0 ~ 1e4); the FP64 work per pair stays a
+  // handful of operations
+  const double r2 = fma(dx0, dx0, dy0 * dy0);
+  const float sf = sqrtf((float)r2);
+  const double R0 = (double)sf + fma(-(double)sf, (double)sf, r2) * (double)(0.5f / sf);
   const double kR0 = A.k * R0;
   const double twopi_hi = 6.283185307179586, twopi_lo = 2.4492935982947064e-16;
   const double nrev = rint(kR0 * (1.0 / twopi_hi));
   const float ph0 = (float)fma(-nrev, twopi_lo, fma(-nrev, twopi_hi, kR0));
   const float fdx0 = (float)dx0, fdy0 = (float)dy0, fR0 = (float)R0;
-  const float k = (float)A.k, beta = (float)A.kt.y;
-  // sqrt(2/(pi k~)) and i/k~ for the complex wavenumber
-  const zd ckd = zsqrt((2.0 / WCS_PI) * zrecip(A.kt));
-  const zd ikd = zrecip(A.kt);
-  const cf ck = {(float)ckd.x, (float)ckd.y};
-  const cf ik = {(float)(-ikd.y), (float)ikd.x};           // i / k~
-  const cf kt4 = {(float)(-0.25 * A.kt.y), (float)(0.25 * A.kt.x)};  // i k~ / 4
-  const float ampk = sqrtf((float)(2.0 / (WCS_PI * A.k)));
-  const float kk2h2 = (float)(A.k * A.k * A.h * A.h);
+  const FastConsts& F = A.fk;
+  const float k = F.kf, beta = F.beta;
+  const cf ck = {F.ck[0], F.ck[1]};      // sqrt(2 / (pi k~))
+  const cf ik = {F.ik[0], F.ik[1]};      // i / k~
+  const cf kt4 = {F.kt4[0], F.kt4[1]};   // i k~ / 4
+  const float ampk = F.ampk;             // sqrt(2 / (pi k))
+  const float kk2h2 = F.kk2h2;
   cf v[4][4];
 #pragma unroll
   for (int op = 0; op < 4; ++op)
@@ -298,7 +311,7 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
         }
     }
   }
-  const float h2 = (float)(A.h * A.h);
+  const float h2 = F.h2;
 #pragma unroll
   for (int op = 0; op < 4; ++op)
 #pragma unroll
@@ -307,8 +320,8 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
 
 __device__ __forceinline__ bool fast_ok(const AsmArgs& A, int64_t e, int64_t f) {
   if (periodic_dist(e, f, A.N) <= A.near_band) return false;
-  const double dx0 = A.cx[e] - A.cx[f], dy0 = A.cy[e] - A.cy[f];
-  return A.k * sqrt(dx0 * dx0 + dy0 * dy0) >= A.zfast;
+  const float dx0 = (float)(A.cx[e] - A.cx[f]), dy0 = (float)(A.cy[e] - A.cy[f]);
+  return A.fk.kf * A.fk.kf * (dx0 * dx0 + dy0 * dy0) >= A.fk.zfast2;
 }
 
 __device__ __forceinline__ void pair_any(const AsmArgs& A, int64_t e, int64_t f, PairOut& o) {
@@ -475,6 +488,20 @@ __device__ __forceinline__ void split_store(double x, int planes, uint16_t* cons
   }
 }
 
+// FP32 values: x - hi and (x - hi) - mid are exact in FP32, so the planes
+// equal those of split_store((double)x)
+__device__ __forceinline__ void split_store_f(float x, int planes, uint16_t* const* P, int64_t off) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+  float r = x - __bfloat162float(h0);
+  P[0][off] = __bfloat16_as_ushort(h0);
+  if (planes > 1) {
+    const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
+    r -= __bfloat162float(h1);
+    P[1][off] = __bfloat16_as_ushort(h1);
+    if (planes > 2) P[2][off] = __bfloat16_as_ushort(__float2bfloat16_rn(r));
+  }
+}
+
 static int upload_hankel_coefficients() {
   float a0[10], a1[10];
   double t0 = 1.0, t1 = 1.0;
@@ -557,7 +584,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_
     const int li = rem / TILE, lj = rem - (rem / TILE) * TILE;
     if (i0 + li < N && j0 + lj < N) {
       const cf v = acc[(op * TILE + li) * TILE + lj];
-      split_store(comp ? v.y : v.x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
+      split_store_f(comp ? v.y : v.x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
     }
   }
   for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
@@ -566,7 +593,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_
     const int lj = rem / TILE, li = rem - (rem / TILE) * TILE;
     if (i0 + li < N && j0 + lj < N) {
       const cf v = acc[(op * TILE + li) * TILE + lj];
-      split_store(comp ? v.y : v.x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
+      split_store_f(comp ? v.y : v.x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
     }
   }
 }

@@ -18,6 +18,15 @@ struct __align__(8) zf {
   float x, y;
 };
 
+// k~ = k (1 + i t): per-run constants for evaluating both wavenumbers of a
+// point pair from one real argument x = k R.
+struct KtPair {
+  double t = 0.0;
+  zd c1;   // 1 / (1 + i t)
+  zd c2;   // (1 + i t)^(-1/2), principal branch
+};
+
+
 __host__ __device__ __forceinline__ zd mkz(double a, double b = 0.0) { zd r; r.x = a; r.y = b; return r; }
 __host__ __device__ __forceinline__ zd operator+(zd a, zd b) { return mkz(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ zd operator-(zd a, zd b) { return mkz(a.x - b.x, a.y - b.y); }

@@ -19,6 +19,8 @@
 // MMAs, frees TMEM and returns, so the host sees WCS_ERR_TIMEOUT.
 #include <cuda.h>
 
+#include <algorithm>
+
 #include "gemm_tc.h"
 
 namespace wcs {
@@ -140,7 +142,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * TC_BM;
   const int n0 = blockIdx.x * NT;
-  const int nk = (args.K + TC_BK - 1) / TC_BK;
+  // split-K: CTA z takes k-blocks [z kper, (z + 1) kper); the host picks kper
+  // so that every split is non-empty
+  const int nk_all = (args.K + TC_BK - 1) / TC_BK;
+  const int kb0 = (args.kper > 0) ? (int)blockIdx.z * args.kper : 0;
+  const int nk = (args.kper > 0) ? min(args.kper, nk_all - kb0) : nk_all;
 
   if (*(volatile int*)args.err != 0) return;  // another CTA already gave up: do nothing
   if (threadIdx.x == 0) {
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (*abort_flag) break;
       uint8_t* st = smem + s * L::STAGE_BYTES;
       mbar_expect_tx(&full[s], L::STAGE_BYTES);
-      const int k0 = kb * TC_BK;
+      const int k0 = (kb0 + kb) * TC_BK;
 #pragma unroll
       for (int p = 0; p < PA; ++p) tma_load_2d(st + p * L::A_BYTES, mapA[p], &full[s], k0, m0);
 #pragma unroll
@@ -232,7 +238,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int c0 = 0; c0 < NT; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      epilogue_store(args, row, n0 + c0, v);
+      if (args.ws) {
+        // split-K partial, column-major [split][Nc][M]: a warp writes 32 consecutive rows per column
+        if (row < args.M) {
+          float* w = args.ws + (int64_t)blockIdx.z * args.Nc * args.M + row;
+#pragma unroll
+          for (int i = 0; i < 32; ++i)
+            if (n0 + c0 + i < args.Nc) w[(int64_t)(n0 + c0 + i) * args.M] = v[i];
+        }
+      } else {
+        epilogue_store(args, row, n0 + c0, v);
+      }
     }
   }
   tc_fence_before();
@@ -291,12 +307,43 @@ static int launch_tc(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaS
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
     attr = true;
   }
-  dim3 grid((unsigned)((args.Nc + NT - 1) / NT), (unsigned)((args.M + TC_BM - 1) / TC_BM));
+  const int nk = (args.K + TC_BK - 1) / TC_BK;
+  const int splits = (args.kper > 0) ? (nk + args.kper - 1) / args.kper : 1;
+  dim3 grid((unsigned)((args.Nc + NT - 1) / NT), (unsigned)((args.M + TC_BM - 1) / TC_BM), (unsigned)splits);
   kern<<<grid, TC_THREADS, L::TOTAL, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], args);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) { set_error(std::string("gemm_tc launch: ") + cudaGetErrorString(e)); return 3; }
   return 0;
+}
+
+// Sum of the split-K partials in a fixed order (FP64) and the epilogue.
+__global__ void k_splitk_reduce(TcArgs a, int splits) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t plane = (int64_t)a.Nc * a.M;
+  if (a.epi == EPI_RAW_F64) {
+    if (t >= plane) return;
+    const int row = (int)(t % a.M), col = (int)(t / a.M);
+    double sum = 0.0;
+    for (int z = 0; z < splits; ++z) sum += (double)a.ws[z * plane + t];
+    double* o = (double*)a.out + (int64_t)row * a.ldo + col;
+    *o = a.alpha.x * sum + ((a.beta.x == 0.0) ? 0.0 : a.beta.x * (*o));
+    return;
+  }
+  const int ncols = a.Nc / 2;
+  if (t >= (int64_t)a.M * ncols) return;
+  const int row = (int)(t % a.M), j = (int)(t / a.M);
+  const float* w = a.ws + (int64_t)(2 * j) * a.M + row;
+  double re = 0.0, im = 0.0;
+  for (int z = 0; z < splits; ++z) {
+    re += (double)w[z * plane];
+    im += (double)w[z * plane + a.M];
+  }
+  zd p = mkz(re, a.conj_out ? -im : im);
+  p = a.alpha * p;
+  zd* o = (zd*)a.out + (int64_t)j * a.ldo + row;
+  if (!(a.beta.x == 0.0 && a.beta.y == 0.0)) p += a.beta * (*o);
+  *o = p;
 }
 
 
@@ -503,6 +550,25 @@ int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaSt
   return 1;
 }
 
+int gemm_tc_split_plan(int M, int Nc, int K, int planesA, int planesB, int epi, int64_t* ws_elems) {
+  *ws_elems = 0;
+  if (M <= 0 || Nc <= 0 || K <= 0) return 0;
+  if (!(epi == EPI_RAW_F64 || (epi == EPI_CPLX_F64 && (Nc % 2) == 0))) return 0;
+  const int NT = ((planesA == 3 && planesB == 3) || Nc <= 128) ? 128 : 256;
+  const int nk = (K + TC_BK - 1) / TC_BK;
+  const int64_t ctas = (int64_t)((Nc + NT - 1) / NT) * ((M + TC_BM - 1) / TC_BM);
+  if (ctas >= 152 || nk < 8) return 0;
+  int64_t want = (2 * 152 + ctas - 1) / ctas;
+  want = std::min<int64_t>(want, nk / 4);
+  // at most 64 MB of partials
+  want = std::min<int64_t>(want, ((int64_t)1 << 24) / ((int64_t)Nc * M));
+  if (want <= 1) return 0;
+  const int kper = (int)((nk + want - 1) / want);
+  const int splits = (nk + kper - 1) / kper;   // <= want, every split non-empty
+  *ws_elems = (int64_t)splits * Nc * M;
+  return kper;
+}
+
 int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s) {
   if (args.M <= 0 || args.Nc <= 0 || args.K <= 0) return 0;
   if (args.nprod < 1 || args.nprod > 6) { set_error("gemm_tc: 1..6 products"); return 1; }
@@ -511,12 +577,37 @@ int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s)
     if (args.ia[p] >= A.planes || args.ib[p] >= B.planes) { set_error("gemm_tc: plane index"); return 1; }
   if ((args.M + TC_BM - 1) / TC_BM > 65535) { set_error("gemm_tc: M too large"); return 1; }
   const int key = A.planes * 10 + B.planes;
+  const int NT = (key == 33 || args.Nc <= 128) ? 128 : 256;
+  // split-K when the output tiles cannot fill the GPU (tall-K products such
+  // as Q^H Y with few rows); needs the caller's FP32 workspace
+  float* ws = args.ws;
+  args.ws = nullptr;
+  args.kper = 0;
+  int splits = 1;
+  if (ws) {
+    int64_t need = 0;
+    const int kper = gemm_tc_split_plan(args.M, args.Nc, args.K, A.planes, B.planes, args.epi, &need);
+    if (kper > 0 && need <= args.ws_elems) {
+      args.kper = kper;
+      args.ws = ws;
+      const int nk = (args.K + TC_BK - 1) / TC_BK;
+      splits = (nk + kper - 1) / kper;
+    }
+  }
+  int r = 0;
   switch (key) {
-    case 11: return launch_tc<256, 1, 1, 4>(A, B, args, s);
-    case 22: return launch_tc<256, 2, 2, 2>(A, B, args, s);
-    case 33: return launch_tc<128, 3, 3, 2>(A, B, args, s);
+    case 11: r = (NT == 128) ? launch_tc<128, 1, 1, 4>(A, B, args, s) : launch_tc<256, 1, 1, 4>(A, B, args, s); break;
+    case 22: r = (NT == 128) ? launch_tc<128, 2, 2, 3>(A, B, args, s) : launch_tc<256, 2, 2, 2>(A, B, args, s); break;
+    case 33: r = launch_tc<128, 3, 3, 2>(A, B, args, s); break;
     default: set_error("gemm_tc: plane combination not built"); return 1;
   }
+  if (r || splits == 1) return r;
+  const int64_t n = (int64_t)args.M * ((args.epi == EPI_RAW_F64) ? args.Nc : args.Nc / 2);
+  k_splitk_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(args, splits);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("split-K reduce: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
 }
 
 }  // namespace wcs

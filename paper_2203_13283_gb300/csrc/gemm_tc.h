@@ -30,6 +30,11 @@ struct TcArgs {
   int64_t ldo = 0;
   zd alpha = {1.0, 0.0}, beta = {0.0, 0.0};
   int* err = nullptr;    // device flag set to 1 when a bounded wait expires
+  // optional FP32 workspace for split-K (complex epilogue only); gemm_tc
+  // splits K when the output tiles cannot fill the GPU and ws_elems allows
+  float* ws = nullptr;
+  int64_t ws_elems = 0;
+  int kper = 0;          // set by gemm_tc: k-blocks per split (0: no split)
 };
 
 #define TRY_TC(x)          \
@@ -71,6 +76,11 @@ __device__ __forceinline__ void epilogue_store(const TcArgs& a, int row, int col
 }
 
 int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s);
+// Split-K plan of gemm_tc for a shape: k-blocks per split (0: no split) and
+// the FP32 workspace it needs.  gemm_tc splits exactly when args.ws is set
+// and args.ws_elems >= that need, so two callers that provide the need get
+// identical results.
+int gemm_tc_split_plan(int M, int Nc, int K, int planesA, int planesB, int epi, int64_t* ws_elems);
 // Same contraction with the accumulator drained every K = 16 step into
 // compensated FP32 registers (accuracy ~1e-7 independent of K).
 int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s);

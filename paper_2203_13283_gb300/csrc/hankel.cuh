@@ -147,6 +147,182 @@ __device__ inline Hankel01 hankel01_asymptotic(zd z) {
   return r;
 }
 
+// ---------------------------------------------------------------------------
+// Both wavenumbers of a point pair from one real evaluation.  k~ = k + i beta
+// (Sec. III) has Re k~ = k, so the two arguments are x = k R and x (1 + i t)
+// with t = beta / k.  J0, J1, Y0, Y1 are evaluated at the real x in real
+// arithmetic and carried to x + i y (y = x t) by their Taylor series in i y.
+// The derivatives follow from Bessel's equation (DLMF 10.2.1) differentiated
+// m times,
+//     x f^(m+2) = -(m+1) f^(m+1) - x f^(m) - m f^(m-1)      (f = J0 or Y0),
+// with J1 = -J0', Y1 = -Y0' (DLMF 10.6.3).  The terms fall like t^m for every
+// x (Y0's branch point is at distance x), so the form is used for t <= 0.1.
+// Large x uses the Hankel expansion of both with one shared sincos.
+// ---------------------------------------------------------------------------
+__constant__ double c_recip[72] = {
+    0.0, 1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7,
+    1.0 / 8, 1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15,
+    1.0 / 16, 1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23,
+    1.0 / 24, 1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31,
+    1.0 / 32, 1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39,
+    1.0 / 40, 1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47,
+    1.0 / 48, 1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55,
+    1.0 / 56, 1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63,
+    1.0 / 64, 1.0 / 65, 1.0 / 66, 1.0 / 67, 1.0 / 68, 1.0 / 69, 1.0 / 70, 1.0 / 71,
+};
+
+struct Bessel01 {
+  double J0, J1, Y0, Y1;
+};
+
+__device__ inline Bessel01 bessel01_series_real(double x) {
+  // the ascending series of hankel01_series for real x
+  const double q = -0.25 * x * x;
+  double t0 = 1.0, t1 = 1.0, J0 = 1.0, J1s = 1.0, S0 = 0.0, T1 = 1.0 - 2.0 * WCS_EULER_GAMMA, H = 0.0;
+  for (int m = 1; m < 40; ++m) {
+    const double rm = c_recip[m], rm1 = c_recip[m + 1];
+    t0 *= q * (rm * rm);
+    t1 *= q * (rm * rm1);
+    H += rm;
+    J0 += t0;
+    J1s += t1;
+    S0 -= H * t0;
+    T1 += (2.0 * H + rm1 - 2.0 * WCS_EULER_GAMMA) * t1;
+    if (fabs(t0) < 1e-18 * fabs(J0) && fabs(t1) < 1e-18 * fabs(J1s)) break;
+  }
+  const double hz = 0.5 * x, lz = log(hz);
+  Bessel01 b;
+  b.J0 = J0;
+  b.J1 = hz * J1s;
+  b.Y0 = (2.0 / WCS_PI) * ((lz + WCS_EULER_GAMMA) * J0 + S0);
+  b.Y1 = (-2.0 / WCS_PI) / x + (2.0 / WCS_PI) * lz * b.J1 - (1.0 / WCS_PI) * hz * T1;
+  return b;
+}
+
+__device__ inline Bessel01 bessel01_miller_real(double x) {
+  // the backward recurrence of hankel01_miller for real x; the threads that
+  // run this branch together start at their largest index, which keeps the
+  // loop (and the reciprocal-table reads) uniform across the warp
+  int n0 = (int)(x + (x < 12.0 ? 25.0 : 45.0));
+  n0 += (n0 & 1);
+  n0 = __reduce_max_sync(__activemask(), n0);
+  const double iz2 = 2.0 / x;
+  double jp1 = 0.0, j = 1e-30, norm = 0.0, s0 = 0.0, s1 = 0.0, J1 = 0.0;
+  for (int n = n0; n > 0; --n) {
+    if ((n & 1) == 0) {
+      const int k = n >> 1;
+      const double r = (k & 1) ? -c_recip[k] : c_recip[k];
+      norm += 2.0 * j;
+      s0 += r * j;
+    } else {
+      const int kp = (n + 1) >> 1, km = (n - 1) >> 1;
+      s1 += ((kp & 1) ? -c_recip[kp] : c_recip[kp]) * j;
+      if (km >= 1) s1 -= ((km & 1) ? -c_recip[km] : c_recip[km]) * j;
+      if (n == 1) J1 = j;
+    }
+    const double jm = ((double)n * iz2) * j - jp1;
+    jp1 = j;
+    j = jm;
+  }
+  norm += j;
+  const double inv = 1.0 / norm;
+  Bessel01 b;
+  b.J0 = j * inv;
+  b.J1 = J1 * inv;
+  const double lz = log(0.5 * x) + WCS_EULER_GAMMA;
+  b.Y0 = (2.0 / WCS_PI) * (lz * b.J0 - 2.0 * (s0 * inv));
+  b.Y1 = (2.0 / WCS_PI) * (lz * b.J1 - b.J0 * (0.5 * iz2) + s1 * inv);
+  return b;
+}
+
+// J0, J1, Y0, Y1 at z = x + i y from their values at x (Taylor series in i y)
+__device__ inline Hankel01 bessel01_shift(double x, double y, const Bessel01& b) {
+  const double ix = 1.0 / x;
+  double fm1 = 0.0, f0 = b.J0, f1 = -b.J1;   // J0^(m-1), J0^(m), J0^(m+1)
+  double gm1 = 0.0, g0 = b.Y0, g1 = -b.Y1;   // same for Y0
+  zd J0 = mkz(b.J0), J1 = mkz(b.J1), Y0 = mkz(b.Y0), Y1 = mkz(b.Y1);
+  zd c = mkz(1.0);                           // (i y)^(m+1) / (m+1)! after the update
+  for (int m = 0; m < 64; ++m) {
+    const double f2 = -((double)(m + 1) * f1 + x * f0 + (double)m * fm1) * ix;
+    const double g2 = -((double)(m + 1) * g1 + x * g0 + (double)m * gm1) * ix;
+    c = mkz(-c.y * y, c.x * y) * c_recip[m + 1];
+    J0 += c * f1;
+    Y0 += c * g1;
+    J1 -= c * f2;
+    Y1 -= c * g2;
+    fm1 = f0; f0 = f1; f1 = f2;
+    gm1 = g0; g0 = g1; g1 = g2;
+    const double tm = (fabs(c.x) + fabs(c.y)) * (fabs(f0) + fabs(g0) + fabs(f1) + fabs(g1));
+    const double vm = fabs(J0.x) + fabs(J0.y) + fabs(Y0.x) + fabs(Y0.y) + fabs(J1.x) + fabs(J1.y) +
+                      fabs(Y1.x) + fabs(Y1.y);
+    if (m >= 1 && tm < 1e-17 * vm) break;
+  }
+  Hankel01 r;
+  r.J0 = J0; r.J1 = J1;
+  r.H0 = mkz(J0.x - Y0.y, J0.y + Y0.x);
+  r.H1 = mkz(J1.x - Y1.y, J1.y + Y1.x);
+  return r;
+}
+
+// Hankel expansion (DLMF 10.17.5) at x and at x (1 + i t) sharing sin/cos of
+// x - pi/4: exp(i(z - pi/4)) = exp(i(x - pi/4)) exp(-x t),
+// sqrt(2/(pi z)) = sqrt(2/(pi x)) (1 + i t)^(-1/2), i/z = (i/x) / (1 + i t).
+__device__ inline void hankel01_asymptotic_pair(double x, const KtPair& kp, Hankel01& hk, Hankel01& ht) {
+  const double ix = 1.0 / x;
+  const zd w = mkz(0.0, ix);                          // i / x
+  const zd wt = mkz(-kp.c1.y * ix, kp.c1.x * ix);     // i / z
+  zd s0 = mkz(1.0), s1 = mkz(1.0), t0 = mkz(1.0), t1 = mkz(1.0);
+  zd u0 = mkz(1.0), u1 = mkz(1.0), v0 = mkz(1.0), v1 = mkz(1.0);
+  bool r0 = true, r1 = true, q0 = true, q1 = true;
+  for (int k = 1; k < 48 && (r0 || r1 || q0 || q1); ++k) {
+    const double o = (double)(2 * k - 1);
+    const double a0 = (-o * o) * (0.125 * c_recip[k]), a1 = (4.0 - o * o) * (0.125 * c_recip[k]);
+    if (r0) {
+      const zd tn = t0 * w * a0;
+      if (abs2(tn) > abs2(t0)) r0 = false;
+      else { t0 = tn; s0 += tn; if (abs2(tn) < 1e-36 * abs2(s0)) r0 = false; }
+    }
+    if (r1) {
+      const zd tn = t1 * w * a1;
+      if (abs2(tn) > abs2(t1)) r1 = false;
+      else { t1 = tn; s1 += tn; if (abs2(tn) < 1e-36 * abs2(s1)) r1 = false; }
+    }
+    if (q0) {
+      const zd tn = v0 * wt * a0;
+      if (abs2(tn) > abs2(v0)) q0 = false;
+      else { v0 = tn; u0 += tn; if (abs2(tn) < 1e-36 * abs2(u0)) q0 = false; }
+    }
+    if (q1) {
+      const zd tn = v1 * wt * a1;
+      if (abs2(tn) > abs2(v1)) q1 = false;
+      else { v1 = tn; u1 += tn; if (abs2(tn) < 1e-36 * abs2(u1)) q1 = false; }
+    }
+  }
+  double sn, cs;
+  sincos(x - 0.25 * WCS_PI, &sn, &cs);
+  const double amp = sqrt((2.0 / WCS_PI) * ix);
+  const zd f = mkz(amp * cs, amp * sn);
+  const zd ft = (f * kp.c2) * exp(-x * kp.t);
+  hk.H0 = f * s0;
+  zd h1 = f * s1;
+  hk.H1 = mkz(h1.y, -h1.x);
+  ht.H0 = ft * u0;
+  h1 = ft * u1;
+  ht.H1 = mkz(h1.y, -h1.x);
+  hk.J0 = hk.J1 = ht.J0 = ht.J1 = mkz(0.0);
+}
+
+// H0, H1 (and J0, J1 below the expansion range) at k R = x and at k~ R
+__device__ inline void hankel01_pair(double x, const KtPair& kp, Hankel01& hk, Hankel01& ht) {
+  if (x > 17.0) { hankel01_asymptotic_pair(x, kp, hk, ht); return; }
+  const Bessel01 b = (x <= 2.0) ? bessel01_series_real(x) : bessel01_miller_real(x);
+  hk.J0 = mkz(b.J0);
+  hk.J1 = mkz(b.J1);
+  hk.H0 = mkz(b.J0, b.Y0);
+  hk.H1 = mkz(b.J1, b.Y1);
+  ht = bessel01_shift(x, x * kp.t, b);
+}
+
 // Full evaluation.  want_J: also return J0, J1 (only used for small |z|,
 // where the log-singular split of the near-field quadrature needs them).
 __device__ inline Hankel01 hankel01(zd z) {

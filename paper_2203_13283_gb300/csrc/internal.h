@@ -55,10 +55,23 @@ void gauss_legendre01(int n, double* x, double* w);
 void build_quad_tables(QuadTables& q);
 
 // ---------------------------------------------------------------- assembly
+// FP32 constants of the far-pair path, formed once on the host
+struct FastConsts {
+  float kf = 0.f, beta = 0.f;      // k, Im k~
+  float ck[2] = {0.f, 0.f};        // sqrt(2 / (pi k~))
+  float ik[2] = {0.f, 0.f};        // i / k~
+  float kt4[2] = {0.f, 0.f};       // i k~ / 4
+  float ampk = 0.f;                // sqrt(2 / (pi k))
+  float kk2h2 = 0.f, h2 = 0.f;     // k^2 h^2, h^2
+  float zfast2 = 0.f;              // zfast^2 (pair test k^2 |c_e - c_f|^2 >= zfast^2)
+};
+
 struct AsmArgs {
   int64_t N;
   double h, k;
   zd kt;
+  int kt_pair = 0;                 // 1: both wavenumbers from one real evaluation (k~ = k (1 + i t))
+  KtPair ktp;
   int q_far, q_near, near_band;
   Points far, near;                // point tables (far: q_far per element, near: q_near)
   const double* wlog;              // 3 * q_near^2 product weights (device)
@@ -76,6 +89,7 @@ struct AsmArgs {
   const float *ox = nullptr, *oy = nullptr;      // far points minus their element centre
   const float *nxf = nullptr, *nyf = nullptr;    // far-point normals (FP32)
   double zfast = 1e300;
+  FastConsts fk;
   const uint8_t* tile_flags = nullptr;           // mixed tile kernel: only flagged tiles
 };
 int assemble_dense(const AsmArgs& a, cudaStream_t s);

@@ -58,10 +58,16 @@ extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, con
   const int64_t ldp = ((K + 63) / 64) * 64;
   const size_t bytesA = sizeof(uint16_t) * (size_t)ldp * M * planes;
   const size_t bytesB = sizeof(uint16_t) * (size_t)ldp * Nc * planes;
-  const size_t need = ((bytesA + 255) / 256) * 256 + ((bytesB + 255) / 256) * 256 + 256;
+  // the same split-K plan as the allocating entry point (identical results)
+  int64_t ws_elems = 0;
+  gemm_tc_split_plan((int)M, (int)Nc, (int)K, planes, planes, EPI_RAW_F64, &ws_elems);
+  const size_t bytesW = sizeof(float) * (size_t)ws_elems;
+  const size_t offB = ((bytesA + 255) / 256) * 256, offE = offB + ((bytesB + 255) / 256) * 256;
+  const size_t offW = offE + 256;
+  const size_t need = offW + bytesW;
   if (need > kNoAllocBytes) {
-    set_error("wcs_gemm_split_bf16_noalloc: (M + Nc) * ceil64(K) * planes * 2 bytes exceeds the 32 MiB "
-              "scratch; use wcs_gemm_split_bf16");
+    set_error("wcs_gemm_split_bf16_noalloc: (M + Nc) * ceil64(K) * planes * 2 bytes plus the split-K "
+              "partials exceed the 32 MiB scratch; use wcs_gemm_split_bf16");
     return WCS_ERR_ARG;
   }
   void* base = nullptr;
@@ -70,8 +76,9 @@ extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, con
   cudaStream_t s = (cudaStream_t)stream;
   unsigned char* p = (unsigned char*)base;
   uint16_t* pa = (uint16_t*)p;
-  uint16_t* pb = (uint16_t*)(p + ((bytesA + 255) / 256) * 256);
-  int* err = (int*)(p + ((bytesA + 255) / 256) * 256 + ((bytesB + 255) / 256) * 256);
+  uint16_t* pb = (uint16_t*)(p + offB);
+  int* err = (int*)(p + offE);
+  float* ws = (float*)(p + offW);
   // the array keeps the previous call's contents: clear the planes (their
   // K padding must read as zero) and the error flag
   cudaMemsetAsync(pa, 0, bytesA, s);
@@ -96,6 +103,7 @@ extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, con
   t.out = D;
   t.ldo = ldd;
   t.err = err;
+  if (ws_elems > 0) { t.ws = ws; t.ws_elems = ws_elems; }
   if ((r = gemm_tc(oa, ob, t, s))) return r;
   int errh = 0;
   cudaMemcpyAsync(&errh, err, sizeof(int), cudaMemcpyDeviceToHost, s);

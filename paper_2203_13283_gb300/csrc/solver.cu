@@ -7,6 +7,7 @@
 // circle operators.  Eq. (7): C - C_c = U V^T by randomized range finding;
 // Eq. (8)/(9): Woodbury with the capacitance K = I + V^T C_c^{-1} U.
 #include <algorithm>
+#include <complex>
 #include <cstdio>
 #include <cstdlib>
 #include <cmath>
@@ -77,6 +78,8 @@ struct wcs_ctx {
   DevBuf stage0, stage1, stage2;          // staged right-hand blocks (bf16 planes)
   int64_t stage_cols = 0;
   DevBuf tcerr;
+  DevBuf gW;                 // split-K workspace of the small contractions (FP32)
+  DevBuf qh, qt;             // skeleton basis as resident bf16 planes: rows conj(q_i); rows of Q
   DevBuf gA, gB;                          // staging for general complex tensor products
   // optional per-kernel timing: CUDA events on the context stream
   bool profile = false;
@@ -138,14 +141,21 @@ static int ensure_work(wcs_ctx* c, int64_t cols) {
   return 0;
 }
 
+// the device flag of the bounded waits in the tensor-core kernels: zeroed when allocated
+static int ensure_tcerr(wcs_ctx* c) {
+  if (c->tcerr.p) return 0;
+  TRY(c->tcerr.ensure(sizeof(int)));
+  cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), c->s);
+  return 0;
+}
+
 static int ensure_stage(wcs_ctx* c, int64_t cols) {
   if (cols <= c->stage_cols) return 0;
   const size_t b = sizeof(uint16_t) * (size_t)(2 * cols) * c->ldp * c->rhs_planes;
   TRY(c->stage0.ensure(b));
   TRY(c->stage1.ensure(b));
   TRY(c->stage2.ensure(b));
-  TRY(c->tcerr.ensure(sizeof(int)));
-  cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), c->s);
+  TRY(ensure_tcerr(c));
   c->stage_cols = cols;
   return 0;
 }
@@ -222,7 +232,7 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
   const size_t needA = sizeof(uint16_t) * (size_t)m * ldk * P, needB = sizeof(uint16_t) * (size_t)(2 * n) * ldk * P;
   if (needA > c->gA.bytes) TRY(c->gA.ensure(std::max(needA, c->gA.bytes + c->gA.bytes / 2)));
   if (needB > c->gB.bytes) TRY(c->gB.ensure(std::max(needB, c->gB.bytes + c->gB.bytes / 2)));
-  TRY(c->tcerr.ensure(sizeof(int)));
+  TRY(ensure_tcerr(c));
   uint16_t *pa[3], *pb[3];
   for (int p = 0; p < 3; ++p) {
     pa[p] = (uint16_t*)c->gA.p + (int64_t)p * m * ldk;
@@ -244,6 +254,44 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
   t.epi = EPI_CPLX_F64;
   t.out = C; t.ldo = ldc; t.alpha = alpha; t.beta = beta;
   t.err = (int*)c->tcerr.p;
+  TRY(c->gW.ensure((size_t)32 << 20));
+  t.ws = (float*)c->gW.p;
+  t.ws_elems = (int64_t)(c->gW.bytes / sizeof(float));
+  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  TRY(gemm_tc(oa, ob, t, c->s));
+  return 0;
+}
+
+// cgemm with A already held as two split-bf16 planes (row-major real M x 2K,
+// leading dimension lda); A_view is the same matrix for the FP64 fallback.
+static int cgemm_planes(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, const uint16_t* A0,
+                        const uint16_t* A1, int64_t lda, ZView A_view, const zd* X, int64_t ldx, zd beta, zd* C,
+                        int64_t ldc) {
+  if (m <= 0 || n <= 0) return 0;
+  if (!c->mixed || k < 64) return cgemm(c, m, n, k, alpha, A_view, X, ldx, beta, C, ldc);
+  const int P = 2;
+  const int64_t ldk = ((2 * k + 63) / 64) * 64;
+  const size_t needB = sizeof(uint16_t) * (size_t)(2 * n) * ldk * P;
+  if (needB > c->gB.bytes) TRY(c->gB.ensure(std::max(needB, c->gB.bytes + c->gB.bytes / 2)));
+  TRY(ensure_tcerr(c));
+  uint16_t* pb[3];
+  for (int p = 0; p < 3; ++p) pb[p] = (uint16_t*)c->gB.p + (int64_t)p * 2 * n * ldk;
+  TRY(stage_rhs(X, k, n, ldx, 0, P, pb, ldk, c->s));
+  TcOperand oa, ob;
+  oa.planes = ob.planes = P;
+  oa.ld = lda;
+  ob.ld = ldk;
+  oa.plane[0] = A0; oa.plane[1] = A1;
+  ob.plane[0] = pb[0]; ob.plane[1] = pb[1];
+  TcArgs t;
+  t.M = (int)m; t.Nc = (int)(2 * n); t.K = (int)(2 * k);
+  tc_products(P, t);
+  t.epi = EPI_CPLX_F64;
+  t.out = C; t.ldo = ldc; t.alpha = alpha; t.beta = beta;
+  t.err = (int*)c->tcerr.p;
+  TRY(c->gW.ensure((size_t)32 << 20));
+  t.ws = (float*)c->gW.p;
+  t.ws_elems = (int64_t)(c->gW.bytes / sizeof(float));
   ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
   TRY(gemm_tc(oa, ob, t, c->s));
   return 0;
@@ -410,15 +458,27 @@ __global__ void k_absmax(const zd* x, int64_t n, double* out) {
 }
 
 // X0 = K^H / (||K||_1 ||K||_inf): column/row absolute sums
-__global__ void k_abs_sums(const zd* K, int64_t r, double* colsum, double* rowsum) {
+// column sums: one block per column (contiguous); row sums: one thread per row
+// (consecutive threads read consecutive rows of a column)
+__global__ void k_col_abs_sums(const zd* K, int64_t r, double* colsum) {
+  __shared__ double red[256];
+  const int64_t i = blockIdx.x;
+  double cs = 0.0;
+  for (int64_t j = threadIdx.x; j < r; j += blockDim.x) cs += zabs(K[i * r + j]);
+  red[threadIdx.x] = cs;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) colsum[i] = red[0];
+}
+
+__global__ void k_row_abs_sums(const zd* K, int64_t r, double* rowsum) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= r) return;
-  double cs = 0.0, rs = 0.0;
-  for (int64_t j = 0; j < r; ++j) {
-    cs += zabs(K[i * r + j]);   // column i
-    rs += zabs(K[j * r + i]);   // row i
-  }
-  colsum[i] = cs;
+  double rs = 0.0;
+  for (int64_t j = 0; j < r; ++j) rs += zabs(K[j * r + i]);
   rowsum[i] = rs;
 }
 
@@ -449,15 +509,30 @@ __global__ void k_two_minus(zd* T, int64_t r) {
 }
 
 // ||I - T||_F^2 partial sums (one block)
-__global__ void k_eye_residual(const zd* T, int64_t r, double* out) {
+// ||T - I||_F in two deterministic stages: per-block partial sums, then one block
+constexpr int EYE_BLOCKS = 304;
+__global__ void k_eye_partial(const zd* T, int64_t r, double* part) {
   __shared__ double red[256];
   double s = 0.0;
-  for (int64_t t = threadIdx.x; t < r * r; t += blockDim.x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < r * r; t += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = t % r, j = t / r;
     zd v = T[t];
     if (i == j) v.x -= 1.0;
     s += abs2(v);
   }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_eye_finish(const double* part, int n, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) s += part[t];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int o = 128; o > 0; o >>= 1) {
@@ -547,7 +622,7 @@ static void free_mesh(wcs_ctx* c) {
   c->ops.release(); c->mu.release();
   c->opplanes.release(); c->centres.release(); c->offs.release();
   c->stage0.release(); c->stage1.release(); c->stage2.release(); c->stage_cols = 0;
-  c->gA.release(); c->gB.release();
+  c->gA.release(); c->gB.release(); c->gW.release(); c->qh.release(); c->qt.release();
   c->U.release(); c->Vw.release(); c->Wt.release();
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
   c->rank = -1;
@@ -558,7 +633,7 @@ int wcs_destroy(wcs_ctx* c) {
   free_mesh(c);
   c->xf.release(); c->xn.release(); c->wn.release(); c->wlog.release();
   c->w1.release(); c->w2.release(); c->w3.release(); c->w4.release(); c->w5.release();
-  c->small.release();
+  c->small.release(); c->tcerr.release();
   delete c;
   return WCS_OK;
 }
@@ -682,7 +757,34 @@ static AsmArgs asm_args(wcs_ctx* c, bool circle) {
   A.near = circle ? c->near_c : c->near;
   A.wlog = c->wlog.d();
   A.ld = c->ld;
+  // k~ = k (1 + i t): both Hankel evaluations of a point pair from one real one
+  const double t = c->kt.y / c->k;
+  if (c->kt.x == c->k && t >= 0.0 && t <= 0.1) {
+    const std::complex<double> z(1.0, t);
+    const std::complex<double> c1 = 1.0 / z, c2 = 1.0 / std::sqrt(z);
+    A.kt_pair = 1;
+    A.ktp.t = t;
+    A.ktp.c1 = mkz(c1.real(), c1.imag());
+    A.ktp.c2 = mkz(c2.real(), c2.imag());
+  }
   return A;
+}
+
+// FP32 constants of the mixed form's far-pair path (after A.zfast is set)
+static void set_fast_consts(AsmArgs& A) {
+  const std::complex<double> kt(A.kt.x, A.kt.y);
+  const std::complex<double> ck = std::sqrt((2.0 / WCS_PI) / kt), ik = std::complex<double>(0.0, 1.0) / kt;
+  const std::complex<double> kt4 = std::complex<double>(0.0, 0.25) * kt;
+  FastConsts& F = A.fk;
+  F.kf = (float)A.k;
+  F.beta = (float)A.kt.y;
+  F.ck[0] = (float)ck.real(); F.ck[1] = (float)ck.imag();
+  F.ik[0] = (float)ik.real(); F.ik[1] = (float)ik.imag();
+  F.kt4[0] = (float)kt4.real(); F.kt4[1] = (float)kt4.imag();
+  F.ampk = (float)std::sqrt(2.0 / (WCS_PI * A.k));
+  F.kk2h2 = (float)(A.k * A.k * A.h * A.h);
+  F.h2 = (float)(A.h * A.h);
+  F.zfast2 = (float)(A.zfast * A.zfast);
 }
 
 __global__ void k_geom_sample_dummy() {}
@@ -728,7 +830,7 @@ int wcs_assemble(wcs_ctx* c) {
   } else {
     c->ldp = ((2 * N + 63) / 64) * 64;
     TRY(c->opplanes.ensure(sizeof(uint16_t) * (size_t)8 * c->planes * N * c->ldp));
-    cudaMemsetAsync(c->opplanes.p, 0, c->opplanes.bytes, c->s);   // zero the padding columns
+    if (c->ldp != 2 * N) cudaMemsetAsync(c->opplanes.p, 0, c->opplanes.bytes, c->s);   // zero the padding columns
     // element centres (xi = 1/2) and FP32 offsets of the far points
     const int qf = c->opt.q_far;
     TRY(c->centres.ensure(sizeof(double) * 6 * N));
@@ -751,6 +853,7 @@ int wcs_assemble(wcs_ctx* c) {
     A.cx = cp.x; A.cy = cp.y;
     A.ox = of; A.oy = of + N * qf; A.nxf = of + 2 * N * qf; A.nyf = of + 3 * N * qf;
     A.zfast = c->opt.zfast + 2.0 * c->k * c->h;
+    set_fast_consts(A);
     ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * qf * qf, 0.0);   // units: far point pairs
     TRY(assemble_planes(A, c->s));
   }
@@ -903,6 +1006,18 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   zd* Om = c->w4.z();
   zd* Y = c->w5.z();
   const zd one = mkz(1.0), mone = mkz(-1.0), zero = mkz(0.0);
+  // mixed form: the accepted basis also lives as resident split-bf16 planes,
+  // rows conj(q_i) (for Q^H X) and rows of Q (for Q Z), staged once per block
+  const int64_t ldqh = ((2 * N + 63) / 64) * 64, ldqt = ((2 * (cap + b) + 63) / 64) * 64;
+  uint16_t *QH[2] = {nullptr, nullptr}, *QT[2] = {nullptr, nullptr};
+  if (c->mixed) {
+    TRY(c->qh.ensure(sizeof(uint16_t) * 2 * (size_t)(cap + b) * ldqh));
+    TRY(c->qt.ensure(sizeof(uint16_t) * 2 * (size_t)N * ldqt));
+    for (int p = 0; p < 2; ++p) {
+      QH[p] = (uint16_t*)c->qh.p + (int64_t)p * (cap + b) * ldqh;
+      QT[p] = (uint16_t*)c->qt.p + (int64_t)p * N * ldqt;
+    }
+  }
   while (true) {
     if (ell >= cap) { status = (ell < N) ? WCS_ERR_RANK_CAP : WCS_OK; break; }
     {
@@ -915,9 +1030,9 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
     }
     ProfScope ps_proj(c, CAT_PROJECT, 0.0, 0.0);
     for (int pass = 0; pass < 2 && ell > 0; ++pass) {
-      TRY(cgemm(c, ell, b, N, one, blkH(Q, N), Y, N, zero, Zb.z(), ell));
+      TRY(cgemm_planes(c, ell, b, N, one, QH[0], QH[1], ldqh, blkH(Q, N), Y, N, zero, Zb.z(), ell));
       TRY(dbg_check(c, Zb.z(), ell, b, ell, "projection coefficients"));
-      TRY(cgemm(c, N, b, ell, mone, blk(Q, N), Zb.z(), ell, one, Y, N));
+      TRY(cgemm_planes(c, N, b, ell, mone, QT[0], QT[1], ldqt, blk(Q, N), Zb.z(), ell, one, Y, N));
       TRY(dbg_check(c, Y, N, b, N, "projection"));
     }
     TRY(column_norms(Y, N, N, b, Nb.d(), c->s));
@@ -951,17 +1066,25 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
       if (pass == 0) {
         // re-orthogonalise against the accepted basis before the second pass
         if (ell > 0) {
-          TRY(cgemm(c, ell, rk, N, one, blkH(Q, N), c->w3.z(), N, zero, Zb.z(), ell));
-          TRY(cgemm(c, N, rk, ell, mone, blk(Q, N), Zb.z(), ell, one, c->w3.z(), N));
+          TRY(cgemm_planes(c, ell, rk, N, one, QH[0], QH[1], ldqh, blkH(Q, N), c->w3.z(), N, zero, Zb.z(), ell));
+          TRY(cgemm_planes(c, N, rk, ell, mone, QT[0], QT[1], ldqt, blk(Q, N), Zb.z(), ell, one, c->w3.z(), N));
           TRY(dbg_check(c, c->w3.z(), N, rk, N, "re-orthogonalisation"));
         }
         src = c->w3.z();
       }
     }
     if (rk == 0) break;
+    if (c->mixed) {
+      uint16_t* ph[3] = {QH[0] + ell * ldqh, QH[1] + ell * ldqh, nullptr};
+      TRY(stage_view(Q + ell * N, rk, N, N, 1, 1, 2, ph, ldqh, c->s));   // rows conj(q_i)
+      uint16_t* pt[3] = {QT[0] + 2 * ell, QT[1] + 2 * ell, nullptr};
+      TRY(stage_view(Q + ell * N, N, rk, 1, N, 0, 2, pt, ldqt, c->s));   // row p: Q[p, ell + j]
+    }
     ell += rk;
     if (ell > cap) ell = cap;
   }
+  c->qh.release();
+  c->qt.release();
   c->rank = (int)ell;
   // V^T = Q^H (C - C_c)  <=>  Vw = (C - C_c)^H Q  (V = conj(Vw))
   TRY(c->Vw.ensure(sizeof(zd) * N * std::max<int64_t>(ell, 1)));
@@ -1018,9 +1141,11 @@ int wcs_factor(wcs_ctx* c) {
       ProfScope ps(c, CAT_INVERSE, 16.0 * r * (double)r * r, 0.0);
       DevBuf T, sums;
       TRY(T.ensure(sizeof(zd) * r * r));
-      TRY(sums.ensure(sizeof(double) * (2 * r + 2)));
+      TRY(sums.ensure(sizeof(double) * (3 * r + 2 + EYE_BLOCKS)));
       double* cs = sums.d();
-      k_abs_sums<<<(unsigned)((r + 127) / 128), 128, 0, c->s>>>(Kb.z(), r, cs, cs + r);
+      k_col_abs_sums<<<(unsigned)r, 256, 0, c->s>>>(Kb.z(), r, cs);
+      note_launch();
+      k_row_abs_sums<<<(unsigned)((r + 127) / 128), 128, 0, c->s>>>(Kb.z(), r, cs + r);
       note_launch();
       k_scaled_adjoint<<<1024, 256, 0, c->s>>>(Kb.z(), r, cs, cs + r, Kinv.z());
       note_launch();
@@ -1034,7 +1159,9 @@ int wcs_factor(wcs_ctx* c) {
         // T = K X
         TRY(cgemm(c, r, r, r, mkz(1.0), blk(Kb.z(), r), X, r, mkz(0.0), T.z(), r));
         if ((it & 3) == 3) {
-          k_eye_residual<<<1, 256, 0, c->s>>>(T.z(), r, cs + 2 * r);
+          k_eye_partial<<<EYE_BLOCKS, 256, 0, c->s>>>(T.z(), r, cs + 3 * r);
+          note_launch();
+          k_eye_finish<<<1, 256, 0, c->s>>>(cs + 3 * r, EYE_BLOCKS, cs + 2 * r);
           note_launch();
           cudaMemcpyAsync(&res, cs + 2 * r, sizeof(double), cudaMemcpyDeviceToHost, c->s);
           TRY(sync(c));
@@ -1277,10 +1404,13 @@ static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, in
   if (M == 0 || Nc == 0) return WCS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t ldp = ((K + 63) / 64) * 64;
-  DevBuf pa, pb, err;
+  DevBuf pa, pb, err, ws;
   TRY(pa.ensure(sizeof(uint16_t) * ldp * M * planes));
   TRY(pb.ensure(sizeof(uint16_t) * ldp * Nc * planes));
   TRY(err.ensure(sizeof(int)));
+  int64_t ws_need = 0;
+  if (!accurate) gemm_tc_split_plan((int)M, (int)Nc, (int)K, planes, planes, EPI_RAW_F64, &ws_need);
+  if (ws_need > 0) TRY(ws.ensure(sizeof(float) * (size_t)ws_need));
   cudaMemsetAsync(pa.p, 0, pa.bytes, s);
   cudaMemsetAsync(pb.p, 0, pb.bytes, s);
   cudaMemsetAsync(err.p, 0, sizeof(int), s);
@@ -1303,11 +1433,13 @@ static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, in
   t.out = D;
   t.ldo = ldd;
   t.err = (int*)err.p;
+  t.ws = (float*)ws.p;
+  t.ws_elems = (int64_t)(ws.bytes / sizeof(float));
   TRY(accurate ? gemm_tc_accurate(oa, ob, t, s) : gemm_tc(oa, ob, t, s));
   int errh = 0;
   cudaMemcpyAsync(&errh, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
-  pa.release(); pb.release(); err.release();
+  pa.release(); pb.release(); err.release(); ws.release();
   if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
   if (errh) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
   return WCS_OK;

@@ -26,6 +26,25 @@ def test_split_bf16_gemm(M, Nc, K, planes):
     assert err < bound, err
 
 
+@pytest.mark.parametrize("M,Nc,K", [(128, 128, 65536), (96, 70, 16384), (200, 64, 8192)])
+@pytest.mark.parametrize("planes", [2, 3])
+def test_split_bf16_gemm_split_k(M, Nc, K, planes):
+    """Few output tiles and long K: the contraction is split along K over the
+    grid and the FP32 partials are summed in FP64 in a fixed order."""
+    built()
+    from paper_2203_13283_gb300.solver import gemm_split_bf16
+    g = torch.Generator(device="cpu").manual_seed(M + 3 * Nc + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(Nc, K, generator=g, dtype=torch.float64).cuda()
+    D = gemm_split_bf16(A, B, planes)
+    D2 = gemm_split_bf16(A, B, planes)
+    assert torch.equal(D, D2)          # fixed summation order: reproducible
+    ref = A @ B.T
+    err = ((D - ref).abs().max() / (A.abs() @ B.abs().T).max()).item()
+    bound = {2: 6e-5, 3: 1e-5}[planes]
+    assert err < bound, err
+
+
 @pytest.mark.parametrize("M,Nc,K", [(128, 64, 64), (300, 200, 1000), (256, 128, 65536), (130, 70, 300)])
 @pytest.mark.parametrize("planes", [2, 3])
 def test_split_bf16_gemm_accurate(M, Nc, K, planes):
