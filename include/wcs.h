@@ -222,10 +222,12 @@ int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, i
                         const double* B_dev, int64_t ldb, int planes, double* D_dev, int64_t ldd,
                         void* stream);
 
-/* wcs_gemm_split_bf16 with a choice of accumulation: accurate != 0 drains the
- * tensor-memory accumulator into compensated FP32 registers after every
- * K = 16 step (the accumulator of the MMA truncates, so its error grows with
- * the number of steps it spans); planes must then be 2 or 3. */
+/* wcs_gemm_split_bf16 with a choice of accumulation.  The accumulator of the
+ * MMA truncates, so its error grows with the number of K = 16 steps it spans.
+ * accurate = 1 drains the tensor-memory accumulator into FP32 register sums
+ * after every step (~1e-7 relative with 3 planes); accurate = n > 1 drains
+ * every n steps (n = 64: ~1e-5 at close to the speed of accurate = 0);
+ * planes must then be 2 or 3. */
 int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
                            const double* B_dev, int64_t ldb, int planes, int accurate, double* D_dev,
                            int64_t ldd, void* stream);

@@ -60,6 +60,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   }
 }
 
+// The same wait for warps that share a sub-partition with the MMA-issuing or
+// TMA thread: they sleep between polls instead of taking its issue slots.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, long long budget,
+                                                const volatile int* gerr, unsigned ns) {
+  const long long t0 = clock64();
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    __nanosleep(ns);
+    if ((i & 15u) == 15u && (clock64() - t0 > budget || *gerr != 0)) return false;
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -111,6 +123,56 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 64 columns of 32 lanes in one load, waited for inside the same statement
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {"
+      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63"
+      "}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+        "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+        "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+        "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+        "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+        "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+        "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const float (&v)[64]) {
+  uint32_t r[64];
+#pragma unroll
+  for (int i = 0; i < 64; ++i) r[i] = __float_as_uint(v[i]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x64.b32 [%64], {"
+      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63"
+      "};\n"
+      "tcgen05.wait::st.sync.aligned;"
+      :
+      : "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(r[32]),
+        "r"(r[33]), "r"(r[34]), "r"(r[35]), "r"(r[36]), "r"(r[37]), "r"(r[38]), "r"(r[39]), "r"(r[40]),
+        "r"(r[41]), "r"(r[42]), "r"(r[43]), "r"(r[44]), "r"(r[45]), "r"(r[46]), "r"(r[47]), "r"(r[48]),
+        "r"(r[49]), "r"(r[50]), "r"(r[51]), "r"(r[52]), "r"(r[53]), "r"(r[54]), "r"(r[55]), "r"(r[56]),
+        "r"(r[57]), "r"(r[58]), "r"(r[59]), "r"(r[60]), "r"(r[61]), "r"(r[62]), "r"(r[63]), "r"(taddr)
+      : "memory");
 }
 
 // ----------------------------------------------------------------------------- kernel
@@ -356,8 +418,12 @@ __global__ void k_splitk_reduce(TcArgs a, int splits) {
 // sum over 64 steps folded into an outer sum), which keeps the FP32 rounding
 // of ~K/16 additions near 1e-7 at a quarter of the cost of compensated
 // summation.  Tile 128 x 128; warps 0-7 drain (warp w: TMEM lanes 32 (w % 4),
-// columns 64 (w / 4)), warp 8 loads (TMA), warp 9 issues the MMAs.
-constexpr int ACC_NT = 128, ACC_THREADS = 320, ACC_FOLD = 64;
+// columns 64 (w / 4)), warp 8 loads (TMA), warp 9 issues the MMAs.  The drain
+// is bound by the latency of the TMEM load, so each warp moves its 64 columns
+// in one load and keeps only the inner sums in registers; the outer sums live
+// in the last 128 TMEM columns, after three step buffers (384 columns).
+constexpr int ACC_NT = 128, ACC_THREADS = 320, ACC_FOLD = 64, ACC_NBUF = 3;
+constexpr int ACC_OUTER = ACC_NBUF * ACC_NT;   // first TMEM column of the outer sums
 
 template <int PA, int PB, int STAGES>
 struct AccSmem {
@@ -378,9 +444,9 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + STAGES * L::STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;      // [2] MMA -> drain
-  uint64_t* tempty = tfull + 2;          // [2] drain -> MMA
-  uint32_t* tslot = (uint32_t*)(tempty + 2);
+  uint64_t* tfull = empty + STAGES;      // [ACC_NBUF] MMA -> drain
+  uint64_t* tempty = tfull + ACC_NBUF;   // [ACC_NBUF] drain -> MMA
+  uint32_t* tslot = (uint32_t*)(tempty + ACC_NBUF);
   volatile int* abort_flag = (volatile int*)(tslot + 1);
   volatile int* issued = (volatile int*)(tslot + 2);
   volatile int* consumed = (volatile int*)(tslot + 3);
@@ -390,10 +456,14 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   const int n0 = blockIdx.x * ACC_NT;
   const int nk = (args.K + TC_BK - 1) / TC_BK;
   const int nsteps = nk * (TC_BK / 16);
+  // accumulation groups: `drain` consecutive K = 16 steps share one TMEM
+  // buffer before it is drained (1: every step)
+  const int drain = args.drain > 1 ? args.drain : 1;
+  const int ngroups = (nsteps + drain - 1) / drain;
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < STAGES; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
-    for (int q = 0; q < 2; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], 8); }
+    for (int q = 0; q < ACC_NBUF; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], 8); }
     *abort_flag = 0;
     *issued = 0;
     *consumed = 0;
@@ -401,7 +471,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                 "r"((uint32_t)(2 * ACC_NT)));
+                 "r"(512u));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -413,9 +483,9 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ACC_NT >> 3) << 17) |
                          ((uint32_t)(TC_BM >> 4) << 24);
 
-  float inner[64], outer[64];
+  float inner[64];
 #pragma unroll
-  for (int i = 0; i < 64; ++i) { inner[i] = 0.f; outer[i] = 0.f; }
+  for (int i = 0; i < 64; ++i) inner[i] = 0.f;
 
   if (warp == 8) {
     if (lane == 0) {
@@ -437,7 +507,14 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
     }
   } else if (warp == 9) {
     if (lane == 0) {
-      int g = 0;
+      // products of order < planes, smallest first (the order of tc_products,
+      // checked on the host); descriptors are formed once per stage and the
+      // group/buffer counters advance without divisions, so the issuing thread
+      // keeps ahead of the tensor core
+      constexpr int NP = (PA == 3) ? 6 : 3;
+      constexpr int IA[6] = {PA == 3 ? 2 : 1, PA == 3 ? 1 : 0, 0, 1, 0, 0};
+      constexpr int IB[6] = {0, 1, PA == 3 ? 2 : 0, 0, 1, 0};
+      int b = 0, ingroup = 0, q = 0;
       bool ok = true;
       for (int kb = 0; kb < nk && ok; ++kb) {
         const int st = kb % STAGES;
@@ -445,20 +522,33 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
         *consumed = kb + 1;
         if (*abort_flag) break;
         tc_fence_after();
-        uint8_t* sp = smem + st * L::STAGE_BYTES;
-        for (int kk = 0; kk < TC_BK / 16; ++kk, ++g) {
-          const int b = g & 1;
-          if (g >= 2 && !mbar_wait(&tempty[b], ((g >> 1) - 1) & 1, WAIT_LIMIT, args.err)) {
-            *abort_flag = 25; ok = false; break;
+        const uint8_t* sp = smem + st * L::STAGE_BYTES;
+        uint64_t da[NP], db[NP];
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          da[p] = sw128_desc(sp + IA[p] * L::A_BYTES);
+          db[p] = sw128_desc(sp + PA * L::A_BYTES + IB[p] * L::B_BYTES);
+        }
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          if (ingroup == 0 && q >= ACC_NBUF) {
+            if (!mbar_wait(&tempty[b], ((q / ACC_NBUF) - 1) & 1, WAIT_LIMIT, args.err)) {
+              *abort_flag = 25; ok = false; break;
+            }
+            tc_fence_after();
           }
-          tc_fence_after();
           const uint32_t dt = tmem + (uint32_t)(b * ACC_NT);
-          for (int p = 0; p < args.nprod; ++p) {
-            const uint64_t da = sw128_desc(sp + args.ia[p] * L::A_BYTES);
-            const uint64_t db = sw128_desc(sp + PA * L::A_BYTES + args.ib[p] * L::B_BYTES);
-            mma_bf16(dt, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, p > 0 ? 1u : 0u);
+#pragma unroll
+          for (int p = 0; p < NP; ++p)
+            mma_bf16(dt, da[p] + (uint64_t)(2 * kk), db[p] + (uint64_t)(2 * kk), idesc,
+                     (ingroup == 0 && p == 0) ? 0u : 1u);
+          ++ingroup;
+          if (ingroup == drain || (kb == nk - 1 && kk == TC_BK / 16 - 1)) {
+            mma_commit(&tfull[b]);
+            ingroup = 0;
+            ++q;
+            b = (b == ACC_NBUF - 1) ? 0 : b + 1;
           }
-          mma_commit(&tfull[b]);
         }
         mma_commit(&empty[st]);
       }
@@ -466,26 +556,29 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   } else {
     // drain warps
     const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
-    for (int g = 0; g < nsteps; ++g) {
-      const int b = g & 1;
-      bool got = mbar_wait(&tfull[b], (g >> 1) & 1, WAIT_LIMIT, args.err);
+    const uint32_t touter = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colhalf);
+    float v[64];
+#pragma unroll
+    for (int i = 0; i < 64; ++i) v[i] = 0.f;
+    tmem_st64(touter, v);
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g % ACC_NBUF;
+      bool got = (drain > 1) ? mbar_wait_sleep(&tfull[b], (g / ACC_NBUF) & 1, WAIT_LIMIT, args.err, 256u)
+                             : mbar_wait(&tfull[b], (g / ACC_NBUF) & 1, WAIT_LIMIT, args.err);
       got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
       if (!got) { if (lane == 0) atomicCAS((int*)abort_flag, 0, 24); break; }
       tc_fence_after();
-      float v[32];
-      const uint32_t ta = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colhalf);
-      tmem_ld32(ta, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) inner[i] += v[i];
-      tmem_ld32(ta + 32, v);
-#pragma unroll
-      for (int i = 0; i < 32; ++i) inner[32 + i] += v[i];
+      tmem_ld64(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colhalf), v);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
-      if ((g % ACC_FOLD) == ACC_FOLD - 1) {
 #pragma unroll
-        for (int i = 0; i < 64; ++i) { outer[i] += inner[i]; inner[i] = 0.f; }
+      for (int i = 0; i < 64; ++i) inner[i] += v[i];
+      if ((g % ACC_FOLD) == ACC_FOLD - 1) {
+        tmem_ld64(touter, v);
+#pragma unroll
+        for (int i = 0; i < 64; ++i) { v[i] += inner[i]; inner[i] = 0.f; }
+        tmem_st64(touter, v);
       }
     }
   }
@@ -499,18 +592,20 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
         (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
     }
   } else if (warp < 8) {
-    float out[32];
+    const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
+    float v[64], out[32];
+    tmem_ld64(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colhalf), v);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) out[i] = outer[i] + inner[i];
-    epilogue_store(args, m0 + 32 * (warp & 3) + lane, n0 + 64 * (warp >> 2), out);
+    for (int i = 0; i < 32; ++i) out[i] = v[i] + inner[i];
+    epilogue_store(args, m0 + lanebase + lane, n0 + colhalf, out);
 #pragma unroll
-    for (int i = 0; i < 32; ++i) out[i] = outer[32 + i] + inner[32 + i];
-    epilogue_store(args, m0 + 32 * (warp & 3) + lane, n0 + 64 * (warp >> 2) + 32, out);
+    for (int i = 0; i < 32; ++i) out[i] = v[32 + i] + inner[32 + i];
+    epilogue_store(args, m0 + lanebase + lane, n0 + colhalf + 32, out);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)(2 * ACC_NT)));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
   }
 }
 
@@ -544,6 +639,14 @@ int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaSt
   for (int p = 0; p < args.nprod; ++p)
     if (args.ia[p] >= A.planes || args.ib[p] >= B.planes) { set_error("gemm_tc: plane index"); return 1; }
   if ((args.M + TC_BM - 1) / TC_BM > 65535) { set_error("gemm_tc: M too large"); return 1; }
+  {
+    // the kernel issues the full product list of tc_products for its plane count
+    TcArgs ref;
+    tc_products(A.planes, ref);
+    bool same = (A.planes == B.planes) && (args.nprod == ref.nprod);
+    for (int p = 0; same && p < ref.nprod; ++p) same = (args.ia[p] == ref.ia[p] && args.ib[p] == ref.ib[p]);
+    if (!same) { set_error("gemm_tc_accurate: needs the full product list of tc_products"); return 1; }
+  }
   if (A.planes == 3 && B.planes == 3) return launch_tc_acc<3, 3, 2>(A, B, args, s);
   if (A.planes == 2 && B.planes == 2) return launch_tc_acc<2, 2, 3>(A, B, args, s);
   set_error("gemm_tc_accurate: plane combination not built");

@@ -35,6 +35,10 @@ struct TcArgs {
   float* ws = nullptr;
   int64_t ws_elems = 0;
   int kper = 0;          // set by gemm_tc: k-blocks per split (0: no split)
+  // gemm_tc_accurate: K = 16 steps accumulated in tensor memory before each
+  // drain into FP32 registers (1: every step, error ~1e-7; 64: error ~1e-5 at
+  // close to the speed of gemm_tc)
+  int drain = 1;
 };
 
 #define TRY_TC(x)          \

@@ -158,9 +158,13 @@ __global__ void k_min_curv(Contour c, const double* cum, int P, double L, int64_
   double m = 1e300;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double x, y, nx, ny, kap;
-    point_at(c, cum, P, L, L * (double)i / (double)M, x, y, nx, ny, kap);
-    m = fmin(m, kap);
+    // a dense uniform grid in theta covers the curve as well as one in arc
+    // length and needs no arc-length inversion
+    const double th = 2.0 * WCS_PI * (double)i / (double)M;
+    double r0, r1, r2;
+    rho_derivs(c, th, r0, r1, r2);
+    const double sp2 = r0 * r0 + r1 * r1;
+    m = fmin(m, (r0 * r0 + 2.0 * r1 * r1 - r0 * r2) / (sp2 * sqrt(sp2)));
   }
   red[threadIdx.x] = m;
   __syncthreads();
@@ -217,7 +221,7 @@ int points_build(const Contour& c, const ArcTable& t, int64_t N, double h, const
 
 int min_curvature(const Contour& c, const ArcTable& t, int64_t samples, double* kmin,
                   cudaStream_t s) {
-  const int blocks = 64;
+  const int blocks = 304;
   double* d = nullptr;
   if (cudaMalloc(&d, sizeof(double) * blocks) != cudaSuccess) { set_error("oom"); return 4; }
   k_min_curv<<<blocks, 256, 0, s>>>(c, t.cum, t.P, t.L, samples, d);

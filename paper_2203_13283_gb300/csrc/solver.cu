@@ -78,6 +78,7 @@ struct wcs_ctx {
   DevBuf stage0, stage1, stage2;          // staged right-hand blocks (bf16 planes)
   int64_t stage_cols = 0;
   DevBuf tcerr;
+  bool first_accurate = false;   // mixed form: the first residual has been small enough to skip the fast pass
   DevBuf gW;                 // split-K workspace of the small contractions (FP32)
   DevBuf qh, qt;             // skeleton basis as resident bf16 planes: rows conj(q_i); rows of Q
   DevBuf gA, gB;                          // staging for general complex tensor products
@@ -173,11 +174,19 @@ static int stage(wcs_ctx* c, DevBuf& buf, const zd* X, int64_t ldx, int64_t cols
 static bool debug_finite();
 static int check_tc(wcs_ctx* c);
 
+// Precision of a tensor-core operator product (mixed form):
+//   PREC_FAST      two leading planes, one accumulator over all of K (~1e-4 at
+//                  K ~ 1e5): skeleton sampling, Woodbury products
+//   PREC_ACCURATE  all stored planes, accumulator drained every K = 16 step
+//                  (~1e-7): refinement residual, preconditioned right-hand side
+//   PREC_PERIODIC  two leading planes, accumulator drained every 64 steps
+//                  (~1e-5): residual updates R <- R - C dx, whose error scales
+//                  with |dx|
+enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2 };
+
 static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols, zd alpha, zd beta, zd* Y,
-                    int64_t ldy, bool accurate = false) {
-  // accurate: all stored planes, accumulator drained every K step (refinement
-  // residual, preconditioned right-hand side); otherwise the two leading
-  // planes with one TMEM accumulator (skeleton sampling, Woodbury products)
+                    int64_t ldy, int mode = PREC_FAST) {
+  const bool accurate = (mode == PREC_ACCURATE);
   const int P = accurate ? std::min(c->planes, c->rhs_planes) : std::min(2, std::min(c->planes, c->rhs_planes));
   TcOperand A, B;
   A.planes = P;
@@ -199,12 +208,13 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.alpha = alpha;
   t.beta = beta;
   t.err = (int*)c->tcerr.p;
-  ProfScope ps(c, accurate ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
-  TRY(accurate ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
+  t.drain = (mode == PREC_PERIODIC) ? 64 : 1;
+  ProfScope ps(c, mode != PREC_FAST ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  TRY(mode != PREC_FAST ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
   if (debug_finite()) {
     int r = check_tc(c);
-    if (r) fprintf(stderr, "[wcs debug] operator product op=%d adj=%d acc=%d M=%d Nc=%d K=%d: %s\n", op,
-                   (int)adjoint, (int)accurate, t.M, t.Nc, t.K, g_err.c_str());
+    if (r) fprintf(stderr, "[wcs debug] operator product op=%d adj=%d mode=%d M=%d Nc=%d K=%d: %s\n", op,
+                   (int)adjoint, mode, t.M, t.Nc, t.K, g_err.c_str());
     return r;
   }
   return 0;
@@ -298,7 +308,7 @@ static int cgemm_planes(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, c
 }
 
 static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj,
-                         bool acc) {
+                         int acc) {
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -331,8 +341,8 @@ static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ld
 
 // Y = C X (adjoint: C^H X); uses w1, w2 as temporaries.  Y must not alias X.
 static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj,
-                   bool accurate = false) {
-  if (c->mixed) return apply_C_mixed(c, X, ldx, Y, ldy, cols, adj, accurate);
+                   int mode = PREC_FAST) {
+  if (c->mixed) return apply_C_mixed(c, X, ldx, Y, ldy, cols, adj, mode);
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -939,8 +949,8 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
     const zd* xc = x + c0 * ldx;
     zd* yc = y + c0 * ldy;
     switch (op) {
-      case WCS_OP_C: TRY(apply_C(c, xc, ldx, yc, ldy, cc, false, true)); break;
-      case WCS_OP_CH: TRY(apply_C(c, xc, ldx, yc, ldy, cc, true, true)); break;
+      case WCS_OP_C: TRY(apply_C(c, xc, ldx, yc, ldy, cc, false, PREC_ACCURATE)); break;
+      case WCS_OP_CH: TRY(apply_C(c, xc, ldx, yc, ldy, cc, true, PREC_ACCURATE)); break;
       case WCS_OP_CC: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 0)); break;
       case WCS_OP_CCH: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 1)); break;
       case WCS_OP_CC_INV: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 2)); break;
@@ -952,7 +962,7 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
           const int which = op - WCS_OP_S;
           TRY(ensure_stage(c, cc));
           TRY(stage(c, c->stage0, xc, ldx, cc, 0));
-          TRY(tc_apply(c, which, false, c->stage0, cc, mkz(1.0), mkz(0.0), yc, ldy, true));
+          TRY(tc_apply(c, which, false, c->stage0, cc, mkz(1.0), mkz(0.0), yc, ldy, PREC_ACCURATE));
           break;
         }
         if (op != WCS_OP_S) goto fp64_ops;
@@ -988,7 +998,12 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   const int64_t cap = (max_rank <= 0 || max_rank > N) ? N : max_rank;
   const int b = c->opt.block;
   ProfScope whole(c, CAT_SKELETON, 0.0, 0.0);
-  TRY(ensure_work(c, b));
+  // samples are drawn SB = 4b columns per pass over the operators and
+  // orthonormalised b columns at a time; Y is linear in Omega and Omega's
+  // columns come from one counter stream, so the basis is the one of the
+  // b-column loop
+  const int64_t SB = std::min<int64_t>(4 * (int64_t)b, ((cap + b - 1) / b) * b);
+  TRY(ensure_work(c, SB));
   TRY(c->U.ensure(sizeof(zd) * N * (cap + b)));
   zd* Q = c->U.z();
   const double thr = tol * c->norm_cc / (10.0 * std::sqrt(2.0 / WCS_PI));
@@ -1004,7 +1019,8 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   int status = WCS_OK;
   std::vector<double> norms(b);
   zd* Om = c->w4.z();
-  zd* Y = c->w5.z();
+  zd* Ys = c->w5.z();
+  int64_t batch_cols = 0, batch_used = 0;
   const zd one = mkz(1.0), mone = mkz(-1.0), zero = mkz(0.0);
   // mixed form: the accepted basis also lives as resident split-bf16 planes,
   // rows conj(q_i) (for Q^H X) and rows of Q (for Q Z), staged once per block
@@ -1020,20 +1036,26 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   }
   while (true) {
     if (ell >= cap) { status = (ell < N) ? WCS_ERR_RANK_CAP : WCS_OK; break; }
-    {
+    if (batch_used == batch_cols) {
       ProfScope ps(c, CAT_SAMPLE, 0.0, 0.0);
-      TRY(gaussian_fill(Om, N, N, b, seed, offset, c->s));
-      TRY(dbg_check(c, Om, N, b, N, "gaussian"));
-      offset += (uint64_t)N * b;
-      TRY(apply_remainder(c, Om, N, Y, N, b, false));
-      TRY(dbg_check(c, Y, N, b, N, "sample"));
+      batch_cols = std::min<int64_t>(SB, ((cap - ell + b - 1) / b) * b);
+      batch_used = 0;
+      TRY(gaussian_fill(Om, N, N, batch_cols, seed, offset, c->s));
+      TRY(dbg_check(c, Om, N, batch_cols, N, "gaussian"));
+      offset += (uint64_t)N * batch_cols;
+      TRY(apply_remainder(c, Om, N, Ys, N, batch_cols, false));
+      TRY(dbg_check(c, Ys, N, batch_cols, N, "sample"));
     }
-    ProfScope ps_proj(c, CAT_PROJECT, 0.0, 0.0);
-    for (int pass = 0; pass < 2 && ell > 0; ++pass) {
-      TRY(cgemm_planes(c, ell, b, N, one, QH[0], QH[1], ldqh, blkH(Q, N), Y, N, zero, Zb.z(), ell));
-      TRY(dbg_check(c, Zb.z(), ell, b, ell, "projection coefficients"));
-      TRY(cgemm_planes(c, N, b, ell, mone, QT[0], QT[1], ldqt, blk(Q, N), Zb.z(), ell, one, Y, N));
-      TRY(dbg_check(c, Y, N, b, N, "projection"));
+    zd* Y = Ys + batch_used * N;
+    batch_used += b;
+    {
+      ProfScope ps_proj(c, CAT_PROJECT, 0.0, 0.0);
+      for (int pass = 0; pass < 2 && ell > 0; ++pass) {
+        TRY(cgemm_planes(c, ell, b, N, one, QH[0], QH[1], ldqh, blkH(Q, N), Y, N, zero, Zb.z(), ell));
+        TRY(dbg_check(c, Zb.z(), ell, b, ell, "projection coefficients"));
+        TRY(cgemm_planes(c, N, b, ell, mone, QT[0], QT[1], ldqt, blk(Q, N), Zb.z(), ell, one, Y, N));
+        TRY(dbg_check(c, Y, N, b, N, "projection"));
+      }
     }
     TRY(column_norms(Y, N, N, b, Nb.d(), c->s));
     cudaMemcpyAsync(norms.data(), Nb.p, sizeof(double) * b, cudaMemcpyDeviceToHost, c->s);
@@ -1229,8 +1251,8 @@ static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b
     TRY(ensure_stage(c, cc));
     TRY(stage(c, c->stage1, T1, N, cc, 0));
     TRY(stage(c, c->stage2, T2, N, cc, 0));
-    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb, true));
-    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb, true));
+    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb, PREC_ACCURATE));
+    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb, PREC_ACCURATE));
   } else {
     TRY(zgemm(N, cc, N, mkz(0.0, -c->k), op_view(c->S, c->ld, false), blk(T1, N), mkz(0.0), b, ldb, c->s));
     TRY(zgemm(N, cc, N, mkz(-1.0), op_view(c->Dt, c->ld, false), blk(T2, N), mkz(1.0), b, ldb, c->s));
@@ -1251,36 +1273,73 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
   cudaMemcpyAsync(bn.data(), nb.p, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
   zd* R = c->w4.z();
   zd* dx = c->w5.z();
-  int it = 0;
-  double worst = 0, prev = 1e300;
-  bool accurate = !c->mixed;   // mixed form: fast residuals while the error is large
-  for (;; ++it) {
-    TRY(apply_C(c, x, ldx, R, N, cc, false, accurate || !c->mixed));
-    TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));   // R = b - C x
+  zd* T = c->w3.z();
+  // largest relative residual over the block's columns
+  auto worst_of = [&](double& worst) -> int {
     TRY(column_norms(R, N, N, cc, nb.d() + cc, c->s));
     cudaMemcpyAsync(rn.data(), nb.d() + cc, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
     TRY(sync(c));
     worst = 0;
     for (int64_t j = 0; j < cc; ++j) worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
-    if (!accurate && (worst < 3e-3 || it >= c->opt.max_refine / 2)) {
-      // the fast contraction's own error (~1e-4 at large K) is now comparable
-      // with the residual: recompute it with the drained accumulation
-      accurate = true;
-      TRY(apply_C(c, x, ldx, R, N, cc, false, true));
-      TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));
-      TRY(column_norms(R, N, N, cc, nb.d() + cc, c->s));
-      cudaMemcpyAsync(rn.data(), nb.d() + cc, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
-      TRY(sync(c));
-      worst = 0;
-      for (int64_t j = 0; j < cc; ++j) worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
+    return 0;
+  };
+  // R = b - C x with the given precision
+  auto residual = [&](int mode, double& worst) -> int {
+    TRY(apply_C(c, x, ldx, R, N, cc, false, mode));
+    TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));
+    return worst_of(worst);
+  };
+  int it = 0;
+  double worst = 0;
+  if (!c->mixed) {
+    // FP64 form: plain refinement on the exact residual
+    TRY(residual(PREC_ACCURATE, worst));
+    while (worst > c->opt.refine_tol && it < c->opt.max_refine) {
+      TRY(woodbury(c, R, N, dx, N, cc));
+      TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
+      ++it;
+      TRY(residual(PREC_ACCURATE, worst));
     }
-    if ((accurate && worst <= c->opt.refine_tol) || it >= c->opt.max_refine) break;
-    // stagnation: the residual no longer decreases (its floor is the
-    // contraction's rounding); further steps cannot improve the solution
-    if (accurate && c->mixed && worst > 0.7 * prev) break;
-    if (accurate) prev = worst;
-    TRY(woodbury(c, R, N, dx, N, cc));
-    TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
+  } else {
+    // Mixed form.  While the first residual is large, fast residuals do (their
+    // own error, ~1e-4, is below it); once it is small, the residual is formed
+    // with the drained accumulation (~1e-7) and then carried forward by updates
+    // R <- R - C dx in the periodic-drain precision: their error is ~1e-5 of
+    // |C dx|, i.e. far below the residual once |dx| is small.  Each round ends
+    // with a recomputed residual, so the reported residual is the true one;
+    // rounds stop when it reaches refine_tol or stops decreasing (its floor is
+    // the accuracy of the drained product).
+    if (!c->first_accurate) {
+      TRY(residual(PREC_FAST, worst));
+      while (worst >= 3e-3 && it < c->opt.max_refine / 2) {
+        TRY(woodbury(c, R, N, dx, N, cc));
+        TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
+        ++it;
+        TRY(residual(PREC_FAST, worst));
+      }
+      if (it == 0) c->first_accurate = true;   // later blocks skip the fast pass
+    }
+    TRY(residual(PREC_ACCURATE, worst));
+    double prev_true = 1e300;
+    bool floor = false;   // a round ended with the true residual far above the carried one
+    while (worst > c->opt.refine_tol && it < c->opt.max_refine && worst < 0.5 * prev_true && !floor) {
+      prev_true = worst;
+      double upd = worst, prev_upd = 1e300;
+      // updates until the carried residual is well below the target
+      while (upd > 0.1 * c->opt.refine_tol && it < c->opt.max_refine && upd < 0.7 * prev_upd) {
+        TRY(woodbury(c, R, N, dx, N, cc));
+        TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
+        ++it;
+        TRY(apply_C(c, dx, N, T, N, cc, false, PREC_PERIODIC));
+        TRY(axpby(N, cc, mkz(-1.0), T, N, mkz(1.0), R, N, c->s));
+        prev_upd = upd;
+        TRY(worst_of(upd));
+      }
+      TRY(residual(PREC_ACCURATE, worst));
+      // the gap is the evaluation floor of the drained product: another round
+      // would start from (and return to) the same floor
+      floor = worst > 10.0 * upd;
+    }
   }
   nb.release();
   *steps = std::max(*steps, it);
@@ -1395,7 +1454,7 @@ int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A, in
 
 static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
                            int64_t ldb, int planes, int accurate, double* D, int64_t ldd, void* stream) {
-  if (accurate && planes < 2) { set_error("accurate contraction needs 2 or 3 planes"); return WCS_ERR_ARG; }
+  if (accurate < 0 || (accurate && planes < 2)) { set_error("accurate contraction needs 2 or 3 planes"); return WCS_ERR_ARG; }
   if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (!A || lda < K)) ||
       (Nc > 0 && (!B || ldb < K)) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
     set_error("bad argument");
@@ -1435,6 +1494,7 @@ static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, in
   t.err = (int*)err.p;
   t.ws = (float*)ws.p;
   t.ws_elems = (int64_t)(ws.bytes / sizeof(float));
+  t.drain = accurate;
   TRY(accurate ? gemm_tc_accurate(oa, ob, t, s) : gemm_tc(oa, ob, t, s));
   int errh = 0;
   cudaMemcpyAsync(&errh, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -203,13 +203,16 @@ def quadrature_tables(q):
 
 
 def gemm_split_bf16(A, B, planes=2, accurate=False):
-    """D = A @ B.T on the tensor cores with split-bf16 operands (FP64 in/out, cuda)."""
+    """D = A @ B.T on the tensor cores with split-bf16 operands (FP64 in/out, cuda).
+
+    accurate: False/0 one accumulator over all of K; True/1 accumulator
+    drained every K = 16 step; an int n > 1 drains every n steps."""
     A = torch.as_tensor(A, dtype=torch.float64, device="cuda").contiguous()
     B = torch.as_tensor(B, dtype=torch.float64, device="cuda").contiguous()
     M, K = A.shape
     Nc = B.shape[0]
     D = torch.empty((M, Nc), dtype=torch.float64, device=A.device)
     st = torch.cuda.current_stream(A.device)
-    check(load().wcs_gemm_split_bf16_ex(M, Nc, K, _ptr(A), K, _ptr(B), K, int(planes), int(bool(accurate)),
+    check(load().wcs_gemm_split_bf16_ex(M, Nc, K, _ptr(A), K, _ptr(B), K, int(planes), int(accurate),
                                         _ptr(D), Nc, C.c_void_p(st.cuda_stream)))
     return D

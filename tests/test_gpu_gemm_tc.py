@@ -59,3 +59,21 @@ def test_split_bf16_gemm_accurate(M, Nc, K, planes):
     err = ((D - ref).norm() / ref.norm()).item()
     bound = {2: 3e-5, 3: 5e-7}[planes]
     assert err < bound, err
+
+
+@pytest.mark.parametrize("M,Nc,K", [(256, 128, 65536), (300, 200, 5000)])
+@pytest.mark.parametrize("planes", [2, 3])
+def test_split_bf16_gemm_periodic_drain(M, Nc, K, planes):
+    """Accumulator drained every 64 steps (K = 1024): its truncation error
+    spans at most 64 steps, so it stays near 1e-5 at any K, between the
+    one-accumulator contraction and the every-step drain."""
+    built()
+    from paper_2203_13283_gb300.solver import gemm_split_bf16
+    g = torch.Generator(device="cpu").manual_seed(M + 5 * Nc + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(Nc, K, generator=g, dtype=torch.float64).cuda()
+    ref = A @ B.T
+    D = gemm_split_bf16(A, B, planes, accurate=64)
+    err = ((D - ref).norm() / ref.norm()).item()
+    bound = {2: 4e-5, 3: 2e-5}[planes]
+    assert err < bound, err
