@@ -151,9 +151,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2203_13283_gb300 import dist as wdist
+    rank, world, local = wdist.world()
     w = dict(workloads.WORKLOADS[args.workload])
     if args.rhs:
         w["angles"] = workloads.uniform_angles(args.rhs)
@@ -230,12 +229,9 @@ def main():
     prof = S.profile_read(reset=True)
     S.profile(False)
     solve_s = sum(solves)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total, solve_s], device=S.device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total, solve_s = t.tolist()
-    value = world * B * args.steps / solve_s
+    # replicas: every rank solves its own batch; the slowest rank sets the time
+    total, solve_s = wdist.max_over_ranks([total, solve_s], device=S.device)
+    value = wdist.job_throughput(B * args.steps, world, solve_s)
     info = S.info()
     last = dict(S.last_solve)
 

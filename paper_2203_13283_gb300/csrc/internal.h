@@ -163,9 +163,10 @@ int lu_inverse(zd* A, int64_t n, zd* Ainv, int* piv, int* info_dev, double* minp
                cudaStream_t s);
 
 // ---------------------------------------------------------------- right-hand sides / far field
+// split_phase: FP64 phase at one point per hat and FP32 offsets (~1e-7; mixed form)
 int planewave_rhs(const Points& near, const double* wn, const double* xn, int q, int64_t N,
                   double h, double k, const double* angles, int B, zd* e, zd* hv, int64_t ld,
-                  cudaStream_t s);
+                  cudaStream_t s, bool split_phase = false);
 int farfield_matrix(const Points& near, const double* wn, const double* xn, int q, int64_t N,
                     double h, double k, const double* phi, int nphi, zd* E, int64_t lde,
                     cudaStream_t s);

@@ -284,13 +284,27 @@ int axpby(int64_t m, int64_t n, zd a, const zd* X, int64_t ldx, zd b, zd* Y, int
 // b x b Grams, a second kernel sums the partials (fixed order: deterministic).
 constexpr int GRAM_ROWS = 256;
 
+// Partial Gram sums over GRAM_ROWS rows: only the upper triangle i <= j of the
+// Hermitian b x b result is formed (pair index p -> column j = row of the
+// triangular numbers, row i = p - j (j + 1) / 2); both halves are written.
 __global__ void k_gram_partial(const zd* X, int64_t ld, int64_t m, int b, zd* part) {
   __shared__ zd xs[64][33];
   const int64_t r0 = (int64_t)blockIdx.x * GRAM_ROWS;
-  const int tid = threadIdx.x;                  // 256 threads: (i, j) pairs
-  zd acc[16];
+  const int tid = threadIdx.x;                  // 256 threads: up to 9 pairs each
+  const int npairs = b * (b + 1) / 2;
+  int ii[9], jj[9];
 #pragma unroll
-  for (int t = 0; t < 16; ++t) acc[t] = mkz(0.0);
+  for (int t = 0; t < 9; ++t) {
+    const int p = tid + 256 * t;
+    int j = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+    while (j * (j + 1) / 2 > p) --j;
+    while ((j + 1) * (j + 2) / 2 <= p) ++j;
+    ii[t] = (p < npairs) ? p - j * (j + 1) / 2 : -1;
+    jj[t] = j;
+  }
+  zd acc[9];
+#pragma unroll
+  for (int t = 0; t < 9; ++t) acc[t] = mkz(0.0);
   for (int64_t rr = r0; rr < min(m, r0 + GRAM_ROWS); rr += 32) {
     __syncthreads();
     for (int u = tid; u < 32 * b; u += blockDim.x) {
@@ -299,18 +313,20 @@ __global__ void k_gram_partial(const zd* X, int64_t ld, int64_t m, int b, zd* pa
     }
     __syncthreads();
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
-      const int pidx = tid + 256 * t;
-      const int i = pidx / 64, j = pidx % 64;
-      if (i < b && j < b)
+    for (int t = 0; t < 9; ++t) {
+      if (ii[t] >= 0) {
+        const int i = ii[t], j = jj[t];
         for (int r = 0; r < 32; ++r) zfma(acc[t], conj(xs[i][r]), xs[j][r]);
+      }
     }
   }
 #pragma unroll
-  for (int t = 0; t < 16; ++t) {
-    const int pidx = tid + 256 * t;
-    const int i = pidx / 64, j = pidx % 64;
-    if (i < b && j < b) part[(int64_t)blockIdx.x * b * b + j * b + i] = acc[t];
+  for (int t = 0; t < 9; ++t) {
+    if (ii[t] < 0) continue;
+    const int i = ii[t], j = jj[t];
+    zd* P = part + (int64_t)blockIdx.x * b * b;
+    P[j * b + i] = acc[t];
+    if (i != j) P[i * b + j] = conj(acc[t]);
   }
 }
 
@@ -408,7 +424,8 @@ __global__ void k_trsm_rows(const zd* X, int64_t ldx, int64_t m, const zd* R, in
   const int r = *rank_dev;
   for (int u = threadIdx.x; u < r * r; u += blockDim.x) {
     const int row = u % r, col = u / r;
-    Rs[col * r + row] = (row <= col) ? R[col * b + row] : mkz(0.0);
+    // diagonal stored as its reciprocal: one division per entry of R, not per row
+    Rs[col * r + row] = (row < col) ? R[col * b + row] : ((row == col) ? zrecip(R[col * b + row]) : mkz(0.0));
   }
   __shared__ int ps[128];
   for (int u = threadIdx.x; u < r; u += blockDim.x) ps[u] = perm[u];
@@ -418,7 +435,7 @@ __global__ void k_trsm_rows(const zd* X, int64_t ldx, int64_t m, const zd* R, in
   for (int j = 0; j < r; ++j) {
     zd v = X[(int64_t)ps[j] * ldx + i];
     for (int l = 0; l < j; ++l) v -= Y[(int64_t)l * ldy + i] * Rs[j * r + l];
-    Y[(int64_t)j * ldy + i] = zdiv(v, Rs[j * r + j]);
+    Y[(int64_t)j * ldy + i] = v * Rs[j * r + j];
   }
 }
 

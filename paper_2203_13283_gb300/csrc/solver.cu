@@ -1241,7 +1241,8 @@ int wcs_planewave_rhs(wcs_ctx* c, int64_t B, const double* angles, double* e, do
 }
 
 // b = -i k S~ G^{-1} e - (G/2 + D~) G^{-1} h  (Eq. 5), cc columns.
-static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b, int64_t ldb, int64_t cc) {
+static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b, int64_t ldb, int64_t cc,
+                        int mode = PREC_ACCURATE) {
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -1251,8 +1252,8 @@ static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b
     TRY(ensure_stage(c, cc));
     TRY(stage(c, c->stage1, T1, N, cc, 0));
     TRY(stage(c, c->stage2, T2, N, cc, 0));
-    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb, PREC_ACCURATE));
-    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb, PREC_ACCURATE));
+    TRY(tc_apply(c, 0, false, c->stage1, cc, mkz(0.0, -c->k), mkz(0.0), b, ldb, mode));
+    TRY(tc_apply(c, 2, false, c->stage2, cc, mkz(-1.0), mkz(1.0), b, ldb, mode));
   } else {
     TRY(zgemm(N, cc, N, mkz(0.0, -c->k), op_view(c->S, c->ld, false), blk(T1, N), mkz(0.0), b, ldb, c->s));
     TRY(zgemm(N, cc, N, mkz(-1.0), op_view(c->Dt, c->ld, false), blk(T2, N), mkz(1.0), b, ldb, c->s));
@@ -1261,9 +1262,38 @@ static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b
   return 0;
 }
 
+// Mixed form: R = b - C x with b of Eq. (5) left implicit,
+//   R = -(G/2 + D~) G^{-1} (h + (G/2 - D) x) - S~ G^{-1} (i k e + N x),
+// i.e. the four products of C x and no product for b.  Uses w1, w2.
+static int residual_rhs_mixed(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, const zd* x, int64_t ldx,
+                              zd* R, int64_t cc, int mode) {
+  const int64_t N = c->N;
+  zd* T1 = c->w1.z();
+  zd* T2 = c->w2.z();
+  const zd one = mkz(1.0), zero = mkz(0.0), mone = mkz(-1.0);
+  TRY(ensure_stage(c, cc));
+  TRY(stage(c, c->stage0, x, ldx, cc, 0));
+  TRY(tc_apply(c, 1, false, c->stage0, cc, mone, zero, T1, N, mode));   // -D x
+  TRY(tc_apply(c, 3, false, c->stage0, cc, one, zero, T2, N, mode));    // N x
+  TRY(gram_apply(x, ldx, T1, N, N, cc, c->h, 0.5, 1.0, c->s));          // + G x / 2
+  TRY(axpby(N, cc, one, hv, ld, one, T1, N, c->s));                     // + h
+  TRY(axpby(N, cc, mkz(0.0, c->k), e, ld, one, T2, N, c->s));           // + i k e
+  TRY(gram_inverse(T1, N, T1, N, N, cc, c->h, c->s));
+  TRY(gram_inverse(T2, N, T2, N, N, cc, c->h, c->s));
+  TRY(stage(c, c->stage1, T1, N, cc, 0));
+  TRY(stage(c, c->stage2, T2, N, cc, 0));
+  TRY(tc_apply(c, 2, false, c->stage1, cc, mone, zero, R, N, mode));    // -D~ T1
+  TRY(tc_apply(c, 0, false, c->stage2, cc, mone, one, R, N, mode));     // - S~ T2
+  TRY(gram_apply(T1, N, R, N, N, cc, c->h, -0.5, 1.0, c->s));           // - G T1 / 2
+  return 0;
+}
+
 // x = C^{-1} b with Woodbury + iterative refinement on the exact operator.
+// Mixed form with e, hv given: b only seeds x and scales the residual norm;
+// every residual is formed from e and hv directly (residual_rhs_mixed).
 static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx, int64_t cc,
-                       int* steps, double* relres) {
+                       int* steps, double* relres, const zd* e = nullptr, const zd* hv = nullptr,
+                       int64_t ld_eh = 0) {
   const int64_t N = c->N;
   TRY(woodbury(c, b, ldb, x, ldx, cc));
   DevBuf nb;
@@ -1285,8 +1315,12 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
   };
   // R = b - C x with the given precision
   auto residual = [&](int mode, double& worst) -> int {
-    TRY(apply_C(c, x, ldx, R, N, cc, false, mode));
-    TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));
+    if (c->mixed && e && hv) {
+      TRY(residual_rhs_mixed(c, e, hv, ld_eh, x, ldx, R, cc, mode));
+    } else {
+      TRY(apply_C(c, x, ldx, R, N, cc, false, mode));
+      TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));
+    }
     return worst_of(worst);
   };
   int it = 0;
@@ -1362,8 +1396,11 @@ int wcs_solve_rhs(wcs_ctx* c, int64_t B, const double* e, const double* hv, int6
   double rr = 0;
   for (int64_t c0 = 0; c0 < B; c0 += chunk) {
     const int64_t cc = std::min(chunk, B - c0);
-    TRY(precondition(c, (const zd*)e + c0 * ld, (const zd*)hv + c0 * ld, ld, bb.z(), N, cc));
-    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr);
+    // mixed form: b only seeds the solution (residuals are formed from e, h)
+    const zd* ec = (const zd*)e + c0 * ld;
+    const zd* hc = (const zd*)hv + c0 * ld;
+    TRY(precondition(c, ec, hc, ld, bb.z(), N, cc, c->mixed ? PREC_PERIODIC : PREC_ACCURATE));
+    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr, ec, hc, ld);
     if (r == WCS_ERR_NOT_CONVERGED) status = r;
     else if (r) return r;
   }
@@ -1393,9 +1430,9 @@ int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j,
   for (int64_t c0 = 0; c0 < B; c0 += chunk) {
     const int64_t cc = std::min(chunk, B - c0);
     TRY(planewave_rhs(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, N, c->h, c->k, ang.d() + c0,
-                      (int)cc, eb.z(), hb.z(), N, c->s));
-    TRY(precondition(c, eb.z(), hb.z(), N, bb.z(), N, cc));
-    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr);
+                      (int)cc, eb.z(), hb.z(), N, c->s, c->mixed));
+    TRY(precondition(c, eb.z(), hb.z(), N, bb.z(), N, cc, c->mixed ? PREC_PERIODIC : PREC_ACCURATE));
+    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr, eb.z(), hb.z(), N);
     if (r == WCS_ERR_NOT_CONVERGED) status = r;
     else if (r) return r;
   }
