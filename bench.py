@@ -40,6 +40,21 @@ def peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def measured_traffic_ratio():
+    """DRAM bytes (read + write) per algorithmic byte of the operator-product
+    contraction, from the ncu capture summarised in profiles/ (a small case of
+    the same kernel; the traffic of a launch scales with its planes read)."""
+    path = os.path.join(ROOT, "profiles", "k_gemm_tc_ellipse_n4096_mixed.md")
+    try:
+        with open(path) as f:
+            for line in f:
+                if line.startswith("dram_bytes_per_algorithmic_byte:"):
+                    return float(line.split(":")[1]), "profiles/k_gemm_tc_ellipse_n4096_mixed.md"
+    except OSError:
+        pass
+    return None, None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -245,14 +260,18 @@ def main():
     del jh
 
     hbm, bf16, bf16s, src = peaks()
+    traffic_ratio, traffic_src = measured_traffic_ratio()
     g = prof["gemm_tc"]
     a = prof["assembly"]
     roof = None
     if g["launches"]:
         ms_per = g["ms"] / g["launches"]
         achieved = g["work"] / g["launches"] / (ms_per / 1e3) / 1e12
+        alg_bytes = g["bytes"] / g["launches"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s",
-                "frac": achieved / bf16s, "traffic": None,
+                "frac": achieved / bf16s,
+                "traffic": (traffic_ratio * alg_bytes) if traffic_ratio else None,
+                "algorithmic_bytes_per_launch": alg_bytes, "traffic_source": traffic_src,
                 "kernel": "k_gemm_tc (tcgen05 split-bf16 complex operator product)",
                 "work": "useful complex-product flops 2*M*Nc*K (split-bf16 executes nprod x these)",
                 "peak_source": f"{src} bf16 sustained", "launches": g["launches"], "ms_total": g["ms"]}

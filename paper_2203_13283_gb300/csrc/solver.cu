@@ -184,6 +184,13 @@ static int check_tc(wcs_ctx* c);
 //                  with |dx|
 enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2 };
 
+// Algorithmic HBM bytes of one contraction: every plane of A and B read once,
+// the complex FP64 output written (and read when beta != 0).
+static double tc_bytes(const TcArgs& t, int pa, int pb) {
+  const double out = 16.0 * t.M * (t.Nc / 2) * ((t.beta.x != 0.0 || t.beta.y != 0.0) ? 2.0 : 1.0);
+  return 2.0 * ((double)pa * t.M * t.K + (double)pb * t.Nc * t.K) + out;
+}
+
 static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols, zd alpha, zd beta, zd* Y,
                     int64_t ldy, int mode = PREC_FAST) {
   const bool accurate = (mode == PREC_ACCURATE);
@@ -209,7 +216,8 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.beta = beta;
   t.err = (int*)c->tcerr.p;
   t.drain = (mode == PREC_PERIODIC) ? 64 : 1;
-  ProfScope ps(c, mode != PREC_FAST ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  ProfScope ps(c, mode != PREC_FAST ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K,
+               tc_bytes(t, P, P));
   TRY(mode != PREC_FAST ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
   if (debug_finite()) {
     int r = check_tc(c);
@@ -267,7 +275,7 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
   TRY(c->gW.ensure((size_t)32 << 20));
   t.ws = (float*)c->gW.p;
   t.ws_elems = (int64_t)(c->gW.bytes / sizeof(float));
-  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, tc_bytes(t, P, P));
   TRY(gemm_tc(oa, ob, t, c->s));
   return 0;
 }
@@ -302,7 +310,7 @@ static int cgemm_planes(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, c
   TRY(c->gW.ensure((size_t)32 << 20));
   t.ws = (float*)c->gW.p;
   t.ws_elems = (int64_t)(c->gW.bytes / sizeof(float));
-  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, 0.0);
+  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, tc_bytes(t, P, P));
   TRY(gemm_tc(oa, ob, t, c->s));
   return 0;
 }
