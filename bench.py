@@ -163,6 +163,8 @@ def main():
                     help="skeleton rank cap (default N/8 in the mixed form, none in FP64)")
     ap.add_argument("--refine-tol", type=float, default=None)
     ap.add_argument("--rhs", type=int, default=None)
+    ap.add_argument("--sample-planes", type=int, default=0,
+                    help="mixed form: bf16 planes in the skeleton's sampling products (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -191,7 +193,7 @@ def main():
     max_rank = args.max_rank if args.max_rank is not None else (w["N"] // 8 if mixed else 0)
     rtol = args.refine_tol if args.refine_tol is not None else (1e-7 if mixed else 1e-12)
     S = Solver(device=f"cuda:{local}", precision=1 if mixed else 0, refine_tol=rtol, max_refine=12,
-               rhs_chunk=1024 if mixed else 256, block=64)
+               rhs_chunk=1024 if mixed else 256, block=64, sample_planes=args.sample_planes)
     stream = S.stream
     angles = w["angles"]
     B = len(angles)

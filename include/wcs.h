@@ -58,7 +58,9 @@ typedef struct wcs_options {
   int precision;      /* wcs_precision */
   int q_far;          /* Gauss points per element for element pairs farther than near_band
                          (default 0 = automatic: 6 in the FP64 form, 4 in the mixed form) */
-  int q_near;         /* Gauss points per element for near and singular pairs (default 12, max 16) */
+  int q_near;         /* Gauss points per element for near and singular pairs (default 0 =
+                         automatic: 12 in the FP64 form, 8 in the mixed form, where entries
+                         need ~1e-9; max 16) */
   int near_band;      /* periodic element distance treated as near (default 4) */
   int block;          /* randomized sampling block width (default 32, max 64) */
   int max_refine;     /* maximum iterative-refinement steps per solve (default 12) */
@@ -67,7 +69,9 @@ typedef struct wcs_options {
   int mixed_planes;   /* mixed form: bf16 planes per operator entry (default 3, max 3) */
   int rhs_planes;     /* mixed form: bf16 planes per staged vector entry (= mixed_planes) */
   double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h use the FP32 path (default 9) */
-  int reserved[2];
+  int sample_planes;  /* mixed form: bf16 planes of each operand in the skeleton's sampling
+                         products (default 0 = 2; 1 = one product per pass, ~4e-3 relative) */
+  int reserved;
 } wcs_options;
 
 typedef struct wcs_info {

@@ -20,7 +20,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("q_far", C.c_int), ("q_near", C.c_int),
                 ("near_band", C.c_int), ("block", C.c_int), ("max_refine", C.c_int),
                 ("refine_tol", C.c_double), ("rhs_chunk", C.c_int), ("mixed_planes", C.c_int),
-                ("rhs_planes", C.c_int), ("zfast", C.c_double), ("reserved", C.c_int * 2)]
+                ("rhs_planes", C.c_int), ("zfast", C.c_double), ("sample_planes", C.c_int),
+                ("reserved", C.c_int)]
 
 
 class Info(C.Structure):

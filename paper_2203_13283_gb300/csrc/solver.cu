@@ -182,7 +182,9 @@ static int check_tc(wcs_ctx* c);
 //   PREC_PERIODIC  two leading planes, accumulator drained every 64 steps
 //                  (~1e-5): residual updates R <- R - C dx, whose error scales
 //                  with |dx|
-enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2 };
+//   PREC_FAST1     leading plane only, one product (~4e-3): optional skeleton
+//                  sampling (sample_planes = 1)
+enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2, PREC_FAST1 = 3 };
 
 // Algorithmic HBM bytes of one contraction: every plane of A and B read once,
 // the complex FP64 output written (and read when beta != 0).
@@ -194,7 +196,8 @@ static double tc_bytes(const TcArgs& t, int pa, int pb) {
 static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols, zd alpha, zd beta, zd* Y,
                     int64_t ldy, int mode = PREC_FAST) {
   const bool accurate = (mode == PREC_ACCURATE);
-  const int P = accurate ? std::min(c->planes, c->rhs_planes) : std::min(2, std::min(c->planes, c->rhs_planes));
+  const int P = accurate ? std::min(c->planes, c->rhs_planes)
+                         : (mode == PREC_FAST1 ? 1 : std::min(2, std::min(c->planes, c->rhs_planes)));
   TcOperand A, B;
   A.planes = P;
   A.ld = c->ldp;
@@ -216,9 +219,10 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.beta = beta;
   t.err = (int*)c->tcerr.p;
   t.drain = (mode == PREC_PERIODIC) ? 64 : 1;
-  ProfScope ps(c, mode != PREC_FAST ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K,
+  const bool drained = (mode == PREC_ACCURATE || mode == PREC_PERIODIC);
+  ProfScope ps(c, drained ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K,
                tc_bytes(t, P, P));
-  TRY(mode != PREC_FAST ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
+  TRY(drained ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
   if (debug_finite()) {
     int r = check_tc(c);
     if (r) fprintf(stderr, "[wcs debug] operator product op=%d adj=%d mode=%d M=%d Nc=%d K=%d: %s\n", op,
@@ -397,8 +401,8 @@ static int apply_Cc(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, in
 
 // Y = (C - C_c) X or its adjoint; uses w1, w2, w3.
 static int apply_remainder(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols,
-                           bool adj) {
-  TRY(apply_C(c, X, ldx, Y, ldy, cols, adj));
+                           bool adj, int mode = PREC_FAST) {
+  TRY(apply_C(c, X, ldx, Y, ldy, cols, adj, mode));
   zd* T3 = c->w3.z();
   TRY(apply_Cc(c, X, ldx, T3, c->N, cols, adj ? 1 : 0));
   TRY(axpby(c->N, cols, mkz(-1.0), T3, c->N, mkz(1.0), Y, ldy, c->s));
@@ -592,7 +596,7 @@ int wcs_default_options(wcs_options* o) {
   std::memset(o, 0, sizeof(*o));
   o->precision = WCS_PREC_FP64;
   o->q_far = 0;   // automatic: 6 (FP64 form) or 4 (mixed form)
-  o->q_near = 12;
+  o->q_near = 0;   // automatic: 12 (FP64 form) or 8 (mixed form)
   o->near_band = 4;
   o->block = 32;
   o->max_refine = 12;
@@ -614,6 +618,9 @@ int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream) {
     return WCS_ERR_ARG;
   }
   if (o.q_far == 0) o.q_far = (o.precision == WCS_PREC_MIXED) ? 4 : 6;
+  if (o.q_near == 0) o.q_near = (o.precision == WCS_PREC_MIXED) ? 8 : 12;
+  if (o.sample_planes == 0) o.sample_planes = 2;
+  if (o.sample_planes < 1 || o.sample_planes > 2) { set_error("sample_planes must be 1 or 2"); return WCS_ERR_ARG; }
   if (o.q_far < 2 || o.q_far > 16 || o.q_near < 4 || o.q_near > 16 || o.near_band < 1 ||
       o.block < 1 || o.block > 64 || o.rhs_chunk < 1 || o.max_refine < 0) {
     set_error("option out of range");
@@ -1051,7 +1058,8 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
       TRY(gaussian_fill(Om, N, N, batch_cols, seed, offset, c->s));
       TRY(dbg_check(c, Om, N, batch_cols, N, "gaussian"));
       offset += (uint64_t)N * batch_cols;
-      TRY(apply_remainder(c, Om, N, Ys, N, batch_cols, false));
+      TRY(apply_remainder(c, Om, N, Ys, N, batch_cols, false,
+                          (c->mixed && c->opt.sample_planes == 1) ? PREC_FAST1 : PREC_FAST));
       TRY(dbg_check(c, Ys, N, batch_cols, N, "sample"));
     }
     zd* Y = Ys + batch_used * N;

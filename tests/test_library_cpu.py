@@ -40,7 +40,7 @@ def test_exports_every_declared_symbol(lib):
 def test_options_defaults(lib):
     from paper_2203_13283_gb300.solver import default_options
     o = default_options()
-    assert (o.q_far, o.q_near, o.near_band, o.precision) == (0, 12, 4, 0)
+    assert (o.q_far, o.q_near, o.near_band, o.precision, o.sample_planes) == (0, 0, 4, 0, 0)
 
 
 @pytest.mark.parametrize("q", [8, 12])
