@@ -181,6 +181,21 @@ int wcs_skeleton(wcs_ctx* ctx, double tol, int max_rank, uint64_t seed, int* ran
  * of Eq. (9). */
 int wcs_factor(wcs_ctx* ctx);
 
+/* Checkpoint of a factored context.  The paper defines no file format; this
+ * stores what the solve of Eq. (9) needs beyond the operators: the single
+ * skeleton U V^T of Eq. (7) (U = Q and V_w = conj(V), N x rank each) and
+ * W~ = C_c^-1 U (I + V^T C_c^-1 U)^-1, plus the contour, N, k and the
+ * options, in a host file at `path` (complex FP64, about 48 N rank bytes).
+ * The operators are not stored.  wcs_load re-runs the mesh and the assembly,
+ * which are deterministic, on a context created with the same precision and
+ * quadrature options (else WCS_ERR_ARG), then restores the factors; the
+ * context is then in the factored state.  Both synchronise the context
+ * stream.  Errors: WCS_ERR_STATE (save before wcs_factor), WCS_ERR_ARG
+ * (null arguments, unreadable/truncated/foreign file, option mismatch),
+ * or the status of the mesh/assembly step. */
+int wcs_save(wcs_ctx* ctx, const char* path);
+int wcs_load(wcs_ctx* ctx, const char* path);
+
 /* x = C^-1 b through Eq. (9) only (no refinement), B columns, device pointers. */
 int wcs_woodbury_apply(wcs_ctx* ctx, int64_t B, const double* b_dev, int64_t ldb, double* x_dev,
                        int64_t ldx);

@@ -6,7 +6,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libwcs.so")
 
-WCS_OK, WCS_ERR_NOT_CONVERGED, WCS_ERR_RANK_CAP = 0, 7, 6
+WCS_OK, WCS_ERR_ARG, WCS_ERR_NOT_CONVERGED, WCS_ERR_RANK_CAP = 0, 1, 7, 6
 STATUS_NAMES = {0: "WCS_OK", 1: "WCS_ERR_ARG", 2: "WCS_ERR_NOT_CONVEX", 3: "WCS_ERR_CUDA",
                 4: "WCS_ERR_OOM", 5: "WCS_ERR_SINGULAR", 6: "WCS_ERR_RANK_CAP",
                 7: "WCS_ERR_NOT_CONVERGED", 8: "WCS_ERR_TIMEOUT", 9: "WCS_ERR_STATE",
@@ -55,6 +55,8 @@ SIGNATURES = {
     "wcs_apply": (I, [P, I, I64, P, I64, P, I64]),
     "wcs_skeleton": (I, [P, D, I, U64, C.POINTER(I)]),
     "wcs_factor": (I, [P]),
+    "wcs_save": (I, [P, C.c_char_p]),
+    "wcs_load": (I, [P, C.c_char_p]),
     "wcs_woodbury_apply": (I, [P, I64, P, I64, P, I64]),
     "wcs_solve_planewaves": (I, [P, I64, P, P, I64, C.POINTER(SolveInfo)]),
     "wcs_solve_planewaves_host": (I, [P, I64, P, P, I64, C.POINTER(SolveInfo)]),

@@ -29,9 +29,17 @@ using namespace wcs;
 
 enum Stage { ST_NEW = 0, ST_CONTOUR = 1, ST_MESH = 2, ST_ASSEMBLED = 3, ST_SKELETON = 4, ST_FACTORED = 5 };
 
+// Owned device buffer: grows on demand (contents not kept), freed by release()
+// or when it goes out of scope; not copyable.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
   int ensure(size_t b) {
     if (b <= bytes) return 0;
     cudaFree(p);
@@ -82,6 +90,7 @@ struct wcs_ctx {
   DevBuf gW;                 // split-K workspace of the small contractions (FP32)
   DevBuf qh, qt;             // skeleton basis as resident bf16 planes: rows conj(q_i); rows of Q
   DevBuf gA, gB;                          // staging for general complex tensor products
+  DevBuf sol_e, sol_h, sol_b, sol_ang, sol_j;   // solve blocks (grow-only, kept across calls)
   // optional per-kernel timing: CUDA events on the context stream
   bool profile = false;
   struct Rec { int cat; cudaEvent_t a, b; double flops, bytes; };
@@ -649,6 +658,7 @@ static void free_mesh(wcs_ctx* c) {
   c->stage0.release(); c->stage1.release(); c->stage2.release(); c->stage_cols = 0;
   c->gA.release(); c->gB.release(); c->gW.release(); c->qh.release(); c->qt.release();
   c->U.release(); c->Vw.release(); c->Wt.release();
+  c->sol_e.release(); c->sol_h.release(); c->sol_b.release(); c->sol_ang.release(); c->sol_j.release();
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
   c->rank = -1;
 }
@@ -1226,6 +1236,104 @@ int wcs_factor(wcs_ctx* c) {
   return WCS_OK;
 }
 
+// ---------------------------------------------------------------- checkpoint
+// Binary file: header, then U, V_w and W~ (N x rank complex FP64 each, column
+// by column).  The operators are not stored: loading re-runs the mesh and
+// the assembly, which are deterministic, and which the refinement needs anyway.
+struct CkptHeader {
+  char magic[8];
+  int32_t version;
+  int32_t rank;
+  int64_t N;
+  double k;
+  wcs_options opt;
+  Contour contour;
+};
+static const char kCkptMagic[8] = {'W', 'C', 'S', 'C', 'K', 'P', 'T', '1'};
+
+static int ckpt_arrays(wcs_ctx* c, FILE* f, bool write) {
+  const int64_t N = c->N, r = c->rank;
+  if (r <= 0) return 0;
+  zd* arrs[3] = {c->U.z(), c->Vw.z(), c->Wt.z()};
+  const int64_t chunk = std::max<int64_t>(1, ((int64_t)64 << 20) / (int64_t)(sizeof(zd) * N));   // columns
+  std::vector<zd> host((size_t)N * std::min(chunk, r));
+  for (int a = 0; a < 3; ++a) {
+    for (int64_t c0 = 0; c0 < r; c0 += chunk) {
+      const int64_t cc = std::min(chunk, r - c0);
+      const size_t n = (size_t)N * cc;
+      if (write) {
+        cudaMemcpyAsync(host.data(), arrs[a] + c0 * N, sizeof(zd) * n, cudaMemcpyDeviceToHost, c->s);
+        TRY(sync(c));
+        if (fwrite(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: write failed"); return WCS_ERR_ARG; }
+      } else {
+        if (fread(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
+        cudaMemcpyAsync(arrs[a] + c0 * N, host.data(), sizeof(zd) * n, cudaMemcpyHostToDevice, c->s);
+        TRY(sync(c));
+      }
+    }
+  }
+  return 0;
+}
+
+int wcs_save(wcs_ctx* c, const char* path) {
+  if (!c || !path) { set_error("bad argument"); return WCS_ERR_ARG; }
+  if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
+  FILE* f = fopen(path, "wb");
+  if (!f) { set_error(std::string("checkpoint: cannot open ") + path); return WCS_ERR_ARG; }
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.rank = c->rank;
+  hd.N = c->N;
+  hd.k = c->k;
+  hd.opt = c->opt;
+  hd.contour = c->contour;
+  int r = (fwrite(&hd, sizeof(hd), 1, f) == 1) ? 0 : WCS_ERR_ARG;
+  if (r) set_error("checkpoint: write failed");
+  if (!r) r = ckpt_arrays(c, f, true);
+  if (fclose(f) != 0 && !r) { set_error("checkpoint: write failed"); r = WCS_ERR_ARG; }
+  return r;
+}
+
+int wcs_load(wcs_ctx* c, const char* path) {
+  if (!c || !path) { set_error("bad argument"); return WCS_ERR_ARG; }
+  FILE* f = fopen(path, "rb");
+  if (!f) { set_error(std::string("checkpoint: cannot open ") + path); return WCS_ERR_ARG; }
+  CkptHeader hd;
+  int r = 0;
+  if (fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1) {
+    set_error("checkpoint: not a checkpoint of this library");
+    r = WCS_ERR_ARG;
+  }
+  // the factors only fit operators assembled the same way
+  const wcs_options& o = c->opt;
+  if (!r && (hd.opt.precision != o.precision || hd.opt.q_far != o.q_far || hd.opt.q_near != o.q_near ||
+             hd.opt.near_band != o.near_band || hd.opt.mixed_planes != o.mixed_planes ||
+             hd.opt.rhs_planes != o.rhs_planes || hd.opt.zfast != o.zfast)) {
+    set_error("checkpoint: made with other precision or quadrature options than this context");
+    r = WCS_ERR_ARG;
+  }
+  if (!r && (hd.N < 12 || hd.rank < 0 || hd.rank > hd.N)) { set_error("checkpoint: bad sizes"); r = WCS_ERR_ARG; }
+  if (!r) r = set_contour(c, hd.contour);
+  if (!r) r = wcs_mesh(c, hd.N, hd.k);
+  if (!r) r = wcs_assemble(c);
+  if (!r && hd.rank > 0) {
+    const size_t b = sizeof(zd) * (size_t)hd.N * hd.rank;
+    r = c->U.ensure(b);
+    if (!r) r = c->Vw.ensure(b);
+    if (!r) r = c->Wt.ensure(b);
+  }
+  if (!r) {
+    c->rank = hd.rank;
+    r = ckpt_arrays(c, f, false);
+  }
+  fclose(f);
+  if (r) return r;
+  c->stage = ST_FACTORED;
+  return WCS_OK;
+}
+
 int wcs_woodbury_apply(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
   if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
@@ -1434,7 +1542,7 @@ int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j,
   if (B == 0) return WCS_OK;
   const int64_t chunk = c->opt.rhs_chunk, N = c->N;
   TRY(ensure_work(c, std::min(B, chunk)));
-  DevBuf eb, hb, bb, ang;
+  DevBuf &eb = c->sol_e, &hb = c->sol_h, &bb = c->sol_b, &ang = c->sol_ang;
   const int64_t cmax = std::min(B, chunk);
   TRY(eb.ensure(sizeof(zd) * N * cmax));
   TRY(hb.ensure(sizeof(zd) * N * cmax));
@@ -1461,14 +1569,13 @@ int wcs_solve_planewaves_host(wcs_ctx* c, int64_t B, const double* angles, doubl
                               int64_t ldj, wcs_solve_info* info) {
   if (!c || (B > 0 && (!angles || !j_host)) || ldj < (c ? c->N : 0)) { set_error("bad argument"); return WCS_ERR_ARG; }
   if (B == 0) return WCS_OK;
-  DevBuf jd;
+  DevBuf& jd = c->sol_j;
   TRY(jd.ensure(sizeof(zd) * c->N * B));
   int r = wcs_solve_planewaves(c, B, angles, jd.d(), c->N, info);
-  if (r && r != WCS_ERR_NOT_CONVERGED) { jd.release(); return r; }
+  if (r && r != WCS_ERR_NOT_CONVERGED) return r;
   cudaMemcpy2DAsync(j_host, sizeof(zd) * ldj, jd.p, sizeof(zd) * c->N, sizeof(zd) * c->N, B,
                     cudaMemcpyDeviceToHost, c->s);
   int r2 = sync(c);
-  jd.release();
   return r2 ? r2 : r;
 }
 

@@ -105,6 +105,18 @@ class Solver:
         check(self.lib.wcs_factor(self.h))
         return self
 
+    def save(self, path):
+        """Write the skeleton and Woodbury factors (host file; see wcs_save)."""
+        check(self.lib.wcs_save(self.h, str(path).encode()))
+        return self
+
+    def load(self, path):
+        """Rebuild mesh and operators and restore the factors written by save()."""
+        check(self.lib.wcs_load(self.h, str(path).encode()))
+        info = self.info()
+        self.N = int(info["N"])
+        return self
+
     # ---- blocks: (N, B) views of column-major storage
     def _block(self, B):
         return torch.empty((B, self.N), dtype=torch.complex128, device=self.device)

@@ -72,3 +72,10 @@ def test_product_weights_symmetry(lib):
     assert np.max(np.abs(W[0] - W[0].T)) < 1e-14
     # log(xi + 1 - eta) is log(1 - xi' + eta') with the roles of xi and eta swapped
     assert np.max(np.abs(W[2] - W[1].T)) < 1e-14
+
+
+def test_checkpoint_rejects_null_arguments(lib):
+    """wcs_save / wcs_load validate their arguments before touching a device."""
+    from paper_2203_13283_gb300._lib import WCS_ERR_ARG
+    assert lib.wcs_save(None, b"/nonexistent/ckpt") == WCS_ERR_ARG
+    assert lib.wcs_load(None, b"/nonexistent/ckpt") == WCS_ERR_ARG
