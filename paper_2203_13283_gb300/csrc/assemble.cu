@@ -23,6 +23,7 @@
 namespace wcs {
 
 __constant__ double c_xf[16], c_wf[16], c_xn[16], c_wn[16];
+__constant__ float c_xff[16], c_wff[16];   // the far rule in FP32 (no FP64 conversion per point pair)
 
 struct PairOut {
   zd v[4][4];  // [operator S~, D, D~, N][a * 2 + b]
@@ -214,21 +215,56 @@ __device__ void pair_fast(const AsmArgs& A, int64_t e, int64_t f, PairOut& out) 
     for (int j = 0; j < 4; ++j) out.v[op][j] = mkz((double)o.v[op][j].x, (double)o.v[op][j].y);
 }
 
+// Float-float arithmetic (value = hi + lo, ~48 bits; Dekker/Knuth error-free
+// transformations).  The far-pair phase k |c_e - c_f| mod 2 pi needs ~1e-7
+// absolute accuracy at k R ~ 2e4; float-float gives ~1e-10 without touching
+// the FP64 pipe, which runs at 1/64 of the FP32 rate on this GPU.
+struct ff {
+  float hi, lo;
+};
+__device__ __forceinline__ ff ff_quick(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ ff ff_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ ff ff_two_prod(float a, float b) {
+  const float p = a * b;
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b) {
+  const ff s = ff_two_sum(a.hi, b.hi);
+  return ff_quick(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+  ff p = ff_two_prod(a.hi, b.hi);
+  return ff_quick(p.hi, p.lo + fmaf(a.hi, b.lo, a.lo * b.hi));
+}
+__device__ __forceinline__ ff ff_sqrt(ff a) {
+  // one Newton step from the FP32 root: x + (a - x^2) / (2x)
+  const float x = sqrtf(a.hi);
+  const ff d = ff_add(a, ff_neg(ff_two_prod(x, x)));
+  return ff_quick(x, d.hi * (0.5f / x));
+}
+
 __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& out) {
   const int q = A.q_far;
-  const double dx0 = A.cx[e] - A.cx[f], dy0 = A.cy[e] - A.cy[f];
-  // R0 from an FP32 square root and one Newton step in FP64 (relative error
-  // ~1e-15, enough for the phase k R0 ~ 1e4); the FP64 work per pair stays a
-  // handful of operations
-  const double r2 = fma(dx0, dx0, dy0 * dy0);
-  const float sf = sqrtf((float)r2);
-  const double R0 = (double)sf + fma(-(double)sf, (double)sf, r2) * (double)(0.5f / sf);
-  const double kR0 = A.k * R0;
-  const double twopi_hi = 6.283185307179586, twopi_lo = 2.4492935982947064e-16;
-  const double nrev = rint(kR0 * (1.0 / twopi_hi));
-  const float ph0 = (float)fma(-nrev, twopi_lo, fma(-nrev, twopi_hi, kR0));
-  const float fdx0 = (float)dx0, fdy0 = (float)dy0, fR0 = (float)R0;
   const FastConsts& F = A.fk;
+  const float4 ce = A.cff[e], cf_ = A.cff[f];   // (x hi, x lo, y hi, y lo)
+  const ff dx = ff_add(ff_two_sum(ce.x, -cf_.x), ff_two_sum(ce.y, -cf_.y));
+  const ff dy = ff_add(ff_two_sum(ce.z, -cf_.z), ff_two_sum(ce.w, -cf_.w));
+  const ff R0 = ff_sqrt(ff_add(ff_mul(dx, dx), ff_mul(dy, dy)));
+  const ff kR0 = ff_mul({F.k_hi, F.k_lo}, R0);
+  // kR0 - n 2pi with 2pi = t1 + t2 + t3 (24 + 24 + 24 bits); n < 2^13 so n t1, n t2 are exact products
+  const float n = rintf(kR0.hi * 0.15915494309189535f);
+  ff t = ff_add(kR0, ff_neg(ff_two_prod(n, F.twopi[0])));
+  t = ff_add(t, ff_neg(ff_two_prod(n, F.twopi[1])));
+  const float ph0 = (t.hi + t.lo) - n * F.twopi[2];
+  const float fdx0 = dx.hi, fdy0 = dy.hi, fR0 = R0.hi;
   const float k = F.kf, beta = F.beta;
   const cf ck = {F.ck[0], F.ck[1]};      // sqrt(2 / (pi k~))
   const cf ik = {F.ik[0], F.ik[1]};      // i / k~
@@ -243,7 +279,7 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
   for (int p = 0; p < q; ++p) {
     const int64_t ip = e * q + p;
     const float oxp = A.ox[ip], oyp = A.oy[ip], nxt = A.nxf[ip], nyt = A.nyf[ip];
-    const float xip = (float)c_xf[p], wp = (float)c_wf[p];
+    const float xip = c_xff[p], wp = c_wff[p];
     for (int r = 0; r < q; ++r) {
       const int64_t ir = f * q + r;
       const float dx = oxp - A.ox[ir], dy = oyp - A.oy[ir];
@@ -289,9 +325,9 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
       const cf gt = {-0.25f * Ht0.y, 0.25f * Ht0.x};
       const cf dgt = cscale(cmul(kt4, Ht1), gg);
       const float ph[2] = {1.f - xip, xip};
-      const float xir = (float)c_xf[r];
+      const float xir = c_xff[r];
       const float ps[2] = {1.f - xir, xir};
-      const float w2 = wp * (float)c_wf[r];
+      const float w2 = wp * c_wff[r];
 #pragma unroll
       for (int aa = 0; aa < 2; ++aa)
 #pragma unroll
@@ -320,7 +356,8 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
 
 __device__ __forceinline__ bool fast_ok(const AsmArgs& A, int64_t e, int64_t f) {
   if (periodic_dist(e, f, A.N) <= A.near_band) return false;
-  const float dx0 = (float)(A.cx[e] - A.cx[f]), dy0 = (float)(A.cy[e] - A.cy[f]);
+  const float4 ce = A.cff[e], cf_ = A.cff[f];
+  const float dx0 = ce.x - cf_.x, dy0 = ce.z - cf_.z;
   return A.fk.kf * A.fk.kf * (dx0 * dx0 + dy0 * dy0) >= A.fk.zfast2;
 }
 
@@ -460,6 +497,10 @@ static int upload_rules(const AsmArgs& A) {
   if (cudaMemcpyToSymbol(c_wf, wf, sizeof(double) * A.q_far) != cudaSuccess) return 3;
   if (cudaMemcpyToSymbol(c_xn, xn, sizeof(double) * A.q_near) != cudaSuccess) return 3;
   if (cudaMemcpyToSymbol(c_wn, wn, sizeof(double) * A.q_near) != cudaSuccess) return 3;
+  float xff[16], wff[16];
+  for (int i = 0; i < A.q_far; ++i) { xff[i] = (float)xf[i]; wff[i] = (float)wf[i]; }
+  if (cudaMemcpyToSymbol(c_xff, xff, sizeof(float) * A.q_far) != cudaSuccess) return 3;
+  if (cudaMemcpyToSymbol(c_wff, wff, sizeof(float) * A.q_far) != cudaSuccess) return 3;
   return 0;
 }
 
@@ -632,9 +673,18 @@ __global__ void k_far_offsets(Points far, const double* cx, const double* cy, in
   nyf[t] = (float)far.ny[t];
 }
 
+__global__ void k_centres_ff(const double* cx, const double* cy, int64_t N, float4* cff) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= N) return;
+  const float xh = (float)cx[e], yh = (float)cy[e];
+  cff[e] = make_float4(xh, (float)(cx[e] - (double)xh), yh, (float)(cy[e] - (double)yh));
+}
+
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                float* oy, float* nxf, float* nyf, cudaStream_t s) {
+                float* oy, float* nxf, float* nyf, float4* cff, cudaStream_t s) {
   k_far_offsets<<<(unsigned)((N * q + 255) / 256), 256, 0, s>>>(far, cx, cy, N, q, ox, oy, nxf, nyf);
+  note_launch();
+  k_centres_ff<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(cx, cy, N, cff);
   note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("far offsets: ") + cudaGetErrorString(err)); return 3; }

@@ -64,6 +64,8 @@ struct FastConsts {
   float ampk = 0.f;                // sqrt(2 / (pi k))
   float kk2h2 = 0.f, h2 = 0.f;     // k^2 h^2, h^2
   float zfast2 = 0.f;              // zfast^2 (pair test k^2 |c_e - c_f|^2 >= zfast^2)
+  float k_hi = 0.f, k_lo = 0.f;    // k as a float-float pair
+  float twopi[3] = {0.f, 0.f, 0.f};   // 2 pi = twopi[0] + twopi[1] + twopi[2]
 };
 
 struct AsmArgs {
@@ -88,6 +90,7 @@ struct AsmArgs {
   const double *cx = nullptr, *cy = nullptr;     // element centres (xi = 1/2)
   const float *ox = nullptr, *oy = nullptr;      // far points minus their element centre
   const float *nxf = nullptr, *nyf = nullptr;    // far-point normals (FP32)
+  const float4* cff = nullptr;                   // element centres as float-float (x hi, x lo, y hi, y lo)
   double zfast = 1e300;
   FastConsts fk;
   const uint8_t* tile_flags = nullptr;           // mixed tile kernel: only flagged tiles
@@ -97,7 +100,7 @@ int assemble_dense(const AsmArgs& a, cudaStream_t s);
 int assemble_planes(const AsmArgs& a, cudaStream_t s);
 // FP32 offset tables of the far points relative to element centres.
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                float* oy, float* nxf, float* nyf, cudaStream_t s);
+                float* oy, float* nxf, float* nyf, float4* cff, cudaStream_t s);
 // First row of the four circulant operators on the circle (row 0, N entries each).
 int assemble_circle_row(const AsmArgs& a, cudaStream_t s);
 // Sampled entries (row, col) of the four operators, computed point-wise.

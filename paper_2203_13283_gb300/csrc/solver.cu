@@ -820,6 +820,13 @@ static void set_fast_consts(AsmArgs& A) {
   F.kk2h2 = (float)(A.k * A.k * A.h * A.h);
   F.h2 = (float)(A.h * A.h);
   F.zfast2 = (float)(A.zfast * A.zfast);
+  F.k_hi = (float)A.k;
+  F.k_lo = (float)(A.k - (double)F.k_hi);
+  const double tp = 2.0 * WCS_PI;   // 2 pi to ~72 bits: double plus its float-float residual
+  const double tp_lo = 2.4492935982947064e-16;
+  F.twopi[0] = (float)tp;
+  F.twopi[1] = (float)(tp - (double)F.twopi[0]);
+  F.twopi[2] = (float)((tp - (double)F.twopi[0] - (double)F.twopi[1]) + tp_lo);
 }
 
 __global__ void k_geom_sample_dummy() {}
@@ -875,9 +882,10 @@ int wcs_assemble(wcs_ctx* c) {
     Points cp;
     cp.x = c->centres.d(); cp.y = cp.x + N; cp.nx = cp.y + N; cp.ny = cp.nx + N; cp.kappa = nullptr; cp.n = N;
     TRY(points_build(c->contour, c->arc, N, c->h, half, 1, cp, c->s));
-    TRY(c->offs.ensure(sizeof(float) * 4 * N * qf));
+    TRY(c->offs.ensure(sizeof(float) * 4 * N * (qf + 1)));
     float* of = (float*)c->offs.p;
-    TRY(far_offsets(c->far, cp.x, cp.y, N, qf, of, of + N * qf, of + 2 * N * qf, of + 3 * N * qf, c->s));
+    float4* cff = (float4*)(of + 4 * N * qf);
+    TRY(far_offsets(c->far, cp.x, cp.y, N, qf, of, of + N * qf, of + 2 * N * qf, of + 3 * N * qf, cff, c->s));
     AsmArgs A = asm_args(c, false);
     A.mixed = 1;
     A.planes = c->planes;
@@ -887,6 +895,7 @@ int wcs_assemble(wcs_ctx* c) {
         for (int p = 0; p < 3; ++p) A.P[op][l][p] = (p < c->planes) ? plane_ptr(c, op, l, p) : nullptr;
     A.cx = cp.x; A.cy = cp.y;
     A.ox = of; A.oy = of + N * qf; A.nxf = of + 2 * N * qf; A.nyf = of + 3 * N * qf;
+    A.cff = cff;
     A.zfast = c->opt.zfast + 2.0 * c->k * c->h;
     set_fast_consts(A);
     ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * qf * qf, 0.0);   // units: far point pairs
@@ -1023,11 +1032,11 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   const int64_t cap = (max_rank <= 0 || max_rank > N) ? N : max_rank;
   const int b = c->opt.block;
   ProfScope whole(c, CAT_SKELETON, 0.0, 0.0);
-  // samples are drawn SB = 4b columns per pass over the operators and
-  // orthonormalised b columns at a time; Y is linear in Omega and Omega's
-  // columns come from one counter stream, so the basis is the one of the
-  // b-column loop
-  const int64_t SB = std::min<int64_t>(4 * (int64_t)b, ((cap + b - 1) / b) * b);
+  // samples are drawn SB = 8b columns per pass over the operators (wide
+  // products fill the GPU in whole waves) and orthonormalised b columns at a
+  // time; Y is linear in Omega and Omega's columns come from one counter
+  // stream, so the basis is the one of the b-column loop
+  const int64_t SB = std::min<int64_t>(8 * (int64_t)b, ((cap + b - 1) / b) * b);
   TRY(ensure_work(c, SB));
   TRY(c->U.ensure(sizeof(zd) * N * (cap + b)));
   zd* Q = c->U.z();

@@ -167,15 +167,24 @@ class Solver:
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
         return j.t()
 
-    def solve_planewaves_host(self, angles, allow_unconverged=False):
-        a, pa = _host(angles, np.float64)
-        j = np.empty((len(a), self.N), dtype=np.complex128)
+    def solve_planewaves_host(self, angles, allow_unconverged=False, out=None):
+        """Solve with host buffers: angles read from host memory, the (N, B)
+        current written to host memory.  angles and out may be CPU torch
+        tensors (pinned for full copy speed); out has shape (B, N), complex128."""
+        if isinstance(angles, torch.Tensor):
+            a = angles.to(torch.float64).contiguous()
+            pa, na = C.c_void_p(a.data_ptr()), a.numel()
+        else:
+            a, pa = _host(angles, np.float64)
+            na = len(a)
+        if out is None:
+            out = np.empty((na, self.N), dtype=np.complex128)
+        pj = C.c_void_p(out.data_ptr()) if isinstance(out, torch.Tensor) else out.ctypes.data_as(C.c_void_p)
         si = SolveInfo()
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
-        check(self.lib.wcs_solve_planewaves_host(self.h, len(a), pa, j.ctypes.data_as(C.c_void_p),
-                                                 self.N, C.byref(si)), allow)
+        check(self.lib.wcs_solve_planewaves_host(self.h, na, pa, pj, self.N, C.byref(si)), allow)
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
-        return j.T
+        return out.T
 
     def solve_rhs(self, e, hv, allow_unconverged=False):
         ec, hc = self._as_cols(e), self._as_cols(hv)
