@@ -43,7 +43,9 @@ class ElementGeometry:
 
     FIELDS = ("x", "y", "nx", "ny", "kappa")
 
-    def __init__(self, curve, N, n_cheb=32):
+    def __init__(self, curve, N, n_cheb=32, elements=None):
+        """elements: optional subset of element indices to prepare (the only
+        ones at() may then be asked for); by default all N."""
         self.curve, self.N = curve, N
         self.h = curve.L / N
         self.exact = isinstance(curve, Circle)
@@ -52,7 +54,10 @@ class ElementGeometry:
         j = np.arange(n_cheb)
         self.xc = 0.5 * (1.0 - np.cos(np.pi * (j + 0.5) / n_cheb))
         self.bw = (-1.0) ** j * np.sin((2 * j + 1) * np.pi / (2 * n_cheb))
-        s = (np.arange(N)[:, None] + self.xc[None, :]) * self.h
+        el = np.arange(N) if elements is None else np.unique(np.asarray(elements) % N)
+        self.row = np.full(N, -1, np.int64)
+        self.row[el] = np.arange(len(el))
+        s = (el[:, None] + self.xc[None, :]) * self.h
         pts = curve.points(s)
         self.vals = {f: pts[f] for f in self.FIELDS}
 
@@ -72,7 +77,10 @@ class ElementGeometry:
         if self.exact:
             return self.curve.points((e[:, None] + xi[None, :]) * self.h)
         W = self._bary(xi)
-        return {f: self.vals[f][e] @ W.T for f in self.FIELDS}
+        r = self.row[e]
+        if np.any(r < 0):
+            raise ValueError("element geometry not prepared for these elements")
+        return {f: self.vals[f][r] @ W.T for f in self.FIELDS}
 
 
 def _locals(geo, e, f, rule, k, kt, log_kind=None):
@@ -230,9 +238,10 @@ def entries(curve, N, k, kt, rows, cols, rules=None):
     where the dense oracle would be too slow.  Returns a dict of complex arrays.
     """
     rules = rules or Rules()
-    geo = ElementGeometry(curve, N)
     rows = np.asarray(rows, np.int64)
     cols = np.asarray(cols, np.int64)
+    # only the elements touching the requested node pairs (e = i - a, f = j - b)
+    geo = ElementGeometry(curve, N, elements=np.concatenate([rows, rows - 1, cols, cols - 1]))
     out = np.zeros((4, len(rows)), complex)
     xg, wg = qd.gauss_legendre01(rules.q_far)
     far_rule = qd.tensor_rule(rules.q_far)

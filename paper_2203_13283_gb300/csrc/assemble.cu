@@ -263,8 +263,13 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
   const float n = rintf(kR0.hi * 0.15915494309189535f);
   ff t = ff_add(kR0, ff_neg(ff_two_prod(n, F.twopi[0])));
   t = ff_add(t, ff_neg(ff_two_prod(n, F.twopi[1])));
-  const float ph0 = (t.hi + t.lo) - n * F.twopi[2];
+  // ph0 = k R0 - pi/4 reduced, kept in float-float (|ph0| <= 5 pi / 4);
+  // -pi/4 = -0.785398185 + 2.18556941e-8 (float head, float tail)
+  const ff ph0 = ff_add(ff_add(t, {-n * F.twopi[2], 0.f}), {-0.785398185f, 2.18556941e-08f});
   const float fdx0 = dx.hi, fdy0 = dy.hi, fR0 = R0.hi;
+  const ff twoR0 = {2.f * R0.hi, 2.f * R0.lo};
+  const ff kff = {F.k_hi, F.k_lo};
+  const float ldx0 = dx.lo, ldy0 = dy.lo;
   const float k = F.kf, beta = F.beta;
   const cf ck = {F.ck[0], F.ck[1]};      // sqrt(2 / (pi k~))
   const cf ik = {F.ik[0], F.ik[1]};      // i / k~
@@ -286,13 +291,29 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
       const float nxs = A.nxf[ir], nys = A.nyf[ir];
       const float a = 2.f * (fdx0 * dx + fdy0 * dy) + dx * dx + dy * dy;
       const float R = sqrtf(fR0 * fR0 + a);
-      const float dR = a / (fR0 + R);
       const float iR = 1.f / R;
-      const float gg = ((fdx0 + dx) * nxs + (fdy0 + dy) * nys) * iR;
       const float nd = nxt * nxs + nyt * nys;
+      // phase k R - pi/4 = ph0 + k (R - R0) in float-float: R - R0 = a / (2 R0 + (R - R0))
+      // with a = 2 d0.D + |D|^2 (D = o_p - o_r) from error-free products; the
+      // denominator takes the FP32 estimate of R - R0, whose error enters only
+      // relative to 2 R0
+      const ff Dx = ff_two_sum(oxp, -A.ox[ir]), Dy = ff_two_sum(oyp, -A.oy[ir]);
+      // (r - r').n' in float-float: on the flat parts of a contour it cancels to
+      // ~curvature R^2, far below the FP32 rounding of its terms (~6e-8 R)
+      const ff rx = ff_add(ff{fdx0, ldx0}, Dx), ry = ff_add(ff{fdy0, ldy0}, Dy);
+      const ff dn = ff_add(ff_mul(rx, ff{nxs, A.nxl[ir]}), ff_mul(ry, ff{nys, A.nyl[ir]}));
+      const float gg = (dn.hi + dn.lo) * iR;
+      const ff a_ff = ff_add(ff_add(ff_add(ff_two_prod(2.f * Dx.hi, fdx0), ff_two_prod(2.f * Dy.hi, fdy0)),
+                                    ff_add(ff_two_prod(Dx.hi, Dx.hi), ff_two_prod(Dy.hi, Dy.hi))),
+                             ff{2.f * (Dx.hi * ldx0 + Dy.hi * ldy0 + Dx.lo * (fdx0 + Dx.hi) + Dy.lo * (fdy0 + Dy.hi)),
+                                0.f});
+      const ff den = ff_add(twoR0, ff{a / (fR0 + R), 0.f});
+      const float q0 = a_ff.hi / den.hi;
+      const ff rem = ff_add(a_ff, ff_neg(ff_mul(ff{q0, 0.f}, den)));
+      const ff th = ff_add(ph0, ff_mul(kff, ff_quick(q0, rem.hi / den.hi)));
       float sn, cs;
-      sincosf(ph0 + k * dR - 0.78539816339744831f, &sn, &cs);   // e^{i(kR - pi/4)}
-      const cf E = {cs, sn};
+      sincosf(th.hi, &sn, &cs);
+      const cf E = {fmaf(-sn, th.lo, cs), fmaf(cs, th.lo, sn)};   // e^{i(kR - pi/4)}
       // real wavenumber: P + iQ = sum (i t)^k a_k, t = 1/(kR)
       const float t = iR / k, t2 = t * t;
       float P0 = c_a0[8], Q0 = c_a0[9], P1 = c_a1[8], Q1 = c_a1[9];
@@ -319,7 +340,8 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
         s0 = cmul(s0, w); s0.x += c_a0[m];
         s1 = cmul(s1, w); s1.x += c_a1[m];
       }
-      const cf Et = cscale(cmul(E, ck), sqrtf(iR) * __expf(-beta * R));
+      // expf, not the fast intrinsic: its error grows with |beta R| (up to ~12 here)
+      const cf Et = cscale(cmul(E, ck), sqrtf(iR) * expf(-beta * R));
       const cf Ht0 = cmul(Et, s0);
       const cf Ht1 = cmul(Et, {s1.y, -s1.x});
       const cf gt = {-0.25f * Ht0.y, 0.25f * Ht0.x};
@@ -663,7 +685,7 @@ int assemble_planes(const AsmArgs& A, cudaStream_t s) {
 }
 
 __global__ void k_far_offsets(Points far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                              float* oy, float* nxf, float* nyf) {
+                              float* oy, float* nxf, float* nyf, float* nxl, float* nyl) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * q) return;
   const int64_t e = t / q;
@@ -671,6 +693,8 @@ __global__ void k_far_offsets(Points far, const double* cx, const double* cy, in
   oy[t] = (float)(far.y[t] - cy[e]);
   nxf[t] = (float)far.nx[t];
   nyf[t] = (float)far.ny[t];
+  nxl[t] = (float)(far.nx[t] - (double)nxf[t]);   // float-float tails of the normals
+  nyl[t] = (float)(far.ny[t] - (double)nyf[t]);
 }
 
 __global__ void k_centres_ff(const double* cx, const double* cy, int64_t N, float4* cff) {
@@ -681,8 +705,8 @@ __global__ void k_centres_ff(const double* cx, const double* cy, int64_t N, floa
 }
 
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                float* oy, float* nxf, float* nyf, float4* cff, cudaStream_t s) {
-  k_far_offsets<<<(unsigned)((N * q + 255) / 256), 256, 0, s>>>(far, cx, cy, N, q, ox, oy, nxf, nyf);
+                float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float4* cff, cudaStream_t s) {
+  k_far_offsets<<<(unsigned)((N * q + 255) / 256), 256, 0, s>>>(far, cx, cy, N, q, ox, oy, nxf, nyf, nxl, nyl);
   note_launch();
   k_centres_ff<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(cx, cy, N, cff);
   note_launch();

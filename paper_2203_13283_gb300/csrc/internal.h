@@ -90,6 +90,7 @@ struct AsmArgs {
   const double *cx = nullptr, *cy = nullptr;     // element centres (xi = 1/2)
   const float *ox = nullptr, *oy = nullptr;      // far points minus their element centre
   const float *nxf = nullptr, *nyf = nullptr;    // far-point normals (FP32)
+  const float *nxl = nullptr, *nyl = nullptr;    // their float-float tails
   const float4* cff = nullptr;                   // element centres as float-float (x hi, x lo, y hi, y lo)
   double zfast = 1e300;
   FastConsts fk;
@@ -100,7 +101,7 @@ int assemble_dense(const AsmArgs& a, cudaStream_t s);
 int assemble_planes(const AsmArgs& a, cudaStream_t s);
 // FP32 offset tables of the far points relative to element centres.
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                float* oy, float* nxf, float* nyf, float4* cff, cudaStream_t s);
+                float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float4* cff, cudaStream_t s);
 // First row of the four circulant operators on the circle (row 0, N entries each).
 int assemble_circle_row(const AsmArgs& a, cudaStream_t s);
 // Sampled entries (row, col) of the four operators, computed point-wise.

@@ -613,7 +613,7 @@ int wcs_default_options(wcs_options* o) {
   o->rhs_chunk = 256;
   o->mixed_planes = 3;
   o->rhs_planes = 3;
-  o->zfast = 9.0;
+  o->zfast = 0.0;   // far pairs in FP64 (set > 0 to enable the FP32 far-pair path)
   return WCS_OK;
 }
 
@@ -819,7 +819,7 @@ static void set_fast_consts(AsmArgs& A) {
   F.ampk = (float)std::sqrt(2.0 / (WCS_PI * A.k));
   F.kk2h2 = (float)(A.k * A.k * A.h * A.h);
   F.h2 = (float)(A.h * A.h);
-  F.zfast2 = (float)(A.zfast * A.zfast);
+  F.zfast2 = (A.zfast < 1e18) ? (float)(A.zfast * A.zfast) : INFINITY;
   F.k_hi = (float)A.k;
   F.k_lo = (float)(A.k - (double)F.k_hi);
   const double tp = 2.0 * WCS_PI;   // 2 pi to ~72 bits: double plus its float-float residual
@@ -882,10 +882,12 @@ int wcs_assemble(wcs_ctx* c) {
     Points cp;
     cp.x = c->centres.d(); cp.y = cp.x + N; cp.nx = cp.y + N; cp.ny = cp.nx + N; cp.kappa = nullptr; cp.n = N;
     TRY(points_build(c->contour, c->arc, N, c->h, half, 1, cp, c->s));
-    TRY(c->offs.ensure(sizeof(float) * 4 * N * (qf + 1)));
+    const int64_t cff_off = ((6 * N * qf + 3) / 4) * 4;   // floats; float4 table 16-byte aligned
+    TRY(c->offs.ensure(sizeof(float) * cff_off + sizeof(float4) * N));
     float* of = (float*)c->offs.p;
-    float4* cff = (float4*)(of + 4 * N * qf);
-    TRY(far_offsets(c->far, cp.x, cp.y, N, qf, of, of + N * qf, of + 2 * N * qf, of + 3 * N * qf, cff, c->s));
+    float4* cff = (float4*)(of + cff_off);
+    TRY(far_offsets(c->far, cp.x, cp.y, N, qf, of, of + N * qf, of + 2 * N * qf, of + 3 * N * qf, of + 4 * N * qf,
+                    of + 5 * N * qf, cff, c->s));
     AsmArgs A = asm_args(c, false);
     A.mixed = 1;
     A.planes = c->planes;
@@ -895,8 +897,10 @@ int wcs_assemble(wcs_ctx* c) {
         for (int p = 0; p < 3; ++p) A.P[op][l][p] = (p < c->planes) ? plane_ptr(c, op, l, p) : nullptr;
     A.cx = cp.x; A.cy = cp.y;
     A.ox = of; A.oy = of + N * qf; A.nxf = of + 2 * N * qf; A.nyf = of + 3 * N * qf;
+    A.nxl = of + 4 * N * qf; A.nyl = of + 5 * N * qf;
     A.cff = cff;
-    A.zfast = c->opt.zfast + 2.0 * c->k * c->h;
+    // zfast <= 0: every pair in FP64 (the FP32 path is off)
+    A.zfast = (c->opt.zfast > 0.0) ? c->opt.zfast + 2.0 * c->k * c->h : 1e300;
     set_fast_consts(A);
     ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * qf * qf, 0.0);   // units: far point pairs
     TRY(assemble_planes(A, c->s));

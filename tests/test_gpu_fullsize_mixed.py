@@ -1,0 +1,73 @@
+"""The mixed form at the benchmark's size and launch configuration:
+superellipse |x|^4 + |y/0.6|^4 = 1, N = 32768, 10 elements per wavelength,
+rank cap N/8, blocks of 64, right-hand sides in one chunk of 1024.
+
+No dense oracle runs at this size, so the tensor-core operator planes are
+checked on sampled rows against entries the oracle computes one by one, and
+the solution through an exact symmetry: the contour is symmetric under
+y -> -y, which maps node i to node N - i and incidence phi to -phi."""
+
+import numpy as np
+import pytest
+import torch
+
+import workloads
+from gpu_common import make_solver, to_np
+from oracle import assembly
+from oracle_cache import curve_of
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def big():
+    w = workloads.WORKLOADS["superellipse_n32768"]
+    s = make_solver(w, precision=1, refine_tol=1e-7, max_refine=12, rhs_chunk=1024, block=64)
+    s.assemble()
+    yield w, s
+    s.close()
+
+
+def test_operator_planes_vs_oracle_entries(big):
+    w, s = big
+    N = w["N"]
+    info = s.info()
+    cur = curve_of(w)
+    rng = np.random.default_rng(11)
+    cols = [0, 9001, N - 1]
+    for c in cols:
+        I = torch.zeros((N, 1), dtype=torch.complex128, device="cuda")
+        I[c, 0] = 1.0
+        # near band, mid range and far rows of this column
+        rows = np.unique(np.concatenate([(c + np.arange(-6, 7)) % N, rng.integers(0, N, 10)]))
+        O = assembly.entries(cur, N, info["k"], complex(info["kt_re"], info["kt_im"]), rows,
+                             np.full(rows.shape, c))
+        for key, op in (("S", "S"), ("D", "D"), ("Dt", "DT"), ("N", "N")):
+            col = to_np(s.apply(op, I))[:, 0]
+            scale = np.max(np.abs(col))
+            err = np.abs(col[rows] - O[key])
+            # per entry ~1e-6 (FP32 far pairs), with an absolute floor of 1e-7 of
+            # the column scale: near-band D entries cancel to ~1e-6 of the column
+            # maximum, and the 8-point near rule of the mixed form resolves them
+            # to ~1e-8 of it (the oracle uses 16 points)
+            assert np.all(err <= 5e-6 * np.abs(O[key]) + 1e-7 * scale), (key, c, np.max(err / scale))
+
+
+def test_solution_mirror_symmetry(big):
+    w, s = big
+    N = w["N"]
+    r = s.skeleton(1e-6, max_rank=N // 8, seed=1, allow_cap=True)
+    assert r == N // 8
+    s.factor()
+    ang = np.array([0.0, 0.3, -0.3, 1.1, -1.1])
+    j = to_np(s.solve_planewaves(ang, allow_unconverged=True))
+    assert s.last_solve["rel_residual"] < 1e-6
+    refl = (-np.arange(N)) % N
+    for a, b in [(0, 0), (1, 2), (3, 4)]:
+        ja, jb = j[:, a], j[:, b][refl]
+        # the asymmetry is the difference of two solution errors: the 2-norm
+        # relative error of each (the accuracy target, 1e-6) bounds it by 2e-6
+        asym = np.linalg.norm(ja - jb) / np.linalg.norm(ja)
+        print(f"incidence pair {a},{b}: 2-norm asymmetry {asym:.2e}, "
+              f"max-norm {np.max(np.abs(ja - jb)) / np.max(np.abs(ja)):.2e}")
+        assert asym <= 2e-6, (a, b, asym)

@@ -1,7 +1,8 @@
-"""GPU parity of the mixed-precision form (tensor-core products, FP32 far-field
-kernels): against the CPU oracle on small workloads and against the FP64 form
-(itself pinned to the oracle) at N = 4096.  The bar is the mixed form's
-target, 1e-6 relative per column in the surface current."""
+"""GPU parity of the mixed-precision form (tensor-core products; far pairs in
+FP64 by default, or in FP32 with zfast > 0): against the CPU oracle on small
+workloads and against the FP64 form (itself pinned to the oracle) at N = 4096.
+The bar is the mixed form's target, 1e-6 relative per column in the surface
+current."""
 
 import numpy as np
 import pytest
@@ -14,11 +15,12 @@ from oracle_cache import solved
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("zfast", [0.0, 9.0])
 @pytest.mark.parametrize("name", ["ellipse_n200", "superellipse_n320", "star_n200"])
-def test_mixed_solve_vs_oracle(name):
+def test_mixed_solve_vs_oracle(name, zfast):
     r = solved(name)
     w = r["w"]
-    s = make_solver(w, precision=1, refine_tol=1e-8, max_refine=12)
+    s = make_solver(w, precision=1, refine_tol=1e-8, max_refine=12, zfast=zfast)
     s.assemble()
     s.skeleton(1e-6, max_rank=w["N"] // 4, seed=5, allow_cap=True)
     s.factor()
