@@ -17,6 +17,9 @@
 // weights (split K = A log|s - s'| + B, A = -(1/2pi) J0 or -(kappa/2pi) J1 g).
 #include <cuda_bf16.h>
 
+#include <complex>
+#include <cstring>
+
 #include "hankel.cuh"
 #include "internal.h"
 
@@ -511,7 +514,31 @@ __global__ void k_entries(AsmArgs A, int64_t count, const int64_t* rows, const i
   for (int op = 0; op < 4; ++op) out4[op * count + t] = sum[op];
 }
 
+// Coefficient tables of hankel01_asymptotic_fixed for this run's k~ = k (1 + i t)
+static int upload_asymptotic(const AsmArgs& A) {
+  AsymCoef h;
+  std::memset(&h, 0, sizeof(h));
+  const std::complex<double> c1 = std::complex<double>(1.0, 0.0) / std::complex<double>(1.0, A.ktp.t);
+  for (int nu = 0; nu < 2; ++nu) {
+    double a = 1.0;
+    std::complex<double> cp = 1.0;   // c1^k
+    for (int k = 0; k < 2 * ASYM_M; ++k) {
+      if (k > 0) {
+        a *= (4.0 * nu * nu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (8.0 * k);
+        cp *= c1;
+      }
+      const int m = k / 2;
+      const double sg = (m & 1) ? -1.0 : 1.0;
+      const std::complex<double> b = sg * a * cp;
+      if ((k & 1) == 0) { h.re[nu][m] = sg * a; h.ce[nu][m] = mkz(b.real(), b.imag()); }
+      else { h.ro[nu][m] = sg * a; h.co[nu][m] = mkz(b.real(), b.imag()); }
+    }
+  }
+  return cudaMemcpyToSymbol(c_asym, &h, sizeof(h)) == cudaSuccess ? 0 : 3;
+}
+
 static int upload_rules(const AsmArgs& A) {
+  if (upload_asymptotic(A)) return 3;
   double xf[16], wf[16], xn[16], wn[16];
   gauss_legendre01(A.q_far, xf, wf);
   gauss_legendre01(A.q_near, xn, wn);
