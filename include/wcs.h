@@ -221,6 +221,19 @@ int wcs_solve_planewaves_host(wcs_ctx* ctx, int64_t B, const double* angles_host
 int wcs_solve_rhs(wcs_ctx* ctx, int64_t B, const double* e_dev, const double* h_dev, int64_t ld,
                   double* j_dev, int64_t ldj, wcs_solve_info* info);
 
+/* Adjoint solve C^H x = b (Eq. 5's operator C conjugate-transposed), B
+ * columns of complex FP64, device, column-major N x B (ldb, ldx >= N).  The
+ * approximate inverse is the adjoint of Eq. (9): with C~ = C_c + U V^T,
+ * C~^-H b = y - C_c^-H V_w K^-H (U^H y), y = C_c^-H b, K = I + V^T C_c^-1 U;
+ * C_c^-H is Eq. (8) with conjugated eigenvalues.  Refinement uses C^H, so the
+ * result meets refine_tol against the exact adjoint.  Needs the capacitance
+ * inverse that wcs_factor forms (a context restored by wcs_load has none:
+ * WCS_ERR_STATE until wcs_factor runs again).  x must not alias b.  Errors:
+ * WCS_ERR_STATE, WCS_ERR_ARG (null pointer with B > 0, ld < N),
+ * WCS_ERR_NOT_CONVERGED (x still written). */
+int wcs_solve_adjoint(wcs_ctx* ctx, int64_t B, const double* b_dev, int64_t ldb, double* x_dev,
+                      int64_t ldx, wcs_solve_info* info);
+
 /* Plane-wave Galerkin projections e/eta and h of Eq. (4) (device, N x B, ld). */
 int wcs_planewave_rhs(wcs_ctx* ctx, int64_t B, const double* angles_host, double* e_dev,
                       double* h_dev, int64_t ld);

@@ -91,6 +91,8 @@ struct wcs_ctx {
   DevBuf qh, qt;             // skeleton basis as resident bf16 planes: rows conj(q_i); rows of Q
   DevBuf gA, gB;                          // staging for general complex tensor products
   DevBuf sol_e, sol_h, sol_b, sol_ang, sol_j;   // solve blocks (grow-only, kept across calls)
+  DevBuf Kinv;                            // r x r capacitance inverse (adjoint solves)
+  DevBuf Wa;                              // N x r: C_c^-H V_w, formed at the first adjoint solve
   // optional per-kernel timing: CUDA events on the context stream
   bool profile = false;
   struct Rec { int cat; cudaEvent_t a, b; double flops, bytes; };
@@ -403,7 +405,9 @@ static int apply_Cc(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, in
   }
   ProfScope ps(c, CAT_FFT, 0.0, 4.0 * 16.0 * (double)N * cols);
   TRY(fft_columns(c->fft, Y, ldy, cols, -1, c->s));
-  TRY(scale_columns(Y, N, ldy, cols, mu_ptr(c, MU_C), mode == 2, mode == 1, 1.0 / (double)N, c->s));
+  // mode 0: C_c, 1: C_c^H, 2: C_c^-1, 3: C_c^-H (eigenvalues mu_C, conj(mu_C))
+  TRY(scale_columns(Y, N, ldy, cols, mu_ptr(c, MU_C), mode == 2 || mode == 3, mode == 1 || mode == 3,
+                    1.0 / (double)N, c->s));
   TRY(fft_columns(c->fft, Y, ldy, cols, +1, c->s));
   return 0;
 }
@@ -429,6 +433,28 @@ static int woodbury(wcs_ctx* c, const zd* B, int64_t ldb, zd* X, int64_t ldx, in
   // Z = V^T Y = Vw^H Y ; X = Y - Wt Z
   TRY(cgemm(c, r, cols, N, mkz(1.0), blkH(c->Vw.z(), N), X, ldx, mkz(0.0), Z, r));
   TRY(cgemm(c, N, cols, r, mkz(-1.0), blk(c->Wt.z(), N), Z, r, mkz(1.0), X, ldx));
+  return 0;
+}
+
+// X = C^{-H} B through the adjoint of Eq. (9).  With C~ = C_c + Q V_w^H:
+//   C~^-H B = Y - (C_c^-H V_w) K^-H (Q^H Y),  Y = C_c^-H B,  K = I + V_w^H C_c^-1 Q,
+// the capacitance matrix of the forward solve.  C_c^-H V_w is formed once.
+static int woodbury_adj(wcs_ctx* c, const zd* B, int64_t ldb, zd* X, int64_t ldx, int64_t cols) {
+  const int64_t N = c->N;
+  TRY(apply_Cc(c, B, ldb, X, ldx, cols, 3));
+  if (c->rank <= 0) return 0;
+  const int64_t r = c->rank;
+  if (!c->Kinv.p) { set_error("adjoint solve: capacitance inverse missing (factor again)"); return WCS_ERR_STATE; }
+  if (!c->Wa.p) {
+    TRY(c->Wa.ensure(sizeof(zd) * N * r));
+    TRY(apply_Cc(c, c->Vw.z(), N, c->Wa.z(), N, r, 3));
+  }
+  TRY(c->small.ensure(sizeof(zd) * 2 * r * cols));
+  zd* T = c->small.z();
+  zd* Z = T + r * cols;
+  TRY(cgemm(c, r, cols, N, mkz(1.0), blkH(c->U.z(), N), X, ldx, mkz(0.0), T, r));    // Q^H Y
+  TRY(cgemm(c, r, cols, r, mkz(1.0), blkH(c->Kinv.z(), r), T, r, mkz(0.0), Z, r));   // K^-H (Q^H Y)
+  TRY(cgemm(c, N, cols, r, mkz(-1.0), blk(c->Wa.z(), N), Z, r, mkz(1.0), X, ldx));   // Y - C_c^-H V_w Z
   return 0;
 }
 
@@ -462,7 +488,7 @@ static int sync(wcs_ctx* c) {
   return 0;
 }
 
-// ----------------------------------------------------------------------------- kernels local to the driver
+// ----------------------------------------------------------------------------- kernels local to this file
 __global__ void k_mu_finish(zd* mu, int64_t N, double h) {
   const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= N) return;
@@ -657,7 +683,7 @@ static void free_mesh(wcs_ctx* c) {
   c->opplanes.release(); c->centres.release(); c->offs.release();
   c->stage0.release(); c->stage1.release(); c->stage2.release(); c->stage_cols = 0;
   c->gA.release(); c->gB.release(); c->gW.release(); c->qh.release(); c->qt.release();
-  c->U.release(); c->Vw.release(); c->Wt.release();
+  c->U.release(); c->Vw.release(); c->Wt.release(); c->Kinv.release(); c->Wa.release();
   c->sol_e.release(); c->sol_h.release(); c->sol_b.release(); c->sol_ang.release(); c->sol_j.release();
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
   c->rank = -1;
@@ -919,7 +945,7 @@ int wcs_assemble(wcs_ctx* c) {
   note_launch();
   cudaMemcpyAsync(&c->norm_cc, c->small.p, sizeof(double), cudaMemcpyDeviceToHost, c->s);
   TRY(sync(c));
-  c->U.release(); c->Vw.release(); c->Wt.release();
+  c->U.release(); c->Vw.release(); c->Wt.release(); c->Kinv.release(); c->Wa.release();
   c->rank = -1;
   c->stage = ST_ASSEMBLED;
   return WCS_OK;
@@ -1158,7 +1184,7 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   }
   TRY(sync(c));
   if (rank_out) *rank_out = (int)ell;
-  c->Wt.release();
+  c->Wt.release(); c->Kinv.release(); c->Wa.release();
   c->stage = ST_SKELETON;
   return status;
 }
@@ -1171,7 +1197,9 @@ int wcs_factor(wcs_ctx* c) {
   if (r > 0) {
     TRY(c->Wt.ensure(sizeof(zd) * N * r));
     // W = C_c^{-1} U  (held in Wt until the inverse is applied)
-    DevBuf Wb, Kb, Kinv, info;
+    DevBuf Wb, Kb, info;
+    DevBuf& Kinv = c->Kinv;   // kept for adjoint solves
+    c->Wa.release();
     TRY(Wb.ensure(sizeof(zd) * N * r));
     TRY(apply_Cc(c, c->U.z(), N, Wb.z(), N, r, 2));
     // K = I + V^T W = I + Vw^H W
@@ -1430,9 +1458,13 @@ static int residual_rhs_mixed(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld,
 // every residual is formed from e and hv directly (residual_rhs_mixed).
 static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx, int64_t cc,
                        int* steps, double* relres, const zd* e = nullptr, const zd* hv = nullptr,
-                       int64_t ld_eh = 0) {
+                       int64_t ld_eh = 0, bool adj = false) {
   const int64_t N = c->N;
-  TRY(woodbury(c, b, ldb, x, ldx, cc));
+  // adj: solve C^H x = b (the adjoint Woodbury and C^H in every residual)
+  auto approx_inverse = [&](const zd* B, int64_t ldb_, zd* X, int64_t ldx_) -> int {
+    return adj ? woodbury_adj(c, B, ldb_, X, ldx_, cc) : woodbury(c, B, ldb_, X, ldx_, cc);
+  };
+  TRY(approx_inverse(b, ldb, x, ldx));
   DevBuf nb;
   TRY(nb.ensure(sizeof(double) * 2 * cc));
   std::vector<double> bn(cc), rn(cc);
@@ -1452,10 +1484,10 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
   };
   // R = b - C x with the given precision
   auto residual = [&](int mode, double& worst) -> int {
-    if (c->mixed && e && hv) {
+    if (c->mixed && e && hv && !adj) {
       TRY(residual_rhs_mixed(c, e, hv, ld_eh, x, ldx, R, cc, mode));
     } else {
-      TRY(apply_C(c, x, ldx, R, N, cc, false, mode));
+      TRY(apply_C(c, x, ldx, R, N, cc, adj, mode));
       TRY(axpby(N, cc, mkz(1.0), b, ldb, mkz(-1.0), R, N, c->s));
     }
     return worst_of(worst);
@@ -1466,7 +1498,7 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
     // FP64 form: plain refinement on the exact residual
     TRY(residual(PREC_ACCURATE, worst));
     while (worst > c->opt.refine_tol && it < c->opt.max_refine) {
-      TRY(woodbury(c, R, N, dx, N, cc));
+      TRY(approx_inverse(R, N, dx, N));
       TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
       ++it;
       TRY(residual(PREC_ACCURATE, worst));
@@ -1483,7 +1515,7 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
     if (!c->first_accurate) {
       TRY(residual(PREC_FAST, worst));
       while (worst >= 3e-3 && it < c->opt.max_refine / 2) {
-        TRY(woodbury(c, R, N, dx, N, cc));
+        TRY(approx_inverse(R, N, dx, N));
         TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
         ++it;
         TRY(residual(PREC_FAST, worst));
@@ -1498,10 +1530,10 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
       double upd = worst, prev_upd = 1e300;
       // updates until the carried residual is well below the target
       while (upd > 0.1 * c->opt.refine_tol && it < c->opt.max_refine && upd < 0.7 * prev_upd) {
-        TRY(woodbury(c, R, N, dx, N, cc));
+        TRY(approx_inverse(R, N, dx, N));
         TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
         ++it;
-        TRY(apply_C(c, dx, N, T, N, cc, false, PREC_PERIODIC));
+        TRY(apply_C(c, dx, N, T, N, cc, adj, PREC_PERIODIC));
         TRY(axpby(N, cc, mkz(-1.0), T, N, mkz(1.0), R, N, c->s));
         prev_upd = upd;
         TRY(worst_of(upd));
@@ -1542,6 +1574,29 @@ int wcs_solve_rhs(wcs_ctx* c, int64_t B, const double* e, const double* hv, int6
     else if (r) return r;
   }
   bb.release();
+  if (info) { info->refine_steps = steps; info->rel_residual = rr; }
+  if (status) set_error("iterative refinement did not reach refine_tol");
+  return status;
+}
+
+int wcs_solve_adjoint(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx,
+                      wcs_solve_info* info) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
+  TRY(check_block(c, B, b, ldb));
+  TRY(check_block(c, B, x, ldx));
+  if (B == 0) return WCS_OK;
+  const int64_t chunk = c->opt.rhs_chunk;
+  TRY(ensure_work(c, std::min(B, chunk)));
+  int steps = 0, status = WCS_OK;
+  double rr = 0;
+  for (int64_t c0 = 0; c0 < B; c0 += chunk) {
+    const int64_t cc = std::min(chunk, B - c0);
+    int r = solve_block(c, (const zd*)b + c0 * ldb, ldb, (zd*)x + c0 * ldx, ldx, cc, &steps, &rr, nullptr,
+                        nullptr, 0, true);
+    if (r == WCS_ERR_NOT_CONVERGED) status = r;
+    else if (r) return r;
+  }
   if (info) { info->refine_steps = steps; info->rel_residual = rr; }
   if (status) set_error("iterative refinement did not reach refine_tol");
   return status;

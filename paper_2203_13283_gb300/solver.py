@@ -196,6 +196,17 @@ class Solver:
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
         return j.t()
 
+    def solve_adjoint(self, b, allow_unconverged=False):
+        """x with C^H x = b (N x B or N, complex128) through the adjoint factors."""
+        bc = self._as_cols(b)
+        x = self._block(bc.shape[0])
+        si = SolveInfo()
+        allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+        check(self.lib.wcs_solve_adjoint(self.h, bc.shape[0], _ptr(bc), self.N, _ptr(x), self.N, C.byref(si)),
+              allow)
+        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        return x.t()
+
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
                     "sample", "project", "orth", "vw", "inverse")
 
