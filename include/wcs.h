@@ -188,8 +188,11 @@ int wcs_factor(wcs_ctx* ctx);
 /* Checkpoint of a factored context.  The paper defines no file format; this
  * stores what the solve of Eq. (9) needs beyond the operators: the single
  * skeleton U V^T of Eq. (7) (U = Q and V_w = conj(V), N x rank each) and
- * W~ = C_c^-1 U (I + V^T C_c^-1 U)^-1, plus the contour, N, k and the
- * options, in a host file at `path` (complex FP64, about 48 N rank bytes).
+ * W~ = C_c^-1 U (I + V^T C_c^-1 U)^-1 and the capacitance inverse
+ * (I + V^T C_c^-1 U)^-1 (rank x rank, for wcs_solve_adjoint), plus the
+ * contour, N, k and the options, in a host file at `path` (complex FP64,
+ * about 48 N rank bytes).  Files without the capacitance inverse (format
+ * version 1) still load; their contexts solve forward only.
  * The operators are not stored.  wcs_load re-runs the mesh and the assembly,
  * which are deterministic, on a context created with the same precision and
  * quadrature options (else WCS_ERR_ARG), then restores the factors; the
@@ -221,14 +224,25 @@ int wcs_solve_planewaves_host(wcs_ctx* ctx, int64_t B, const double* angles_host
 int wcs_solve_rhs(wcs_ctx* ctx, int64_t B, const double* e_dev, const double* h_dev, int64_t ld,
                   double* j_dev, int64_t ldj, wcs_solve_info* info);
 
+/* Solve C x = b for B general right-hand sides b of Eq. (5)'s preconditioned
+ * system (device, complex FP64, column-major N x B, ldb, ldx >= N): Eq. (9)
+ * then refinement x <- x + C~^-1 (b - C x) with the exact product C, to
+ * refine_tol.  wcs_solve_rhs is the same solve with b formed from e/eta and
+ * h.  x must not alias b.  Errors: WCS_ERR_STATE (before wcs_factor),
+ * WCS_ERR_ARG (null pointer with B > 0, ld < N), WCS_ERR_NOT_CONVERGED (x
+ * still written). */
+int wcs_solve(wcs_ctx* ctx, int64_t B, const double* b_dev, int64_t ldb, double* x_dev, int64_t ldx,
+              wcs_solve_info* info);
+
 /* Adjoint solve C^H x = b (Eq. 5's operator C conjugate-transposed), B
  * columns of complex FP64, device, column-major N x B (ldb, ldx >= N).  The
  * approximate inverse is the adjoint of Eq. (9): with C~ = C_c + U V^T,
  * C~^-H b = y - C_c^-H V_w K^-H (U^H y), y = C_c^-H b, K = I + V^T C_c^-1 U;
  * C_c^-H is Eq. (8) with conjugated eigenvalues.  Refinement uses C^H, so the
  * result meets refine_tol against the exact adjoint.  Needs the capacitance
- * inverse that wcs_factor forms (a context restored by wcs_load has none:
- * WCS_ERR_STATE until wcs_factor runs again).  x must not alias b.  Errors:
+ * inverse that wcs_factor forms and wcs_save stores (a context restored
+ * from a version-1 file has none: WCS_ERR_STATE until wcs_factor runs
+ * again).  x must not alias b.  Errors:
  * WCS_ERR_STATE, WCS_ERR_ARG (null pointer with B > 0, ld < N),
  * WCS_ERR_NOT_CONVERGED (x still written). */
 int wcs_solve_adjoint(wcs_ctx* ctx, int64_t B, const double* b_dev, int64_t ldb, double* x_dev,

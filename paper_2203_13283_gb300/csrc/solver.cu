@@ -1316,6 +1316,24 @@ static int ckpt_arrays(wcs_ctx* c, FILE* f, bool write) {
   return 0;
 }
 
+// The r x r capacitance inverse (version 2 files; adjoint solves need it).
+static int ckpt_kinv(wcs_ctx* c, FILE* f, bool write) {
+  const int64_t r = c->rank;
+  if (r <= 0) return 0;
+  const size_t n = (size_t)r * r;
+  std::vector<zd> host(n);
+  if (write) {
+    cudaMemcpyAsync(host.data(), c->Kinv.p, sizeof(zd) * n, cudaMemcpyDeviceToHost, c->s);
+    TRY(sync(c));
+    if (fwrite(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: write failed"); return WCS_ERR_ARG; }
+    return 0;
+  }
+  if (fread(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
+  TRY(c->Kinv.ensure(sizeof(zd) * n));
+  cudaMemcpyAsync(c->Kinv.p, host.data(), sizeof(zd) * n, cudaMemcpyHostToDevice, c->s);
+  return sync(c);
+}
+
 int wcs_save(wcs_ctx* c, const char* path) {
   if (!c || !path) { set_error("bad argument"); return WCS_ERR_ARG; }
   if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
@@ -1324,7 +1342,7 @@ int wcs_save(wcs_ctx* c, const char* path) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
   std::memcpy(hd.magic, kCkptMagic, 8);
-  hd.version = 1;
+  hd.version = (c->rank > 0 && c->Kinv.p) ? 2 : 1;
   hd.rank = c->rank;
   hd.N = c->N;
   hd.k = c->k;
@@ -1333,6 +1351,7 @@ int wcs_save(wcs_ctx* c, const char* path) {
   int r = (fwrite(&hd, sizeof(hd), 1, f) == 1) ? 0 : WCS_ERR_ARG;
   if (r) set_error("checkpoint: write failed");
   if (!r) r = ckpt_arrays(c, f, true);
+  if (!r && hd.version == 2) r = ckpt_kinv(c, f, true);
   if (fclose(f) != 0 && !r) { set_error("checkpoint: write failed"); r = WCS_ERR_ARG; }
   return r;
 }
@@ -1343,7 +1362,8 @@ int wcs_load(wcs_ctx* c, const char* path) {
   if (!f) { set_error(std::string("checkpoint: cannot open ") + path); return WCS_ERR_ARG; }
   CkptHeader hd;
   int r = 0;
-  if (fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1) {
+  if (fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kCkptMagic, 8) != 0 ||
+      (hd.version != 1 && hd.version != 2)) {
     set_error("checkpoint: not a checkpoint of this library");
     r = WCS_ERR_ARG;
   }
@@ -1368,6 +1388,7 @@ int wcs_load(wcs_ctx* c, const char* path) {
   if (!r) {
     c->rank = hd.rank;
     r = ckpt_arrays(c, f, false);
+    if (!r && hd.version == 2) r = ckpt_kinv(c, f, false);
   }
   fclose(f);
   if (r) return r;
@@ -1579,8 +1600,9 @@ int wcs_solve_rhs(wcs_ctx* c, int64_t B, const double* e, const double* hv, int6
   return status;
 }
 
-int wcs_solve_adjoint(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx,
-                      wcs_solve_info* info) {
+// C x = b (adj: C^H x = b) for B general right-hand sides, chunked.
+static int solve_general(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx,
+                         wcs_solve_info* info, bool adj) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
   if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
   TRY(check_block(c, B, b, ldb));
@@ -1593,13 +1615,23 @@ int wcs_solve_adjoint(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, doubl
   for (int64_t c0 = 0; c0 < B; c0 += chunk) {
     const int64_t cc = std::min(chunk, B - c0);
     int r = solve_block(c, (const zd*)b + c0 * ldb, ldb, (zd*)x + c0 * ldx, ldx, cc, &steps, &rr, nullptr,
-                        nullptr, 0, true);
+                        nullptr, 0, adj);
     if (r == WCS_ERR_NOT_CONVERGED) status = r;
     else if (r) return r;
   }
   if (info) { info->refine_steps = steps; info->rel_residual = rr; }
   if (status) set_error("iterative refinement did not reach refine_tol");
   return status;
+}
+
+int wcs_solve(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx,
+              wcs_solve_info* info) {
+  return solve_general(c, B, b, ldb, x, ldx, info, false);
+}
+
+int wcs_solve_adjoint(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx,
+                      wcs_solve_info* info) {
+  return solve_general(c, B, b, ldb, x, ldx, info, true);
 }
 
 int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j, int64_t ldj,

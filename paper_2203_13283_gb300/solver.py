@@ -196,16 +196,22 @@ class Solver:
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
         return j.t()
 
-    def solve_adjoint(self, b, allow_unconverged=False):
-        """x with C^H x = b (N x B or N, complex128) through the adjoint factors."""
+    def _solve_general(self, fn, b, allow_unconverged):
         bc = self._as_cols(b)
         x = self._block(bc.shape[0])
         si = SolveInfo()
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
-        check(self.lib.wcs_solve_adjoint(self.h, bc.shape[0], _ptr(bc), self.N, _ptr(x), self.N, C.byref(si)),
-              allow)
+        check(fn(self.h, bc.shape[0], _ptr(bc), self.N, _ptr(x), self.N, C.byref(si)), allow)
         self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
         return x.t()
+
+    def solve(self, b, allow_unconverged=False):
+        """x with C x = b (N x B or N, complex128): Eq. (9) plus refinement."""
+        return self._solve_general(self.lib.wcs_solve, b, allow_unconverged)
+
+    def solve_adjoint(self, b, allow_unconverged=False):
+        """x with C^H x = b (N x B or N, complex128) through the adjoint factors."""
+        return self._solve_general(self.lib.wcs_solve_adjoint, b, allow_unconverged)
 
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
                     "sample", "project", "orth", "vw", "inverse")

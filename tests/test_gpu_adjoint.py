@@ -58,3 +58,35 @@ def test_adjoint_duality_and_chunks():
     y = to_np(s.apply("CH", torch.from_numpy(x)))
     assert colrel(y, cvec) < 1e-10
     s.close()
+
+
+def test_general_solve_and_autograd():
+    # wcs_solve on a general b against the oracle's dense solve; the autograd
+    # wrapper's backward is the adjoint solve: for L = Re(c^H x), x = C^-1 b,
+    # dL/db (PyTorch convention) = C^-H c
+    from paper_2203_13283_gb300 import autograd
+    r = solved("superellipse_n320")
+    w = r["w"]
+    N = w["N"]
+    s = make_solver(w, refine_tol=1e-12, max_refine=16)
+    s.assemble()
+    s.skeleton(1e-8, max_rank=N // 4, seed=3, allow_cap=True)
+    s.factor()
+    b = _rhs(N, 3, 21)
+    cvec = _rhs(N, 3, 22)
+    x = to_np(s.solve(torch.from_numpy(b)))
+    assert colrel(x, np.linalg.solve(r["C"], b)) < 1e-10
+    bt = torch.from_numpy(b).cuda().requires_grad_(True)
+    ct = torch.from_numpy(cvec).cuda()
+    xt = autograd.solve(s, bt)
+    loss = torch.real(torch.sum(ct.conj() * xt))
+    loss.backward()
+    g_ref = np.linalg.solve(r["C"].conj().T, cvec)
+    assert colrel(to_np(bt.grad), g_ref) < 1e-10
+    # single column (1-D) input
+    b1 = torch.from_numpy(b[:, 0].copy()).cuda().requires_grad_(True)
+    x1 = autograd.solve(s, b1)
+    assert x1.shape == (N,)
+    torch.real(torch.sum(ct[:, 0].conj() * x1)).backward()
+    assert colrel(to_np(b1.grad), g_ref[:, 0]) < 1e-10
+    s.close()

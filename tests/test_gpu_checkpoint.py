@@ -25,6 +25,9 @@ def test_save_load_gives_identical_solves(tmp_path, precision, name):
     a.factor()
     ang = w["angles"][:4]
     ja = a.solve_planewaves(ang, allow_unconverged=True).clone()
+    g = torch.Generator().manual_seed(3)
+    rhs = torch.randn(w["N"], 2, dtype=torch.complex128, generator=g)
+    xa = a.solve_adjoint(rhs, allow_unconverged=True).clone()
     path = tmp_path / "ctx.wcs"
     a.save(path)
     a.close()
@@ -32,8 +35,11 @@ def test_save_load_gives_identical_solves(tmp_path, precision, name):
     b.load(path)
     assert b.info()["rank"] == rank
     jb = b.solve_planewaves(ang, allow_unconverged=True)
+    xb = b.solve_adjoint(rhs, allow_unconverged=True)
     torch.cuda.synchronize()
     assert torch.equal(ja, jb)
+    # the capacitance inverse travels with the file: adjoint solves match too
+    assert torch.equal(xa, xb)
     b.close()
 
 
