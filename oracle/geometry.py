@@ -14,7 +14,30 @@ import numpy as np
 
 
 def rho_function(family, params):
-    """Radial function rho(theta) of a contour family (vectorised, numpy)."""
+    """Radial function rho(theta) of a contour family (vectorised, numpy).
+
+    Optional keys "alpha" (alpha_0, alpha_1, ...) and "beta" (beta_1, beta_2,
+    ...) add a Fourier perturbation sum_m alpha_m cos(m theta) +
+    sum_m beta_m sin(m theta) to any family (the shape parameters of the
+    far-field objective whose gradient oracle/shape.py computes)."""
+    alpha = np.asarray(params.get("alpha", ()), float)
+    beta = np.asarray(params.get("beta", ()), float)
+    base = _base_rho(family, params)
+    if alpha.size == 0 and beta.size == 0:
+        return base
+
+    def f(th):
+        th = np.asarray(th, float)
+        out = base(th)
+        for m, a in enumerate(alpha):
+            out = out + a * np.cos(m * th)
+        for m, b in enumerate(beta, start=1):
+            out = out + b * np.sin(m * th)
+        return out
+    return f
+
+
+def _base_rho(family, params):
     if family == "circle":
         a = float(params.get("a", 1.0))
         return lambda th: np.full_like(np.asarray(th, float), a)

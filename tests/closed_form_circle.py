@@ -154,3 +154,19 @@ def mie_farfield(a, k, phi, phi_obs, nmax=None):
     coef = sp.jvp(n, k * a) / sp.h1vp(n, k * a)
     return -np.sqrt(2.0 / (np.pi * k)) * np.exp(-0.25j * np.pi) * (
         np.exp(1j * np.outer(np.asarray(phi_obs) - phi, n)) @ coef)
+
+
+def discrete_farfield(a, N, k, j, phi_obs, nmax=None):
+    """Far field F(phi_o) of hat coefficients j on the circle of radius a, in
+    closed form: with psi = theta - phi_o, (x^.n) e^{-i k x^.r} = cos psi
+    e^{-i ka cos psi} = i sum_n (-i)^n J_n'(ka) e^{i n psi}, and a hat of
+    width 2h centred at theta_i integrates e^{i n theta} to
+    h sinc^2(pi n / N) e^{i n theta_i}."""
+    h = 2.0 * np.pi * a / N
+    if nmax is None:
+        nmax = int(abs(k * a) + 60)
+    n = np.arange(-nmax, nmax + 1)
+    jhat = np.fft.ifft(np.asarray(j)) * N                 # sum_i j_i e^{2 pi i n i / N} at n mod N
+    coef = 1j * (-1j) ** n * sp.jvp(n, k * a) * h * np.sinc(n / N) ** 2 * jhat[n % N]
+    integral = np.exp(-1j * np.outer(np.atleast_1d(phi_obs), n)) @ coef
+    return 1j * k * np.exp(0.25j * np.pi) / np.sqrt(8.0 * np.pi * k) * integral

@@ -1,0 +1,72 @@
+"""Pins of the oracle's shape gradient (oracle/shape.py), CPU only.
+
+1. On the unit circle the alpha_0 perturbation is a change of radius, so J
+   and dJ/d alpha_0 follow from the closed-form discrete solution and far
+   field (no quadrature, no assembly).
+2. The adjoint formula agrees with central differences of J itself.
+3. Symmetries of the ellipse with incidence and observation sets closed under
+   y -> -y and rotation by pi: J(beta) = J(-beta) and J(alpha_odd) =
+   J(-alpha_odd), so those derivatives vanish; a swapped cos/sin index or a
+   wrong parameter map fails here.
+"""
+
+import numpy as np
+import pytest
+
+import closed_form_circle as cf
+import workloads
+from oracle import geometry, shape
+
+M = 16
+N = 64
+INC = np.deg2rad(np.arange(0.0, 360.0, 22.5))     # 16 incidences, 22.5 degrees apart
+OBS = np.deg2rad(np.arange(0.0, 360.0, 4.0))      # 90 observation angles, 4 degrees apart
+
+
+def _circle_J(a, k):
+    kt = k + 0.4j * k ** (1.0 / 3.0) * a ** (-2.0 / 3.0)     # Sec. III with a = L / 2 pi
+    J = 0.0
+    for phi in INC:
+        j = cf.discrete_solution(a, N, k, kt, phi)
+        J += np.sum(np.abs(cf.discrete_farfield(a, N, k, j, OBS)) ** 2)
+    return J
+
+
+def test_circle_radius_derivative_closed_form():
+    k = 8.0
+    p = np.zeros(2 * M)
+    J, _ = shape.objective("circle", {"a": 1.0}, p, M, N, k, INC, OBS)
+    assert abs(J - _circle_J(1.0, k)) <= 1e-10 * J
+    d = 1e-5
+    g_ref = (_circle_J(1.0 + d, k) - _circle_J(1.0 - d, k)) / (2 * d)
+    g_fd = shape.gradient_fd("circle", {"a": 1.0}, p, M, N, k, INC, OBS, [0], delta=d)[0]
+    _, g_adj = shape.gradient_adjoint("circle", {"a": 1.0}, p, M, N, k, INC, OBS, [0], delta=1e-6)
+    assert abs(g_fd - g_ref) <= 1e-7 * abs(g_ref)
+    assert abs(g_adj[0] - g_ref) <= 1e-7 * abs(g_ref)
+
+
+@pytest.fixture(scope="module")
+def ellipse():
+    w = workloads.WORKLOADS["ellipse_n8192"]
+    L = geometry.Contour(w["family"], w["params"]).L
+    k = 2.0 * np.pi * (N / 10.0) / L
+    return w["family"], w["params"], k
+
+
+def test_adjoint_matches_central_differences(ellipse):
+    fam, base, k = ellipse
+    p = np.zeros(2 * M)
+    p[2] = 0.01                       # away from the symmetric point as well
+    idx = [0, 2, 5, M + 1]
+    _, g_adj = shape.gradient_adjoint(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    g_fd = shape.gradient_fd(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    scale = np.max(np.abs(g_fd))
+    assert np.max(np.abs(g_adj - g_fd)) <= 1e-8 * scale
+
+
+def test_symmetric_parameters_have_zero_derivative(ellipse):
+    fam, base, k = ellipse
+    p = np.zeros(2 * M)
+    J, g = shape.gradient_adjoint(fam, base, p, M, N, k, INC, OBS, [0, 1, 3, M, M + 1], delta=1e-6)
+    assert abs(g[0]) > 1e-2 * J                       # alpha_0: a real effect
+    assert np.max(np.abs(g[1:])) <= 1e-10 * J         # alpha_1, alpha_3, beta_1, beta_2
