@@ -224,6 +224,35 @@ int wcs_solve_planewaves_host(wcs_ctx* ctx, int64_t B, const double* angles_host
 int wcs_solve_rhs(wcs_ctx* ctx, int64_t B, const double* e_dev, const double* h_dev, int64_t ld,
                   double* j_dev, int64_t ldj, wcs_solve_info* info);
 
+/* Shape perturbation of the current contour (any family): adds
+ * sum_{m<M} alpha[m] cos(m theta) + sum_{m=1..M} beta[m-1] sin(m theta) to its
+ * radial function rho(theta) (Sec. II: gamma star-shaped and convex; a
+ * non-convex result fails in wcs_mesh with WCS_ERR_NOT_CONVEX).  Replaces an
+ * earlier perturbation; M = 0 removes it.  Host arrays of M doubles each,
+ * 0 <= M <= 32.  Like the contour setters it discards the mesh and
+ * everything built on it.  Errors: WCS_ERR_STATE (no contour yet),
+ * WCS_ERR_ARG. */
+int wcs_contour_perturb(wcs_ctx* ctx, int M, const double* alpha, const double* beta);
+
+/* Gradient of the far-field objective J = sum_b sum_o |F(phi_o; angle_b)|^2
+ * (B plane-wave incidences, nphi observation angles; F as in wcs_farfield)
+ * with respect to the 2M shape parameters of wcs_contour_perturb, at the
+ * context's current contour: grad[m] = dJ/d alpha_m (m < M), grad[M+m-1] =
+ * dJ/d beta_m (m = 1..M).  N and k stay fixed; the mesh, k~ (Sec. III) and
+ * everything else follow the contour.  Adjoint route: one forward solve
+ * (Eq. 5 through Eq. 9), one adjoint solve lam = C^-H E^H F, then per
+ * parameter 2 Re sum_b [F_b^H dE j_b + lam_b^H (db_b - dC j_b)] with dE, db, dC
+ * central differences (step delta; delta <= 0 means 1e-6) of the far-field
+ * map, the preconditioned right-hand side and C, assembled in FP64 at the
+ * perturbed contours.  angles_host (B), phi_host (nphi) and the outputs
+ * J_host (1) and grad_host (2M) are host memory.  Needs a factored context;
+ * device scratch about 2 N^2 complex FP64 plus a few N x B blocks.
+ * Synchronises the stream.  Errors: WCS_ERR_STATE, WCS_ERR_ARG,
+ * WCS_ERR_NOT_CONVEX (a perturbed contour), WCS_ERR_NOT_CONVERGED (a solve
+ * missed refine_tol; outputs still written). */
+int wcs_shape_gradient(wcs_ctx* ctx, int64_t B, const double* angles_host, int nphi, const double* phi_host,
+                       int M, double delta, double* J_host, double* grad_host);
+
 /* Solve C x = b for B general right-hand sides b of Eq. (5)'s preconditioned
  * system (device, complex FP64, column-major N x B, ldb, ldx >= N): Eq. (9)
  * then refinement x <- x + C~^-1 (b - C x) with the exact product C, to

@@ -13,8 +13,8 @@ namespace wcs {
 __constant__ double c_gl16x[16];
 __constant__ double c_gl16w[16];
 
-__device__ __forceinline__ void rho_derivs(const Contour& c, double th, double& r0, double& r1,
-                                           double& r2) {
+__device__ __forceinline__ void rho_base(const Contour& c, double th, double& r0, double& r1,
+                                         double& r2) {
   double sn, cs;
   sincos(th, &sn, &cs);
   switch (c.family) {
@@ -70,6 +70,26 @@ __device__ __forceinline__ void rho_derivs(const Contour& c, double th, double& 
   }
 }
 
+// rho and its first two theta-derivatives: the family's own plus the shape
+// perturbation sum_m pc_m cos(m th) + ps_m sin(m th) (angle-addition recurrence)
+__device__ __forceinline__ void rho_derivs(const Contour& c, double th, double& r0, double& r1,
+                                           double& r2) {
+  rho_base(c, th, r0, r1, r2);
+  if (c.np == 0) return;
+  double sn, cs;
+  sincos(th, &sn, &cs);
+  double cm = 1.0, sm = 0.0;
+  for (int m = 0; m < c.np; ++m) {
+    const double a = c.pc[m], b = c.ps[m];
+    r0 += a * cm + b * sm;
+    r1 += m * (-a * sm + b * cm);
+    r2 -= (double)m * m * (a * cm + b * sm);
+    const double cn = cm * cs - sm * sn;
+    sm = sm * cs + cm * sn;
+    cm = cn;
+  }
+}
+
 __device__ __forceinline__ double speed(const Contour& c, double th) {
   double r0, r1, r2;
   rho_derivs(c, th, r0, r1, r2);
@@ -106,7 +126,7 @@ __global__ void k_prefix_kahan(const double* len, int P, double* cum) {
 __device__ void point_at(const Contour& c, const double* cum, int P, double L, double s,
                          double& x, double& y, double& nx, double& ny, double& kap) {
   double th;
-  if (c.family == FAM_CIRCLE) {
+  if (c.family == FAM_CIRCLE && c.np == 0) {
     th = s / c.a;
   } else {
     s = s - floor(s / L) * L;

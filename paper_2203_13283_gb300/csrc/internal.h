@@ -13,6 +13,7 @@ namespace wcs {
 // ---------------------------------------------------------------- geometry
 enum ContourFamily { FAM_CIRCLE = 0, FAM_ELLIPSE = 1, FAM_SUPERELLIPSE = 2, FAM_FOURIER = 3 };
 constexpr int kMaxFourier = 64;
+constexpr int kMaxPerturb = 33;
 
 struct Contour {
   int family;
@@ -20,6 +21,10 @@ struct Contour {
   double ax, ay, p;     // ellipse / superellipse
   int nf;               // Fourier: number of coefficients (m = 0..nf-1)
   double fc[kMaxFourier], fs[kMaxFourier];
+  // shape perturbation added to rho of any family:
+  // sum_{m < np} pc[m] cos(m theta) + ps[m] sin(m theta)   (ps[0] = 0)
+  int np;
+  double pc[kMaxPerturb], ps[kMaxPerturb];
 };
 
 // Structure-of-arrays point table: positions, unit outward normals, curvature.
@@ -146,6 +151,9 @@ int gram_apply(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t 
                double alpha, double beta, cudaStream_t s);
 // Column 2-norms of an m x n column-major block into out (device, n doubles).
 int column_norms(const zd* X, int64_t ld, int64_t m, int64_t n, double* out, cudaStream_t s);
+// out[c] = sum_i conj(X[i, c]) Y[i, c] for the n columns of m x n blocks (device, n complex).
+int column_dotc(const zd* X, int64_t ldx, const zd* Y, int64_t ldy, int64_t m, int64_t n, zd* out,
+                cudaStream_t s);
 // Complex Gaussian samples (unit variance per complex entry), Philox-4x32 counter based.
 int gaussian_fill(zd* X, int64_t ld, int64_t m, int64_t n, uint64_t seed, uint64_t offset,
                   cudaStream_t s);

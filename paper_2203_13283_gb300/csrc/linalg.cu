@@ -203,6 +203,36 @@ __global__ void k_colnorm(const zd* X, int64_t ld, int64_t m, double* out) {
   if (threadIdx.x == 0) out[c] = sqrt(red[0]);
 }
 
+__global__ void k_coldotc(const zd* X, int64_t ldx, const zd* Y, int64_t ldy, int64_t m, zd* out) {
+  __shared__ double re[256], im[256];
+  const int64_t c = blockIdx.x;
+  zd s = mkz(0.0);
+  for (int64_t i = threadIdx.x; i < m; i += blockDim.x) s += conj(X[c * ldx + i]) * Y[c * ldy + i];
+  re[threadIdx.x] = s.x;
+  im[threadIdx.x] = s.y;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      re[threadIdx.x] += re[threadIdx.x + o];
+      im[threadIdx.x] += im[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[c] = mkz(re[0], im[0]);
+}
+
+int column_dotc(const zd* X, int64_t ldx, const zd* Y, int64_t ldy, int64_t m, int64_t n, zd* out,
+                cudaStream_t s) {
+  for (int64_t c0 = 0; c0 < n; c0 += 65535) {
+    const int64_t cc = std::min<int64_t>(65535, n - c0);
+    k_coldotc<<<(unsigned)cc, 256, 0, s>>>(X + c0 * ldx, ldx, Y + c0 * ldy, ldy, m, out + c0);
+    note_launch();
+  }
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
 int column_norms(const zd* X, int64_t ld, int64_t m, int64_t n, double* out, cudaStream_t s) {
   if (n <= 0) return 0;
   k_colnorm<<<(unsigned)n, 256, 0, s>>>(X, ld, m, out);

@@ -744,6 +744,20 @@ int wcs_contour_fourier(wcs_ctx* c, int count, const double* cc, const double* s
   return set_contour(c, k);
 }
 
+int wcs_contour_perturb(wcs_ctx* c, int M, const double* alpha, const double* beta) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_CONTOUR) { set_error("set a contour first"); return WCS_ERR_STATE; }
+  if (M < 0 || M > kMaxPerturb - 1 || (M > 0 && (!alpha || !beta))) {
+    set_error("perturbation: 0 <= M <= 32 and alpha, beta required");
+    return WCS_ERR_ARG;
+  }
+  Contour k = c->contour;
+  k.np = M > 0 ? M + 1 : 0;
+  for (int m = 0; m < kMaxPerturb; ++m) { k.pc[m] = 0.0; k.ps[m] = 0.0; }
+  for (int m = 0; m < M; ++m) { k.pc[m] = alpha[m]; k.ps[m + 1] = beta[m]; }
+  return set_contour(c, k);
+}
+
 static int build_points(wcs_ctx* c, const Contour& k, const ArcTable& t, DevBuf& buf, Points& P,
                         const double* xi_dev, int q, bool with_kappa) {
   const int64_t n = c->N * q;
@@ -1632,6 +1646,113 @@ int wcs_solve(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, in
 int wcs_solve_adjoint(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, double* x, int64_t ldx,
                       wcs_solve_info* info) {
   return solve_general(c, B, b, ldb, x, ldx, info, true);
+}
+
+// Far-field shape gradient by the adjoint route.  With j = C^-1 b (forward
+// solve), F = E j and lam = C^-H E^H F (one adjoint solve),
+//   dJ/dp = 2 Re sum_b [F_b^H (dE j_b) + lam_b^H (db_b - dC j_b)],
+// where dE, db and dC are central differences of the far-field map, the
+// preconditioned right-hand side (Eq. 5) and C (Eq. 6) at fixed j: each
+// parameter re-meshes and re-assembles the perturbed contour (FP64 form) in
+// a scratch context, applies it to j and reduces on the device.
+struct CtxGuard {
+  wcs_ctx* t = nullptr;
+  ~CtxGuard() { if (t) wcs_destroy(t); }
+};
+
+int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, const double* phi, int M,
+                       double delta, double* J_out, double* grad) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
+  if (B < 1 || nphi < 1 || !angles || !phi || !J_out || M < 0 || M > kMaxPerturb - 1 || (M > 0 && !grad)) {
+    set_error("shape gradient: bad argument");
+    return WCS_ERR_ARG;
+  }
+  if (!(delta > 0)) delta = 1e-6;
+  const int64_t N = c->N;
+  DevBuf j, lam, E, F, G, ang, phd, eb, hb, bb, Y, W, dots;
+  TRY(j.ensure(sizeof(zd) * N * B));
+  TRY(lam.ensure(sizeof(zd) * N * B));
+  TRY(G.ensure(sizeof(zd) * N * B));
+  TRY(E.ensure(sizeof(zd) * N * nphi));
+  TRY(F.ensure(sizeof(zd) * nphi * B));
+  TRY(W.ensure(sizeof(zd) * nphi * B));
+  TRY(ang.ensure(sizeof(double) * B));
+  TRY(phd.ensure(sizeof(double) * nphi));
+  TRY(dots.ensure(sizeof(zd) * 2 * B));
+  cudaMemcpyAsync(ang.p, angles, sizeof(double) * B, cudaMemcpyHostToDevice, c->s);
+  cudaMemcpyAsync(phd.p, phi, sizeof(double) * nphi, cudaMemcpyHostToDevice, c->s);
+  // forward: j, F = E j, J
+  int status = WCS_OK;
+  wcs_solve_info si{};
+  int r = wcs_solve_planewaves(c, B, angles, j.d(), N, &si);
+  if (r == WCS_ERR_NOT_CONVERGED) status = r;
+  else if (r) return r;
+  TRY(farfield_matrix(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, N, c->h, c->k, phd.d(), nphi, E.z(),
+                      nphi, c->s));
+  TRY(zgemm(nphi, B, N, mkz(1.0), ZView{E.z(), 1, nphi, false}, blk(j.z(), N), mkz(0.0), F.z(), nphi, c->s));
+  std::vector<zd> hd(2 * B);
+  TRY(column_dotc(F.z(), nphi, F.z(), nphi, nphi, B, dots.z(), c->s));
+  cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * B, cudaMemcpyDeviceToHost, c->s);
+  TRY(sync(c));
+  double J = 0.0;
+  for (int64_t b = 0; b < B; ++b) J += hd[b].x;
+  *J_out = J;
+  if (M == 0) return status;
+  // adjoint: lam = C^-H E^H F
+  TRY(zgemm(N, B, nphi, mkz(1.0), ZView{E.z(), nphi, 1, true}, blk(F.z(), nphi), mkz(0.0), G.z(), N, c->s));
+  r = solve_general(c, B, G.d(), N, lam.d(), N, &si, true);
+  if (r == WCS_ERR_NOT_CONVERGED) status = r;
+  else if (r) return r;
+  G.release();
+  // perturbed operators in a scratch FP64 context on the same stream
+  wcs_options o;
+  wcs_default_options(&o);
+  o.precision = WCS_PREC_FP64;
+  CtxGuard guard;
+  TRY(wcs_create(&guard.t, &o, (void*)c->s));
+  wcs_ctx* t = guard.t;
+  TRY(eb.ensure(sizeof(zd) * N * B));
+  TRY(hb.ensure(sizeof(zd) * N * B));
+  TRY(bb.ensure(sizeof(zd) * N * B));
+  TRY(Y.ensure(sizeof(zd) * N * B));
+  for (int i = 0; i < 2 * M; ++i) {
+    zd side[2];
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      Contour k = c->contour;
+      if (k.np == 0) {
+        for (int m = 0; m < kMaxPerturb; ++m) { k.pc[m] = 0.0; k.ps[m] = 0.0; }
+      }
+      k.np = std::max(k.np, M + 1);
+      const double d = sgn == 0 ? delta : -delta;
+      if (i < M) k.pc[i] += d;            // alpha_i
+      else k.ps[i - M + 1] += d;          // beta_{i-M+1}
+      TRY(set_contour(t, k));
+      TRY(wcs_mesh(t, N, c->k));
+      TRY(wcs_assemble(t));
+      TRY(ensure_work(t, B));
+      // R = b(p) - C(p) j
+      TRY(planewave_rhs(t->near, t->quad.wn, t->quad.xn, t->opt.q_near, N, t->h, t->k, ang.d(), (int)B,
+                        eb.z(), hb.z(), N, c->s));
+      TRY(precondition(t, eb.z(), hb.z(), N, bb.z(), N, B, PREC_ACCURATE));
+      TRY(apply_C(t, j.z(), N, Y.z(), N, B, false, PREC_ACCURATE));
+      TRY(axpby(N, B, mkz(1.0), bb.z(), N, mkz(-1.0), Y.z(), N, c->s));
+      TRY(column_dotc(lam.z(), N, Y.z(), N, N, B, dots.z(), c->s));
+      // E(p) j
+      TRY(farfield_matrix(t->near, t->quad.wn, t->quad.xn, t->opt.q_near, N, t->h, t->k, phd.d(), nphi,
+                          E.z(), nphi, c->s));
+      TRY(zgemm(nphi, B, N, mkz(1.0), ZView{E.z(), 1, nphi, false}, blk(j.z(), N), mkz(0.0), W.z(), nphi,
+                c->s));
+      TRY(column_dotc(F.z(), nphi, W.z(), nphi, nphi, B, dots.z() + B, c->s));
+      cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * 2 * B, cudaMemcpyDeviceToHost, c->s);
+      TRY(sync(c));
+      zd acc = mkz(0.0);
+      for (int64_t b = 0; b < 2 * B; ++b) acc += hd[b];
+      side[sgn] = acc;
+    }
+    grad[i] = (side[0].x - side[1].x) / delta;    // 2 Re(t+ - t-) / (2 delta)
+  }
+  return status;
 }
 
 int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j, int64_t ldj,

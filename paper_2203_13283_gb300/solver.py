@@ -73,6 +73,16 @@ class Solver:
             raise ValueError(family)
         return self
 
+    def perturb(self, alpha, beta):
+        """Add sum alpha_m cos(m theta) + sum beta_m sin(m theta) (m from 0 and
+        from 1) to the contour's radial function; len(alpha) == len(beta)."""
+        a, pa = _host(alpha, np.float64)
+        b, pb = _host(beta, np.float64)
+        if len(a) != len(b):
+            raise ValueError("alpha and beta need the same length")
+        check(self.lib.wcs_contour_perturb(self.h, len(a), pa, pb))
+        return self
+
     def mesh(self, N, k=None):
         check(self.lib.wcs_mesh(self.h, int(N), float(k) if k else 0.0))
         self.N = int(N)
@@ -212,6 +222,18 @@ class Solver:
     def solve_adjoint(self, b, allow_unconverged=False):
         """x with C^H x = b (N x B or N, complex128) through the adjoint factors."""
         return self._solve_general(self.lib.wcs_solve_adjoint, b, allow_unconverged)
+
+    def shape_gradient(self, angles, phi_obs, M, delta=1e-6, allow_unconverged=False):
+        """(J, grad): J = sum |F|^2 over incidences and observation angles and
+        its gradient in (alpha_0..alpha_{M-1}, beta_1..beta_M)."""
+        a, pa = _host(angles, np.float64)
+        p, pp = _host(phi_obs, np.float64)
+        J = np.zeros(1)
+        g = np.zeros(max(2 * int(M), 1))
+        allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+        check(self.lib.wcs_shape_gradient(self.h, len(a), pa, len(p), pp, int(M), float(delta),
+                                          J.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p)), allow)
+        return float(J[0]), g[:2 * int(M)]
 
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
                     "sample", "project", "orth", "vw", "inverse")

@@ -1,0 +1,43 @@
+"""GPU parity of the far-field shape gradient (wcs_shape_gradient) and of
+perturbed contours (wcs_contour_perturb) against the oracle (oracle/shape.py):
+J to 1e-9, the gradient to 1e-6 of its largest entry against central
+differences of the oracle's J, and the derivatives that the ellipse's
+symmetries force to zero."""
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_common import built
+from oracle import geometry, shape
+
+pytestmark = pytest.mark.gpu
+
+M = 16
+N = 64
+INC = np.deg2rad(np.arange(0.0, 360.0, 22.5))
+OBS = np.deg2rad(np.arange(0.0, 360.0, 4.0))
+
+
+def test_shape_gradient_vs_oracle():
+    built()
+    from paper_2203_13283_gb300 import Solver
+    w = workloads.WORKLOADS["ellipse_n8192"]
+    fam, base = w["family"], w["params"]
+    k = 2.0 * np.pi * (N / 10.0) / geometry.Contour(fam, base).L
+    p = np.zeros(2 * M)
+    p[2] = 0.01                                    # alpha_2: keeps both symmetries
+    s = Solver(refine_tol=1e-12, max_refine=16)
+    s.contour(fam, **base).perturb(p[:M], p[M:]).mesh(N, k).assemble()
+    s.skeleton(1e-10, max_rank=N // 2, seed=1, allow_cap=True)
+    s.factor()
+    J, g = s.shape_gradient(INC, OBS, M)
+    J_ref, _ = shape.objective(fam, base, p, M, N, k, INC, OBS)
+    assert abs(J - J_ref) <= 1e-9 * J_ref
+    idx = [0, 2, 4, 6]
+    g_ref = shape.gradient_fd(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    scale = np.max(np.abs(g_ref))
+    assert np.max(np.abs(g[idx] - g_ref)) <= 1e-6 * scale
+    odd = [m for m in range(M) if m % 2 == 1] + list(range(M, 2 * M))
+    assert np.max(np.abs(g[odd])) <= 1e-6 * scale
+    s.close()
