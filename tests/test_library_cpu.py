@@ -79,3 +79,27 @@ def test_checkpoint_rejects_null_arguments(lib):
     from paper_2203_13283_gb300._lib import WCS_ERR_ARG
     assert lib.wcs_save(None, b"/nonexistent/ckpt") == WCS_ERR_ARG
     assert lib.wcs_load(None, b"/nonexistent/ckpt") == WCS_ERR_ARG
+
+
+def test_differentiation_entry_points_validate_before_device_work(lib):
+    """wcs_contour_perturb, wcs_solve, wcs_solve_adjoint and wcs_shape_gradient
+    check their arguments and the call order on the host."""
+    import ctypes as C
+    WCS_ERR_ARG, WCS_ERR_STATE = 1, 9
+    h = C.c_void_p()
+    assert lib.wcs_create(C.byref(h), None, None) == 0
+    z = np.zeros(40)
+    pz = z.ctypes.data_as(C.c_void_p)
+    assert lib.wcs_contour_perturb(h, 0, None, None) == WCS_ERR_STATE      # no contour yet
+    assert lib.wcs_contour_ellipse(h, 1.0, 0.7) == 0
+    assert lib.wcs_contour_perturb(h, 33, pz, pz) == WCS_ERR_ARG           # M <= 32
+    assert lib.wcs_contour_perturb(h, 2, None, None) == WCS_ERR_ARG
+    assert lib.wcs_contour_perturb(h, 2, pz, pz) == 0
+    J, g = np.zeros(1), np.zeros(4)
+    assert lib.wcs_shape_gradient(h, 1, pz, 1, pz, 2, 1e-6, J.ctypes.data_as(C.c_void_p),
+                                  g.ctypes.data_as(C.c_void_p)) == WCS_ERR_STATE   # not factored
+    assert lib.wcs_solve(h, 1, pz, 40, pz, 40, None) == WCS_ERR_STATE
+    assert lib.wcs_solve_adjoint(h, 1, pz, 40, pz, 40, None) == WCS_ERR_STATE
+    assert lib.wcs_solve(None, 1, pz, 40, pz, 40, None) == WCS_ERR_ARG
+    assert lib.wcs_shape_gradient(None, 1, pz, 1, pz, 2, 1e-6, None, None) == WCS_ERR_ARG
+    assert lib.wcs_destroy(h) == 0
