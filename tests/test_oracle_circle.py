@@ -1,5 +1,5 @@
 """Pins of the oracle on the circle: closed-form Galerkin eigenvalues, exact
-discrete solution, Mie series (CPU)."""
+discrete solution and its far field, Mie series (CPU)."""
 
 import numpy as np
 import pytest
@@ -52,6 +52,21 @@ def test_circle_rhs_and_discrete_solution(name):
         assert np.max(np.abs(r["h"][:, col] - hc)) < 1e-13 * np.max(np.abs(hc))
         jc = cf.discrete_solution(r["a"], N, r["k"], r["kt"], phi)
         assert np.linalg.norm(r["j"][:, col] - jc) < 1e-11 * np.linalg.norm(jc)
+
+
+@pytest.mark.parametrize("name", ["circle_n64", "circle_n256"])
+def test_circle_discrete_farfield_closed_form(name):
+    # the far field of the discrete solution, in closed form (Jacobi-Anger
+    # and the hat transform), against the oracle's Gauss quadrature of a11
+    r = solved(name)
+    w = r["w"]
+    N = w["N"]
+    obs = np.deg2rad(np.arange(0.0, 360.0, 7.0))
+    F = solver.farfield(r["curve"], N, r["k"], r["j"], obs)
+    for col, phi in enumerate(w["angles"]):
+        jc = cf.discrete_solution(r["a"], N, r["k"], r["kt"], phi)
+        Fc = cf.discrete_farfield(r["a"], N, r["k"], jc, obs)
+        assert np.max(np.abs(F[:, col] - Fc)) < 1e-11 * np.max(np.abs(Fc))
 
 
 def test_circle_mie_convergence():
