@@ -41,3 +41,29 @@ def test_shape_gradient_vs_oracle():
     odd = [m for m in range(M) if m % 2 == 1] + list(range(M, 2 * M))
     assert np.max(np.abs(g[odd])) <= 1e-6 * scale
     s.close()
+
+
+def test_shape_objective_autograd():
+    # the autograd wrapper returns wcs_shape_gradient's J and, through
+    # backward, its gradient scaled by the incoming gradient
+    built()
+    import torch
+    from paper_2203_13283_gb300 import Solver, autograd
+    w = workloads.WORKLOADS["ellipse_n8192"]
+    fam, base = w["family"], w["params"]
+    k = 2.0 * np.pi * (N / 10.0) / geometry.Contour(fam, base).L
+    m = 2
+    p = torch.zeros(2 * m, dtype=torch.float64)
+    p[0] = 0.003
+    p.requires_grad_(True)
+    J = autograd.shape_objective(p, fam, base, N, k, INC, OBS, refine_tol=1e-12, max_refine=16)
+    (3.0 * J).backward()
+    s = Solver(refine_tol=1e-12, max_refine=16)
+    pv = p.detach().numpy()
+    s.contour(fam, **base).perturb(pv[:m], pv[m:]).mesh(N, k).assemble()
+    s.skeleton(1e-10, seed=1, allow_cap=True)
+    s.factor()
+    J_ref, g_ref = s.shape_gradient(INC, OBS, m)
+    s.close()
+    assert abs(J.item() - J_ref) <= 1e-12 * J_ref
+    assert np.max(np.abs(p.grad.numpy() - 3.0 * g_ref)) <= 1e-10 * np.max(np.abs(g_ref))
