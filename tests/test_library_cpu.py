@@ -103,3 +103,27 @@ def test_differentiation_entry_points_validate_before_device_work(lib):
     assert lib.wcs_solve(None, 1, pz, 40, pz, 40, None) == WCS_ERR_ARG
     assert lib.wcs_shape_gradient(None, 1, pz, 1, pz, 2, 1e-6, None, None) == WCS_ERR_ARG
     assert lib.wcs_destroy(h) == 0
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/wcs.h is a C-ABI header: it compiles as strict C99 and as C++."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "wcs.h"\n'
+                   'int main(void) {\n'
+                   '  int (*f)(wcs_options*) = wcs_default_options;\n'
+                   '  int (*g)(wcs_ctx*, int64_t, const double*, int64_t, double*, int64_t, wcs_solve_info*) =\n'
+                   '      wcs_solve_adjoint;\n'
+                   '  return (int)(sizeof(wcs_options) == 0) + (f == 0) + (g == 0);\n'
+                   '}\n')
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-fsyntax-only", "-I", inc,
+                    str(src)], check=True)
+    gxx = shutil.which("g++")
+    if gxx:
+        subprocess.run([gxx, "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, "-x", "c++", str(src)],
+                       check=True)
