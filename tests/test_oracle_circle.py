@@ -105,3 +105,15 @@ def test_generic_contour_path_on_circle_is_circulant_counterpart():
     assert np.max(np.abs(C - Cc)) < 1e-12 * np.max(np.abs(Cc))
     U, V = solver.reference_skeleton(C, Cc, 1e-10)
     assert U.shape[1] == 0
+
+
+def test_mie_optical_theorem():
+    # the normalisation of the optical theorem used on non-circles, checked
+    # on the exact Mie far field
+    a, k, phi = 1.0, 8.0, 0.3
+    n_obs = 2048
+    po = 2.0 * np.pi * np.arange(n_obs) / n_obs
+    power = np.sum(np.abs(cf.mie_farfield(a, k, phi, po)) ** 2) * 2.0 * np.pi / n_obs
+    Ff = cf.mie_farfield(a, k, phi, np.array([phi]))[0]
+    ext = -np.sqrt(8.0 * np.pi / k) * np.real(np.exp(0.25j * np.pi) * Ff)
+    assert abs(power - ext) < 1e-12 * power

@@ -1,4 +1,4 @@
-"""Pins of the oracle's solver pieces: brute-force Woodbury, invariants (CPU)."""
+"""Pins of the oracle's solver pieces: brute-force Woodbury, invariants, energy balance (CPU)."""
 
 import numpy as np
 import pytest
@@ -57,6 +57,24 @@ def test_reciprocity_farfield():
     F1 = solver.farfield(cur, N, k, j[:, :1], [po])[0, 0]
     F2 = solver.farfield(cur, N, k, j[:, 1:], [pi_ + np.pi])[0, 0]
     assert abs(F1 - F2) < 2e-3 * abs(F1)
+
+
+@pytest.mark.parametrize("name", ["ellipse_n200", "star_n200", "superellipse_n320"])
+def test_optical_theorem(name):
+    # energy balance of a lossless scatterer: the scattered power equals the
+    # extinction read off the forward far field,
+    #   int |F|^2 dphi = -sqrt(8 pi / k) Re(e^{i pi/4} F(phi_inc)),
+    # exact for the Mie series (normalisation and signs), O(h^2) here; a sign
+    # slip in an operator or the right-hand side breaks it at O(1)
+    r = solved(name)
+    w = r["w"]
+    n_obs = 720                                        # trapezoid on a periodic, band-limited F
+    po = 2.0 * np.pi * np.arange(n_obs) / n_obs
+    F = solver.farfield(r["curve"], w["N"], r["k"], r["j"], np.concatenate([po, w["angles"]]))
+    power = np.sum(np.abs(F[:n_obs]) ** 2, axis=0) * 2.0 * np.pi / n_obs
+    for b in range(len(w["angles"])):
+        ext = -np.sqrt(8.0 * np.pi / r["k"]) * np.real(np.exp(0.25j * np.pi) * F[n_obs + b, b])
+        assert abs(power[b] - ext) < 1e-3 * power[b]
 
 
 def test_quadrature_order_convergence():
