@@ -16,8 +16,10 @@ gradient_adjoint takes the adjoint route.  With lam_b = C^-H E^H F_b,
 
 where dE, db, dC are central differences of the far-field map, the
 right-hand side and the operator at fixed j (one adjoint solve instead of a
-solve per parameter).  Both use dense LU; nothing here is shared with the
-CUDA path.
+solve per parameter).  gradient_bilinear is the same gradient with dC
+expanded by the product rule into bilinear forms of the individual operators
+(the reference for a one-pass derivative kernel).  All use dense LU;
+nothing here is shared with the CUDA path.
 """
 
 import numpy as np
@@ -45,6 +47,18 @@ def system(family, base_params, p, M, N, k, inc, obs):
     b = solver.preconditioned_rhs(ops, k, e, hv)
     E = solver.farfield(cur, N, k, np.eye(N), obs)
     return C, b, E
+
+
+def operators_at(family, base_params, p, M, N, k, inc, obs):
+    """Galerkin operators (S~, D, D~, N, G), the Eq. (5) right-hand side b and
+    the far-field map E of the perturbed contour."""
+    cur = geometry.Contour(family, shape_params(base_params, p, M))
+    _, kt, _ = geometry.wavenumbers(cur.L, N, k)
+    ops = assembly.assemble(cur, N, k, kt)
+    e, hv = solver.planewave_rhs(cur, N, k, inc)
+    b = solver.preconditioned_rhs(ops, k, e, hv)
+    E = solver.farfield(cur, N, k, np.eye(N), obs)
+    return ops, b, E, cur.L
 
 
 def objective(family, base_params, p, M, N, k, inc, obs):
@@ -90,3 +104,52 @@ def gradient_adjoint(family, base_params, p, M, N, k, inc, obs, idx, delta=1e-4)
         g = np.sum(F.conj() * (dE @ j)) + np.sum(lam.conj() * (db - dC @ j))
         out.append(2.0 * g.real)
     return J, np.array(out)
+
+
+def gradient_bilinear(family, base_params, p, M, N, k, inc, obs, idx, delta=1e-6):
+    """The adjoint gradient with dC expanded by the product rule over Eq. (6),
+    the form a one-pass derivative kernel evaluates.  With
+    t1 = G^-1 (G/2 - D) j, t2 = G^-1 N j, s1 = G^-H (G/2 + D~)^H lam and
+    s2 = G^-H S~^H lam:
+
+        lam^H dC j = lam^H (dG/2 + dD~) t1 + s1^H (dG/2 - dD) j - s1^H dG t1
+                     + lam^H dS~ t2 + s2^H dN j - s2^H dG t2.
+
+    Each operator derivative is a central difference of that operator alone.
+    Returns (J, grad, terms), terms[i] holding the four operator bilinear
+    forms lam^H dD~ t1, s1^H dD j, lam^H dS~ t2, s2^H dN j (summed over the
+    incidences) and dh / h of parameter i (dG = (dh / h) G on a mesh uniform
+    in arc length)."""
+    p = np.asarray(p, float)
+    ops, b, E, L0 = operators_at(family, base_params, p, M, N, k, inc, obs)
+    G = ops["G"]
+    C = assembly.preconditioned(ops)
+    j = np.linalg.solve(C, b)
+    F = E @ j
+    J = float(np.sum(np.abs(F) ** 2))
+    lam = np.linalg.solve(C.conj().T, E.conj().T @ F)
+    t1 = np.linalg.solve(G, 0.5 * G @ j - ops["D"] @ j)
+    t2 = np.linalg.solve(G, ops["N"] @ j)
+    s1 = np.linalg.solve(G.T, (0.5 * G + ops["Dt"]).conj().T @ lam)
+    s2 = np.linalg.solve(G.T, ops["S"].conj().T @ lam)
+
+    def form(u, X, w):
+        return np.sum(u.conj() * (X @ w))
+
+    grads, terms = [], []
+    for i in idx:
+        u = _unit(p, i, M)
+        op_p, b_p, E_p, L_p = operators_at(family, base_params, p + delta * u, M, N, k, inc, obs)
+        op_m, b_m, E_m, L_m = operators_at(family, base_params, p - delta * u, M, N, k, inc, obs)
+        d = {key: (op_p[key] - op_m[key]) / (2.0 * delta) for key in ("S", "D", "Dt", "N", "G")}
+        db = (b_p - b_m) / (2.0 * delta)
+        dE = (E_p - E_m) / (2.0 * delta)
+        dGt = form(lam, 0.5 * d["G"], t1) - form(s1, d["G"], t1) + form(s1, 0.5 * d["G"], j) \
+            - form(s2, d["G"], t2)
+        fDt, fD = form(lam, d["Dt"], t1), form(s1, d["D"], j)
+        fS, fN = form(lam, d["S"], t2), form(s2, d["N"], j)
+        dCj = dGt + fDt - fD + fS + fN
+        g = np.sum(F.conj() * (dE @ j)) + np.sum(lam.conj() * db) - dCj
+        grads.append(2.0 * g.real)
+        terms.append(dict(Dt=fDt, D=fD, S=fS, N=fN, dh_over_h=(L_p - L_m) / (2.0 * delta * L0)))
+    return J, np.array(grads), terms

@@ -70,3 +70,21 @@ def test_symmetric_parameters_have_zero_derivative(ellipse):
     J, g = shape.gradient_adjoint(fam, base, p, M, N, k, INC, OBS, [0, 1, 3, M, M + 1], delta=1e-6)
     assert abs(g[0]) > 1e-2 * J                       # alpha_0: a real effect
     assert np.max(np.abs(g[1:])) <= 1e-10 * J         # alpha_1, alpha_3, beta_1, beta_2
+
+
+def test_product_rule_bilinear_forms(ellipse):
+    # the product-rule expansion of lam^H dC j over Eq. (6) reproduces the
+    # adjoint gradient, and the Gram derivative is dG = (dh / h) G
+    fam, base, k = ellipse
+    p = np.zeros(2 * M)
+    p[2] = 0.01
+    idx = [0, 2]
+    J, g_bil, terms = shape.gradient_bilinear(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    _, g_adj = shape.gradient_adjoint(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    assert np.max(np.abs(g_bil - g_adj)) <= 1e-9 * np.max(np.abs(g_adj))
+    ops, _, _, L = shape.operators_at(fam, base, p, M, N, k, INC, OBS)
+    ops_p, _, _, L_p = shape.operators_at(fam, base, p + 1e-6 * np.eye(2 * M)[0], M, N, k, INC, OBS)
+    dG = (ops_p["G"] - ops["G"]) / 1e-6
+    assert np.max(np.abs(dG - (L_p - L) / (1e-6 * L) * ops["G"])) <= 1e-12 * np.max(np.abs(ops["G"])) / 1e-6
+    for t in terms:
+        assert all(np.isfinite(t[key]) for key in ("Dt", "D", "S", "N"))
