@@ -253,6 +253,15 @@ int wcs_contour_perturb(wcs_ctx* ctx, int M, const double* alpha, const double* 
 int wcs_shape_gradient(wcs_ctx* ctx, int64_t B, const double* angles_host, int nphi, const double* phi_host,
                        int M, double delta, double* J_host, double* grad_host);
 
+/* wcs_shape_gradient for the parameters i0 <= i < i1 only (0 <= i0 <= i1 <=
+ * 2M, same numbering): grad_host[i - i0] = dJ/dp_i.  J_host is always
+ * written.  The parameters are independent, so ranks of a multi-GPU job can
+ * each take a contiguous range and gather the pieces.  Same errors as
+ * wcs_shape_gradient; grad_host may be null when i0 == i1. */
+int wcs_shape_gradient_range(wcs_ctx* ctx, int64_t B, const double* angles_host, int nphi,
+                             const double* phi_host, int M, double delta, int i0, int i1, double* J_host,
+                             double* grad_host);
+
 /* Solve C x = b for B general right-hand sides b of Eq. (5)'s preconditioned
  * system (device, complex FP64, column-major N x B, ldb, ldx >= N): Eq. (9)
  * then refinement x <- x + C~^-1 (b - C x) with the exact product C, to

@@ -64,6 +64,7 @@ SIGNATURES = {
     "wcs_solve": (I, [P, I64, P, I64, P, I64, C.POINTER(SolveInfo)]),
     "wcs_contour_perturb": (I, [P, C.c_int, P, P]),
     "wcs_shape_gradient": (I, [P, I64, P, C.c_int, P, C.c_int, C.c_double, P, P]),
+    "wcs_shape_gradient_range": (I, [P, I64, P, C.c_int, P, C.c_int, C.c_double, C.c_int, C.c_int, P, P]),
     "wcs_solve_adjoint": (I, [P, I64, P, I64, P, I64, C.POINTER(SolveInfo)]),
     "wcs_planewave_rhs": (I, [P, I64, P, P, P, I64]),
     "wcs_farfield": (I, [P, I64, P, I64, I, P, P, I64]),

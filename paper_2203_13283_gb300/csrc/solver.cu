@@ -1660,11 +1660,12 @@ struct CtxGuard {
   ~CtxGuard() { if (t) wcs_destroy(t); }
 };
 
-int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, const double* phi, int M,
-                       double delta, double* J_out, double* grad) {
+int wcs_shape_gradient_range(wcs_ctx* c, int64_t B, const double* angles, int nphi, const double* phi, int M,
+                             double delta, int i0, int i1, double* J_out, double* grad) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
   if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
-  if (B < 1 || nphi < 1 || !angles || !phi || !J_out || M < 0 || M > kMaxPerturb - 1 || (M > 0 && !grad)) {
+  if (B < 1 || nphi < 1 || !angles || !phi || !J_out || M < 0 || M > kMaxPerturb - 1 || i0 < 0 ||
+      i1 < i0 || i1 > 2 * M || (i1 > i0 && !grad)) {
     set_error("shape gradient: bad argument");
     return WCS_ERR_ARG;
   }
@@ -1698,7 +1699,7 @@ int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, co
   double J = 0.0;
   for (int64_t b = 0; b < B; ++b) J += hd[b].x;
   *J_out = J;
-  if (M == 0) return status;
+  if (i1 == i0) return status;
   // adjoint: lam = C^-H E^H F
   TRY(zgemm(N, B, nphi, mkz(1.0), ZView{E.z(), nphi, 1, true}, blk(F.z(), nphi), mkz(0.0), G.z(), N, c->s));
   r = solve_general(c, B, G.d(), N, lam.d(), N, &si, true);
@@ -1716,7 +1717,7 @@ int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, co
   TRY(hb.ensure(sizeof(zd) * N * B));
   TRY(bb.ensure(sizeof(zd) * N * B));
   TRY(Y.ensure(sizeof(zd) * N * B));
-  for (int i = 0; i < 2 * M; ++i) {
+  for (int i = i0; i < i1; ++i) {
     zd side[2];
     for (int sgn = 0; sgn < 2; ++sgn) {
       Contour k = c->contour;
@@ -1750,9 +1751,14 @@ int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, co
       for (int64_t b = 0; b < 2 * B; ++b) acc += hd[b];
       side[sgn] = acc;
     }
-    grad[i] = (side[0].x - side[1].x) / delta;    // 2 Re(t+ - t-) / (2 delta)
+    grad[i - i0] = (side[0].x - side[1].x) / delta;    // 2 Re(t+ - t-) / (2 delta)
   }
   return status;
+}
+
+int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, const double* phi, int M,
+                       double delta, double* J_out, double* grad) {
+  return wcs_shape_gradient_range(c, B, angles, nphi, phi, M, delta, 0, 2 * M, J_out, grad);
 }
 
 int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j, int64_t ldj,

@@ -223,17 +223,20 @@ class Solver:
         """x with C^H x = b (N x B or N, complex128) through the adjoint factors."""
         return self._solve_general(self.lib.wcs_solve_adjoint, b, allow_unconverged)
 
-    def shape_gradient(self, angles, phi_obs, M, delta=1e-6, allow_unconverged=False):
+    def shape_gradient(self, angles, phi_obs, M, delta=1e-6, allow_unconverged=False, params=None):
         """(J, grad): J = sum |F|^2 over incidences and observation angles and
-        its gradient in (alpha_0..alpha_{M-1}, beta_1..beta_M)."""
+        its gradient in (alpha_0..alpha_{M-1}, beta_1..beta_M); params = (i0, i1)
+        restricts grad to those parameters (a rank's share of a sharded job)."""
         a, pa = _host(angles, np.float64)
         p, pp = _host(phi_obs, np.float64)
+        i0, i1 = (0, 2 * int(M)) if params is None else (int(params[0]), int(params[1]))
         J = np.zeros(1)
-        g = np.zeros(max(2 * int(M), 1))
+        g = np.zeros(max(i1 - i0, 1))
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
-        check(self.lib.wcs_shape_gradient(self.h, len(a), pa, len(p), pp, int(M), float(delta),
-                                          J.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p)), allow)
-        return float(J[0]), g[:2 * int(M)]
+        check(self.lib.wcs_shape_gradient_range(self.h, len(a), pa, len(p), pp, int(M), float(delta), i0, i1,
+                                                J.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p)),
+              allow)
+        return float(J[0]), g[:i1 - i0]
 
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
                     "sample", "project", "orth", "vw", "inverse")

@@ -72,3 +72,37 @@ def test_single_process_max_is_identity():
     assert wdist.max_over_ranks([3.0, 4.0]) == [3.0, 4.0]
     with pytest.raises(ValueError):
         wdist.shard_columns(4, 2, 2)
+
+
+def _gather_main(rank, world_size, port, n, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world_size)
+    try:
+        c0, c1 = wdist.shard_columns(n, rank, world_size)
+        local = [float(i * i) + 0.5 for i in range(c0, c1)]      # a rank's share of a gradient
+        out.put((rank, wdist.gather_shards(local, n)))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("n", [32, 7, 1])
+def test_two_rank_gather_of_parameter_shares(n):
+    # the shape gradient's parameters split over two ranks and gathered back:
+    # each rank ends with the whole vector in parameter order
+    ctx = mp.get_context("spawn")
+    out = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_main, args=(r, 2, port, n, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(out.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    want = [float(i * i) + 0.5 for i in range(n)]
+    assert res[0] == want and res[1] == want
+
+
+def test_gather_shards_single_process():
+    assert wdist.gather_shards([1.0, 2.0], 2) == [1.0, 2.0]

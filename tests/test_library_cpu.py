@@ -102,6 +102,9 @@ def test_differentiation_entry_points_validate_before_device_work(lib):
     assert lib.wcs_solve_adjoint(h, 1, pz, 40, pz, 40, None) == WCS_ERR_STATE
     assert lib.wcs_solve(None, 1, pz, 40, pz, 40, None) == WCS_ERR_ARG
     assert lib.wcs_shape_gradient(None, 1, pz, 1, pz, 2, 1e-6, None, None) == WCS_ERR_ARG
+    assert lib.wcs_shape_gradient_range(None, 1, pz, 1, pz, 2, 1e-6, 0, 4, None, None) == WCS_ERR_ARG
+    assert lib.wcs_shape_gradient_range(h, 1, pz, 1, pz, 2, 1e-6, 0, 4, J.ctypes.data_as(C.c_void_p),
+                                        g.ctypes.data_as(C.c_void_p)) == WCS_ERR_STATE
     assert lib.wcs_destroy(h) == 0
 
 
