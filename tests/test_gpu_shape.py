@@ -13,10 +13,10 @@ from oracle import geometry, shape
 
 pytestmark = pytest.mark.gpu
 
-M = 16
+M = workloads.WORKLOADS["ellipse_n8192"]["shape_modes"]
 N = 64
-INC = np.deg2rad(np.arange(0.0, 360.0, 22.5))
-OBS = np.deg2rad(np.arange(0.0, 360.0, 4.0))
+INC = workloads.WORKLOADS["ellipse_n8192"]["angles"]                # 16 incidences, 22.5 degrees apart
+OBS = workloads.WORKLOADS["ellipse_n8192"]["observation_angles"]    # 90 observation angles, 4 degrees apart
 
 
 def test_shape_gradient_vs_oracle():

@@ -17,10 +17,10 @@ import closed_form_circle as cf
 import workloads
 from oracle import geometry, shape
 
-M = 16
+M = workloads.WORKLOADS["ellipse_n8192"]["shape_modes"]
 N = 64
-INC = np.deg2rad(np.arange(0.0, 360.0, 22.5))     # 16 incidences, 22.5 degrees apart
-OBS = np.deg2rad(np.arange(0.0, 360.0, 4.0))      # 90 observation angles, 4 degrees apart
+INC = workloads.WORKLOADS["ellipse_n8192"]["angles"]                # 16 incidences, 22.5 degrees apart
+OBS = workloads.WORKLOADS["ellipse_n8192"]["observation_angles"]    # 90 observation angles, 4 degrees apart
 
 
 def _circle_J(a, k):

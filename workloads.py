@@ -40,7 +40,8 @@ WORKLOADS = {
                                 N=32768, k=None, angles=uniform_angles(1024), tol=1e-7),
     # ellipse 1.0 x 0.7 (shape-derivative workload), 16 angles 22.5 degrees apart
     "ellipse_n8192": dict(family="ellipse", params={"ax": 1.0, "ay": 0.7}, N=8192, k=None,
-                          angles=uniform_angles(16), tol=1e-10),
+                          angles=uniform_angles(16), tol=1e-10,
+                          shape_modes=16, observation_angles=np.deg2rad(np.arange(0.0, 360.0, 4.0))),
 }
 
 # small cases of the same families, sized so the CPU oracle runs in seconds
