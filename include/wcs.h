@@ -90,9 +90,18 @@ typedef struct wcs_info {
   double min_curvature; /* minimum curvature found by the convexity check */
 } wcs_info;
 
+/* Entries of wcs_solve_info::history. */
+#define WCS_HISTORY 32
+
 typedef struct wcs_solve_info {
   int refine_steps;   /* iterative-refinement steps taken (max over chunks) */
   double rel_residual;/* max over columns of ||b - C x|| / ||b|| at exit */
+  int history_len;    /* entries of history[] that describe steps taken (<= WCS_HISTORY) */
+  double history[WCS_HISTORY]; /* history[i]: max over columns of the relative residual
+                         after i refinement steps (i = 0: the Woodbury solve of Eq. 9 alone).
+                         A chunk that stopped earlier contributes its final residual.  In the
+                         mixed form a step's entry is the residual carried by the updates
+                         R <- R - C dx unless it was recomputed at that step. */
 } wcs_solve_info;
 
 /* Operators selectable by wcs_apply / wcs_circulant_eigs. */
@@ -107,7 +116,8 @@ typedef enum wcs_op {
   WCS_OP_DT = 7,      /* D^k~ */
   WCS_OP_N = 8,       /* N^k */
   WCS_OP_G = 9,       /* Gram matrix of the hats */
-  WCS_OP_SKEL = 10    /* U V^T, the skeleton of C - C_c (Eq. 7) */
+  WCS_OP_SKEL = 10,   /* U V^T, the skeleton of C - C_c (Eq. 7) */
+  WCS_OP_GINV = 11    /* G^-1 (cyclic tridiagonal solve) */
 } wcs_op;
 
 /* Library version string. */
@@ -153,8 +163,11 @@ int wcs_query(const wcs_ctx* ctx, wcs_info* info);
 int wcs_geometry_sample(wcs_ctx* ctx, int64_t count, const double* s_host, double* out_host);
 
 /* Assemble the Galerkin matrices S^k~, D^k, D^k~, N^k of Eq. (4)/(5) on gamma
- * (dense, FP64, device-resident) and the circulant eigenvalues of the same
- * operators on gamma_c, from which mu_C of C_c (Eq. 6 on the circle) follows. */
+ * (device-resident: dense complex FP64 in the FP64 form; in the mixed form
+ * split-bf16 planes of each operator and of its transpose, from entries
+ * integrated in FP64, or for far pairs in FP32 when zfast > 0) and the
+ * circulant eigenvalues of the same operators on gamma_c (always FP64), from
+ * which mu_C of C_c (Eq. 6 on the circle) follows. */
 int wcs_assemble(wcs_ctx* ctx);
 
 /* Entries of (S~, D, D~, N) at (rows_host[t], cols_host[t]), computed point-wise
@@ -191,15 +204,18 @@ int wcs_factor(wcs_ctx* ctx);
  * W~ = C_c^-1 U (I + V^T C_c^-1 U)^-1 and the capacitance inverse
  * (I + V^T C_c^-1 U)^-1 (rank x rank, for wcs_solve_adjoint), plus the
  * contour, N, k and the options, in a host file at `path` (complex FP64,
- * about 48 N rank bytes).  Files without the capacitance inverse (format
- * version 1) still load; their contexts solve forward only.
+ * about 48 N rank bytes).  wcs_save writes format version 3, which ends with
+ * a 64-bit FNV-1a checksum of the whole file; wcs_load checks the file's
+ * length and checksum before any device work, so a truncated or corrupted
+ * file is rejected with the context left as it was.  Files of versions 1
+ * and 2 (no checksum) still load; version-1 contexts solve forward only.
  * The operators are not stored.  wcs_load re-runs the mesh and the assembly,
  * which are deterministic, on a context created with the same precision and
  * quadrature options (else WCS_ERR_ARG), then restores the factors; the
  * context is then in the factored state.  Both synchronise the context
  * stream.  Errors: WCS_ERR_STATE (save before wcs_factor), WCS_ERR_ARG
- * (null arguments, unreadable/truncated/foreign file, option mismatch),
- * or the status of the mesh/assembly step. */
+ * (null arguments, unreadable/truncated/corrupted/foreign file, option
+ * mismatch), or the status of the mesh/assembly step. */
 int wcs_save(wcs_ctx* ctx, const char* path);
 int wcs_load(wcs_ctx* ctx, const char* path);
 
@@ -351,6 +367,15 @@ int wcs_profile(wcs_ctx* ctx, int enable);
  * product), assembly (work = far point pairs), FFT circulant applies (bytes),
  * FP64 GEMM, skeleton, factor, solve.  reset != 0 clears the records. */
 int wcs_profile_read(wcs_ctx* ctx, int reset, double* out_host);
+
+/* Measured issue rate of the FMA pipe (precision 64: FP64, 32: FP32) on the
+ * current device, in flops per second (an FMA counts as 2): a dependency-free
+ * stream of `iters` rounds of 8 independent FMA chains per thread over a grid
+ * of 8 CTAs of 256 threads per SM, timed with CUDA events on `stream`.  The
+ * paper has no counterpart: this gives the roofline denominator of the
+ * point-pair integration kernels (Eq. 4), which run on these pipes.
+ * Allocates a small output buffer; synchronises the stream. */
+int wcs_fma_rate(int precision, int iters, void* stream, double* flops_per_s);
 
 /* Host-only: product-integration weights of the near-field rule with q points
  * (3 * q * q doubles: coincident, next-neighbour, previous-neighbour pairs). */

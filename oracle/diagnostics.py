@@ -51,3 +51,13 @@ def rank_and_error(curve, N, eps, angles, k=None):
     jw = solver.woodbury_solve(Cc, U, V, b)
     err = float(np.max(np.linalg.norm(jw - j, axis=0) / np.linalg.norm(j, axis=0)))
     return U.shape[1], err, k
+
+
+def frequency_response(X, G):
+    """||G^-1 X v_m|| for the unit Fourier vectors v_m(j) = e^{2 pi i m j / N} / sqrt(N),
+    m = 0..N-1: how strongly X acts at each spatial frequency (Sec. IV-V).
+    For a circulant X (the circle) this is |mu_X(m) / mu_G(m)| exactly."""
+    N = X.shape[0]
+    j = np.arange(N)
+    V = np.exp(2j * np.pi * np.outer(j, np.arange(N)) / N) / np.sqrt(N)
+    return np.linalg.norm(np.linalg.solve(G, X @ V), axis=0)

@@ -13,7 +13,7 @@ STATUS_NAMES = {0: "WCS_OK", 1: "WCS_ERR_ARG", 2: "WCS_ERR_NOT_CONVEX", 3: "WCS_
                 10: "WCS_ERR_UNSUPPORTED"}
 
 OPS = {"C": 0, "CH": 1, "CC": 2, "CCH": 3, "CC_INV": 4, "S": 5, "D": 6, "DT": 7, "N": 8, "G": 9,
-       "SKEL": 10}
+       "SKEL": 10, "GINV": 11}
 
 
 class Options(C.Structure):
@@ -30,8 +30,12 @@ class Info(C.Structure):
                 ("rank", C.c_int), ("norm_cc", C.c_double), ("min_curvature", C.c_double)]
 
 
+WCS_HISTORY = 32
+
+
 class SolveInfo(C.Structure):
-    _fields_ = [("refine_steps", C.c_int), ("rel_residual", C.c_double)]
+    _fields_ = [("refine_steps", C.c_int), ("rel_residual", C.c_double), ("history_len", C.c_int),
+                ("history", C.c_double * WCS_HISTORY)]
 
 
 # exported symbol -> (restype, argtypes); mirrors include/wcs.h
@@ -75,6 +79,7 @@ SIGNATURES = {
     "wcs_profile": (I, [P, I]),
     "wcs_profile_read": (I, [P, I, P]),
     "wcs_quadrature_tables": (I, [I, P]),
+    "wcs_fma_rate": (I, [I, I, P, C.POINTER(C.c_double)]),
 }
 
 _lib = None

@@ -26,7 +26,6 @@
 namespace wcs {
 
 __constant__ double c_xf[16], c_wf[16], c_xn[16], c_wn[16];
-__constant__ float c_xff[16], c_wff[16];   // the far rule in FP32 (no FP64 conversion per point pair)
 
 struct PairOut {
   zd v[4][4];  // [operator S~, D, D~, N][a * 2 + b]
@@ -188,34 +187,64 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
 // ---------------------------------------------------------------------------
 // Far element pairs in the mixed form.  With element centres c_e, c_f and
 // point offsets o = r - c (|o| < h), R = |d0 + o_p - o_r| with d0 = c_e - c_f:
-// R0 = |d0| and the phase k R0 mod 2 pi are formed in FP64 once per pair;
-// R - R0 = (2 d0.(o_p - o_r) + |o_p - o_r|^2) / (R + R0) is small and
-// accurate in FP32, so the phase k R = (k R0 mod 2 pi) + k (R - R0) keeps
-// ~1e-7 absolute accuracy even for k R ~ 1e4.  The Hankel functions use the
-// large-argument expansion (DLMF 10.17.5) with ten terms (z >= 9 gives
-// < 1e-7), for k and for k~ = k + i beta (exp(i k~ R) = exp(i k R - beta R)).
+// R0 = |d0| and the phase k R0 mod 2 pi are formed in float-float once per
+// pair; R - R0 = (2 d0.(o_p - o_r) + |o_p - o_r|^2) / (R + R0) is small, so
+// the phase k R = (k R0 mod 2 pi) + k (R - R0) keeps ~1e-7 absolute accuracy
+// even for k R ~ 1e4.  The Hankel functions use the large-argument expansion
+// (DLMF 10.17.5) with ten terms (z >= 9 gives < 1e-7), for k and for
+// k~ = k + i beta (exp(i k~ R) = exp(i k R - beta R)).
+//
+// Roundings that repeat identically in every element pair act like one
+// perturbation of the whole operator and are not averaged out: the products
+// of quadrature weights and hat values, the wavenumber constants, the point
+// offsets and the normals.  So the weights come from float-float tables
+// (the tensor rule is separable: an inner sum over the source points r with
+// weights w_r phi_b(xi_r), an outer sum over the target points p with
+// w_p phi_a(xi_p)), offsets and normals carry float-float tails, and every
+// constant factor of a kernel is left out of the FP32 sums and applied in
+// FP64 when the entry is stored (AsmArgs::fS .. fN, kk2h2).  What remains in
+// FP32 varies from pair to pair (the rounding of R, the Hankel series, the
+// sums), so its effect on the solution averages down.
 // ---------------------------------------------------------------------------
 __constant__ float c_a0[10], c_a1[10];   // a_k(0), a_k(1) of the Hankel expansion
+__constant__ float c_fwt[2][16][2];      // w_r phi_b(xi_r) as float-float [b][r][hi, lo]
+__constant__ float c_fw[16][2];          // w_r as float-float
 
 struct cf {
   float x, y;
 };
 __device__ __forceinline__ cf cmul(cf a, cf b) { return {fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x)}; }
 __device__ __forceinline__ cf cscale(cf a, float s) { return {a.x * s, a.y * s}; }
+// acc += (hi + lo) v, the small term first
+__device__ __forceinline__ void cfma2(cf& acc, float hi, float lo, cf v) {
+  acc.x = fmaf(hi, v.x, fmaf(lo, v.x, acc.x));
+  acc.y = fmaf(hi, v.y, fmaf(lo, v.y, acc.y));
+}
+__device__ __forceinline__ void cadd(cf& acc, cf v) { acc.x += v.x; acc.y += v.y; }
 
+// Reduced sums of one element pair, [a * 2 + b]:
+//   0  S~ / fS     1  D / fD     2  D~ / fD~
+//   3  N, k^2 h^2 (n.n') part     4  N, derivative part (signs s_a s_b applied)
+// with N = fN (v[4] - k^2 h^2 v[3]).
 struct PairOutF {
-  cf v[4][4];
+  cf v[5][4];
 };
 
 __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& out);
 
+__device__ __forceinline__ zd zf2d(cf a) { return mkz((double)a.x, (double)a.y); }
+
+// The four operators of a far pair from the reduced FP32 sums (FP64 factors).
 __device__ void pair_fast(const AsmArgs& A, int64_t e, int64_t f, PairOut& out) {
   PairOutF o;
   pair_fast_f(A, e, f, o);
 #pragma unroll
-  for (int op = 0; op < 4; ++op)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out.v[op][j] = mkz((double)o.v[op][j].x, (double)o.v[op][j].y);
+  for (int j = 0; j < 4; ++j) {
+    out.v[0][j] = A.fS * zf2d(o.v[0][j]);
+    out.v[1][j] = A.fD * zf2d(o.v[1][j]);
+    out.v[2][j] = A.fDt * zf2d(o.v[2][j]);
+    out.v[3][j] = A.fN * (zf2d(o.v[4][j]) - A.kk2h2 * zf2d(o.v[3][j]));
+  }
 }
 
 // Float-float arithmetic (value = hi + lo, ~48 bits; Dekker/Knuth error-free
@@ -273,38 +302,37 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
   const ff twoR0 = {2.f * R0.hi, 2.f * R0.lo};
   const ff kff = {F.k_hi, F.k_lo};
   const float ldx0 = dx.lo, ldy0 = dy.lo;
-  const float k = F.kf, beta = F.beta;
-  const cf ck = {F.ck[0], F.ck[1]};      // sqrt(2 / (pi k~))
+  const float k = F.kf, beta = F.beta, beta_lo = F.beta_lo;
   const cf ik = {F.ik[0], F.ik[1]};      // i / k~
-  const cf kt4 = {F.kt4[0], F.kt4[1]};   // i k~ / 4
-  const float ampk = F.ampk;             // sqrt(2 / (pi k))
-  const float kk2h2 = F.kk2h2;
-  cf v[4][4];
+  cf vS[4], vD[4], vDt[4], vNb[4], vNd = {0.f, 0.f};
 #pragma unroll
-  for (int op = 0; op < 4; ++op)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[op][j] = {0.f, 0.f};
+  for (int j = 0; j < 4; ++j) vS[j] = vD[j] = vDt[j] = vNb[j] = cf{0.f, 0.f};
   for (int p = 0; p < q; ++p) {
     const int64_t ip = e * q + p;
-    const float oxp = A.ox[ip], oyp = A.oy[ip], nxt = A.nxf[ip], nyt = A.nyf[ip];
-    const float xip = c_xff[p], wp = c_wff[p];
+    const float oxp = A.ox[ip], oyp = A.oy[ip], oxlp = A.oxl[ip], oylp = A.oyl[ip];
+    const float nxt = A.nxf[ip], nyt = A.nyf[ip], nxtl = A.nxl[ip], nytl = A.nyl[ip];
+    cf uS[2], uD[2], uDt[2], uNb[2], uNd = {0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 2; ++b) uS[b] = uD[b] = uDt[b] = uNb[b] = cf{0.f, 0.f};
     for (int r = 0; r < q; ++r) {
       const int64_t ir = f * q + r;
-      const float dx = oxp - A.ox[ir], dy = oyp - A.oy[ir];
-      const float nxs = A.nxf[ir], nys = A.nyf[ir];
-      const float a = 2.f * (fdx0 * dx + fdy0 * dy) + dx * dx + dy * dy;
+      // D = o_p - o_r in float-float (the offsets' tails included)
+      ff Dx = ff_two_sum(oxp, -A.ox[ir]), Dy = ff_two_sum(oyp, -A.oy[ir]);
+      Dx = ff_quick(Dx.hi, Dx.lo + (oxlp - A.oxl[ir]));
+      Dy = ff_quick(Dy.hi, Dy.lo + (oylp - A.oyl[ir]));
+      const float nxs = A.nxf[ir], nys = A.nyf[ir], nxsl = A.nxl[ir], nysl = A.nyl[ir];
+      const float a = 2.f * (fdx0 * Dx.hi + fdy0 * Dy.hi) + Dx.hi * Dx.hi + Dy.hi * Dy.hi;
       const float R = sqrtf(fR0 * fR0 + a);
       const float iR = 1.f / R;
-      const float nd = nxt * nxs + nyt * nys;
+      // n . n' with the normals' tails (a rounded normal would repeat in every pair of its point)
+      const float nd = fmaf(nxt, nxs, nyt * nys) + (fmaf(nxtl, nxs, nxt * nxsl) + fmaf(nytl, nys, nyt * nysl));
       // phase k R - pi/4 = ph0 + k (R - R0) in float-float: R - R0 = a / (2 R0 + (R - R0))
-      // with a = 2 d0.D + |D|^2 (D = o_p - o_r) from error-free products; the
-      // denominator takes the FP32 estimate of R - R0, whose error enters only
-      // relative to 2 R0
-      const ff Dx = ff_two_sum(oxp, -A.ox[ir]), Dy = ff_two_sum(oyp, -A.oy[ir]);
+      // with a = 2 d0.D + |D|^2 from error-free products; the denominator
+      // takes the FP32 estimate of R - R0, whose error enters only relative to 2 R0
       // (r - r').n' in float-float: on the flat parts of a contour it cancels to
       // ~curvature R^2, far below the FP32 rounding of its terms (~6e-8 R)
       const ff rx = ff_add(ff{fdx0, ldx0}, Dx), ry = ff_add(ff{fdy0, ldy0}, Dy);
-      const ff dn = ff_add(ff_mul(rx, ff{nxs, A.nxl[ir]}), ff_mul(ry, ff{nys, A.nyl[ir]}));
+      const ff dn = ff_add(ff_mul(rx, ff{nxs, nxsl}), ff_mul(ry, ff{nys, nysl}));
       const float gg = (dn.hi + dn.lo) * iR;
       const ff a_ff = ff_add(ff_add(ff_add(ff_two_prod(2.f * Dx.hi, fdx0), ff_two_prod(2.f * Dy.hi, fdy0)),
                                     ff_add(ff_two_prod(Dx.hi, Dx.hi), ff_two_prod(Dy.hi, Dy.hi))),
@@ -316,9 +344,11 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
       const ff th = ff_add(ph0, ff_mul(kff, ff_quick(q0, rem.hi / den.hi)));
       float sn, cs;
       sincosf(th.hi, &sn, &cs);
-      const cf E = {fmaf(-sn, th.lo, cs), fmaf(cs, th.lo, sn)};   // e^{i(kR - pi/4)}
+      const float sq = sqrtf(iR);
+      // e^{i(kR - pi/4)} / sqrt(R)
+      const cf E1 = {fmaf(-sn, th.lo, cs) * sq, fmaf(cs, th.lo, sn) * sq};
       // real wavenumber: P + iQ = sum (i t)^k a_k, t = 1/(kR)
-      const float t = iR / k, t2 = t * t;
+      const float tt = iR / k, t2 = tt * tt;
       float P0 = c_a0[8], Q0 = c_a0[9], P1 = c_a1[8], Q1 = c_a1[9];
 #pragma unroll
       for (int m = 3; m >= 0; --m) {
@@ -327,14 +357,10 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
         P1 = fmaf(-t2, P1, c_a1[2 * m]);
         Q1 = fmaf(-t2, Q1, c_a1[2 * m + 1]);
       }
-      Q0 *= t;
-      Q1 *= t;
-      const float amp = ampk * sqrtf(iR);
-      const cf AE = cscale(E, amp);
-      const cf H0 = cmul(AE, {P0, Q0});
-      const cf H1 = cmul(AE, {Q1, -P1});                        // e^{-i pi/2} (P1 + i Q1)
-      const cf gk = {-0.25f * H0.y, 0.25f * H0.x};               // (i/4) H0
-      const cf dgk = cscale({-0.25f * H1.y, 0.25f * H1.x}, k * gg);
+      Q0 *= tt;
+      Q1 *= tt;
+      const cf H0 = cmul(E1, {P0, Q0});                         // H0(kR) / sqrt(2 / (pi k))
+      const cf H1g = cscale(cmul(E1, {Q1, -P1}), gg);           // H1(kR) gg / sqrt(2 / (pi k))
       // complex wavenumber: w = i/(k~ R)
       const cf w = cscale(ik, iR);
       cf s0 = {c_a0[9], 0.f}, s1 = {c_a1[9], 0.f};
@@ -343,40 +369,44 @@ __device__ void pair_fast_f(const AsmArgs& A, int64_t e, int64_t f, PairOutF& ou
         s0 = cmul(s0, w); s0.x += c_a0[m];
         s1 = cmul(s1, w); s1.x += c_a1[m];
       }
-      // expf, not the fast intrinsic: its error grows with |beta R| (up to ~12 here)
-      const cf Et = cscale(cmul(E, ck), sqrtf(iR) * expf(-beta * R));
-      const cf Ht0 = cmul(Et, s0);
-      const cf Ht1 = cmul(Et, {s1.y, -s1.x});
-      const cf gt = {-0.25f * Ht0.y, 0.25f * Ht0.x};
-      const cf dgt = cscale(cmul(kt4, Ht1), gg);
-      const float ph[2] = {1.f - xip, xip};
-      const float xir = c_xff[r];
-      const float ps[2] = {1.f - xir, xir};
-      const float w2 = wp * c_wff[r];
+      // exp(-Im k~ R); expf, not the fast intrinsic: its error grows with |beta R| (up to ~12 here)
+      const float damp = expf(-beta * R) * fmaf(-beta_lo, R, 1.f);
+      const cf Et = cscale(E1, damp);
+      const cf Ht0 = cmul(Et, s0);                              // H0(k~R) / sqrt(2 / (pi k~))
+      const cf Ht1g = cscale(cmul(Et, {s1.y, -s1.x}), gg);      // H1(k~R) gg / sqrt(2 / (pi k~))
+      const cf HN = cscale(H0, nd);
 #pragma unroll
-      for (int aa = 0; aa < 2; ++aa)
-#pragma unroll
-        for (int bb = 0; bb < 2; ++bb) {
-          const float c = w2 * ph[aa] * ps[bb];
-          const float cn = w2 * ((aa == bb) ? 1.f : -1.f) - kk2h2 * nd * c;
-          cf* o = &v[0][aa * 2 + bb];
-          v[0][aa * 2 + bb].x = fmaf(c, gt.x, v[0][aa * 2 + bb].x);
-          v[0][aa * 2 + bb].y = fmaf(c, gt.y, v[0][aa * 2 + bb].y);
-          v[1][aa * 2 + bb].x = fmaf(c, dgk.x, v[1][aa * 2 + bb].x);
-          v[1][aa * 2 + bb].y = fmaf(c, dgk.y, v[1][aa * 2 + bb].y);
-          v[2][aa * 2 + bb].x = fmaf(c, dgt.x, v[2][aa * 2 + bb].x);
-          v[2][aa * 2 + bb].y = fmaf(c, dgt.y, v[2][aa * 2 + bb].y);
-          v[3][aa * 2 + bb].x = fmaf(cn, gk.x, v[3][aa * 2 + bb].x);
-          v[3][aa * 2 + bb].y = fmaf(cn, gk.y, v[3][aa * 2 + bb].y);
-          (void)o;
-        }
+      for (int b = 0; b < 2; ++b) {
+        const float wh = c_fwt[b][r][0], wl = c_fwt[b][r][1];
+        cfma2(uS[b], wh, wl, Ht0);
+        cfma2(uD[b], wh, wl, H1g);
+        cfma2(uDt[b], wh, wl, Ht1g);
+        cfma2(uNb[b], wh, wl, HN);
+      }
+      cfma2(uNd, c_fw[r][0], c_fw[r][1], H0);
     }
+#pragma unroll
+    for (int aa = 0; aa < 2; ++aa) {
+      const float wh = c_fwt[aa][p][0], wl = c_fwt[aa][p][1];
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        cfma2(vS[aa * 2 + b], wh, wl, uS[b]);
+        cfma2(vD[aa * 2 + b], wh, wl, uD[b]);
+        cfma2(vDt[aa * 2 + b], wh, wl, uDt[b]);
+        cfma2(vNb[aa * 2 + b], wh, wl, uNb[b]);
+      }
+    }
+    cfma2(vNd, c_fw[p][0], c_fw[p][1], uNd);
   }
-  const float h2 = F.h2;
 #pragma unroll
-  for (int op = 0; op < 4; ++op)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) out.v[op][j] = (op < 3) ? cscale(v[op][j], h2) : v[op][j];
+  for (int j = 0; j < 4; ++j) {
+    out.v[0][j] = vS[j];
+    out.v[1][j] = vD[j];
+    out.v[2][j] = vDt[j];
+    out.v[3][j] = vNb[j];
+    // derivative part of the Maue form: phi_a' phi_b' h^2 = s_a s_b, + on the diagonal of the 2x2 block
+    out.v[4][j] = (j == 0 || j == 3) ? vNd : cf{-vNd.x, -vNd.y};
+  }
 }
 
 __device__ __forceinline__ bool fast_ok(const AsmArgs& A, int64_t e, int64_t f) {
@@ -546,10 +576,20 @@ static int upload_rules(const AsmArgs& A) {
   if (cudaMemcpyToSymbol(c_wf, wf, sizeof(double) * A.q_far) != cudaSuccess) return 3;
   if (cudaMemcpyToSymbol(c_xn, xn, sizeof(double) * A.q_near) != cudaSuccess) return 3;
   if (cudaMemcpyToSymbol(c_wn, wn, sizeof(double) * A.q_near) != cudaSuccess) return 3;
-  float xff[16], wff[16];
-  for (int i = 0; i < A.q_far; ++i) { xff[i] = (float)xf[i]; wff[i] = (float)wf[i]; }
-  if (cudaMemcpyToSymbol(c_xff, xff, sizeof(float) * A.q_far) != cudaSuccess) return 3;
-  if (cudaMemcpyToSymbol(c_wff, wff, sizeof(float) * A.q_far) != cudaSuccess) return 3;
+  // float-float weights of the FP32 far path: w_r phi_b(xi_r) and w_r
+  float fwt[2][16][2], fw[16][2];
+  std::memset(fwt, 0, sizeof(fwt));
+  std::memset(fw, 0, sizeof(fw));
+  for (int i = 0; i < A.q_far; ++i) {
+    const double v[3] = {wf[i] * (1.0 - xf[i]), wf[i] * xf[i], wf[i]};
+    float* dst[3] = {fwt[0][i], fwt[1][i], fw[i]};
+    for (int t = 0; t < 3; ++t) {
+      dst[t][0] = (float)v[t];
+      dst[t][1] = (float)(v[t] - (double)dst[t][0]);
+    }
+  }
+  if (cudaMemcpyToSymbol(c_fwt, fwt, sizeof(fwt)) != cudaSuccess) return 3;
+  if (cudaMemcpyToSymbol(c_fw, fw, sizeof(fw)) != cudaSuccess) return 3;
   return 0;
 }
 
@@ -627,15 +667,17 @@ __global__ void k_tile_flags(AsmArgs A, int64_t nt, uint8_t* flag) {
   if (threadIdx.x == 0) flag[t] = (uint8_t)any;
 }
 
-// Tiles whose element pairs all take the FP32 path: FP32 accumulation in
-// shared memory, same four conflict-free phases, planes written directly.
+// Tiles whose element pairs all take the FP32 path: the reduced sums of
+// pair_fast_f accumulated per node pair in shared memory (FP32, four
+// conflict-free phases), then scaled by their FP64 factors, combined (N) and
+// written as split-bf16 planes.
 __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_t nt, const uint8_t* flag) {
   const int64_t ti = blockIdx.y, tj = blockIdx.x;
   if (flag[ti * nt + tj]) return;
-  __shared__ cf acc[4 * TILE * TILE];
+  __shared__ cf acc[5 * TILE * TILE];
   const int64_t N = A.N;
   const int64_t i0 = ti * TILE, j0 = tj * TILE;
-  for (int t = threadIdx.x; t < 4 * TILE * TILE; t += blockDim.x) acc[t] = {0.f, 0.f};
+  for (int t = threadIdx.x; t < 5 * TILE * TILE; t += blockDim.x) acc[t] = {0.f, 0.f};
   __syncthreads();
   const int span = TILE + 1;
   const int npairs = span * span;
@@ -658,23 +700,27 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_
         const int li = el - 1 + a, lj = fl - 1 + b;
         if (li >= 0 && li < TILE && lj >= 0 && lj < TILE && i0 + li < N && j0 + lj < N) {
 #pragma unroll
-          for (int op = 0; op < 4; ++op) {
-            cf& d = acc[(op * TILE + li) * TILE + lj];
-            d.x += o.v[op][ph].x;
-            d.y += o.v[op][ph].y;
-          }
+          for (int op = 0; op < 5; ++op) cadd(acc[(op * TILE + li) * TILE + lj], o.v[op][ph]);
         }
       }
       __syncthreads();
     }
   }
+  // entry (li, lj) of operator op in FP64
+  auto entry = [&](int op, int li, int lj) -> zd {
+    const int t = li * TILE + lj;
+    if (op == 0) return A.fS * zf2d(acc[t]);
+    if (op == 1) return A.fD * zf2d(acc[TILE * TILE + t]);
+    if (op == 2) return A.fDt * zf2d(acc[2 * TILE * TILE + t]);
+    return A.fN * (zf2d(acc[4 * TILE * TILE + t]) - A.kk2h2 * zf2d(acc[3 * TILE * TILE + t]));
+  };
   for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
     const int comp = t & 1, u = t >> 1;
     const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
     const int li = rem / TILE, lj = rem - (rem / TILE) * TILE;
     if (i0 + li < N && j0 + lj < N) {
-      const cf v = acc[(op * TILE + li) * TILE + lj];
-      split_store_f(comp ? v.y : v.x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
+      const zd v = entry(op, li, lj);
+      split_store(comp ? v.y : v.x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
     }
   }
   for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
@@ -682,8 +728,8 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_
     const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
     const int lj = rem / TILE, li = rem - (rem / TILE) * TILE;
     if (i0 + li < N && j0 + lj < N) {
-      const cf v = acc[(op * TILE + li) * TILE + lj];
-      split_store_f(comp ? v.y : v.x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
+      const zd v = entry(op, li, lj);
+      split_store(comp ? v.y : v.x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
     }
   }
 }
@@ -712,12 +758,15 @@ int assemble_planes(const AsmArgs& A, cudaStream_t s) {
 }
 
 __global__ void k_far_offsets(Points far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                              float* oy, float* nxf, float* nyf, float* nxl, float* nyl) {
+                              float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float* oxl, float* oyl) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= N * q) return;
   const int64_t e = t / q;
-  ox[t] = (float)(far.x[t] - cx[e]);
-  oy[t] = (float)(far.y[t] - cy[e]);
+  const double dxo = far.x[t] - cx[e], dyo = far.y[t] - cy[e];
+  ox[t] = (float)dxo;
+  oy[t] = (float)dyo;
+  oxl[t] = (float)(dxo - (double)ox[t]);   // float-float tails of the offsets
+  oyl[t] = (float)(dyo - (double)oy[t]);
   nxf[t] = (float)far.nx[t];
   nyf[t] = (float)far.ny[t];
   nxl[t] = (float)(far.nx[t] - (double)nxf[t]);   // float-float tails of the normals
@@ -732,8 +781,10 @@ __global__ void k_centres_ff(const double* cx, const double* cy, int64_t N, floa
 }
 
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float4* cff, cudaStream_t s) {
-  k_far_offsets<<<(unsigned)((N * q + 255) / 256), 256, 0, s>>>(far, cx, cy, N, q, ox, oy, nxf, nyf, nxl, nyl);
+                float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float* oxl, float* oyl, float4* cff,
+                cudaStream_t s) {
+  k_far_offsets<<<(unsigned)((N * q + 255) / 256), 256, 0, s>>>(far, cx, cy, N, q, ox, oy, nxf, nyf, nxl, nyl,
+                                                                oxl, oyl);
   note_launch();
   k_centres_ff<<<(unsigned)((N + 255) / 256), 256, 0, s>>>(cx, cy, N, cff);
   note_launch();

@@ -175,11 +175,12 @@ static int launch_tile(const zd* in, int64_t in_es, int64_t in_ss, int64_t in_cs
   if (nseq > 16) nseq = 16;
   if (in_ss != 1 && out_ss != 1) nseq = 1;
   size_t smem = sizeof(zd) * nseq * L;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_fft_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)(sizeof(zd) * FFT_SMEM_MAX));
-    attr = true;
+  static DeviceOnce attr;
+  if (attr.need()) {
+    cudaError_t e = cudaFuncSetAttribute(k_fft_tile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(zd) * FFT_SMEM_MAX));
+    if (e != cudaSuccess) { set_error(std::string("fft: shared-memory opt-in: ") + cudaGetErrorString(e)); return 3; }
+    attr.done();
   }
   int threads = (int)std::min<int64_t>(512, std::max<int64_t>(32, nseq * L / 2));
   for (int64_t c0 = 0; c0 < cols; c0 += 65535) {

@@ -364,10 +364,11 @@ static int launch_tc(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaS
   for (int p = PA; p < 3; ++p) ma[p] = ma[0];
   for (int p = PB; p < 3; ++p) mb[p] = mb[0];
   auto kern = k_gemm_tc<NT, PA, PB, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
-    attr = true;
+  static DeviceOnce attr;   // one instance per template instantiation
+  if (attr.need()) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e != cudaSuccess) { set_error(std::string("gemm_tc: shared-memory opt-in: ") + cudaGetErrorString(e)); return 3; }
+    attr.done();
   }
   const int nk = (args.K + TC_BK - 1) / TC_BK;
   const int splits = (args.kper > 0) ? (nk + args.kper - 1) / args.kper : 1;
@@ -620,10 +621,11 @@ static int launch_tc_acc(const TcOperand& A, const TcOperand& B, TcArgs& args, c
   for (int p = PA; p < 3; ++p) ma[p] = ma[0];
   for (int p = PB; p < 3; ++p) mb[p] = mb[0];
   auto kern = k_gemm_tc_acc<PA, PB, STAGES>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
-    attr = true;
+  static DeviceOnce attr;   // one instance per template instantiation
+  if (attr.need()) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e != cudaSuccess) { set_error(std::string("gemm_tc: shared-memory opt-in: ") + cudaGetErrorString(e)); return 3; }
+    attr.done();
   }
   dim3 grid((unsigned)((args.Nc + ACC_NT - 1) / ACC_NT), (unsigned)((args.M + TC_BM - 1) / TC_BM));
   kern<<<grid, ACC_THREADS, L::TOTAL, s>>>(ma[0], ma[1], ma[2], mb[0], mb[1], mb[2], args);

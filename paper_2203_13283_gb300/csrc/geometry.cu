@@ -195,15 +195,15 @@ __global__ void k_min_curv(Contour c, const double* cum, int P, double L, int64_
   if (threadIdx.x == 0) kmin[blockIdx.x] = red[0];
 }
 
-static bool g_gl16_ready = false;
+static DeviceOnce g_gl16_ready;   // __constant__ tables are per device
 
 static int ensure_gl16() {
-  if (g_gl16_ready) return 0;
+  if (!g_gl16_ready.need()) return 0;
   double x[16], w[16];
   gauss_legendre01(16, x, w);
   if (cudaMemcpyToSymbol(c_gl16x, x, sizeof(x)) != cudaSuccess) return 1;
   if (cudaMemcpyToSymbol(c_gl16w, w, sizeof(w)) != cudaSuccess) return 1;
-  g_gl16_ready = true;
+  g_gl16_ready.done();
   return 0;
 }
 

@@ -10,6 +10,27 @@
 
 namespace wcs {
 
+// A one-time set-up step per CUDA device.  Kernel attributes (the opt-in to
+// more than 48 KB of dynamic shared memory) and __constant__ tables belong to
+// a device, so a process that uses several devices repeats the step on each.
+// need() is true until done() has been called with that device current;
+// device indices >= 64 are not remembered (the step then runs every time).
+struct DeviceOnce {
+  bool flag[64] = {};
+  static int device() {
+    int d = -1;
+    return (cudaGetDevice(&d) == cudaSuccess) ? d : -1;
+  }
+  bool need() const {
+    const int d = device();
+    return d < 0 || d >= 64 || !flag[d];
+  }
+  void done() {
+    const int d = device();
+    if (d >= 0 && d < 64) flag[d] = true;
+  }
+};
+
 // ---------------------------------------------------------------- geometry
 enum ContourFamily { FAM_CIRCLE = 0, FAM_ELLIPSE = 1, FAM_SUPERELLIPSE = 2, FAM_FOURIER = 3 };
 constexpr int kMaxFourier = 64;
@@ -68,6 +89,7 @@ struct FastConsts {
   float kt4[2] = {0.f, 0.f};       // i k~ / 4
   float ampk = 0.f;                // sqrt(2 / (pi k))
   float kk2h2 = 0.f, h2 = 0.f;     // k^2 h^2, h^2
+  float beta_lo = 0.f;             // Im k~ - beta (float-float tail)
   float zfast2 = 0.f;              // zfast^2 (pair test k^2 |c_e - c_f|^2 >= zfast^2)
   float k_hi = 0.f, k_lo = 0.f;    // k as a float-float pair
   float twopi[3] = {0.f, 0.f, 0.f};   // 2 pi = twopi[0] + twopi[1] + twopi[2]
@@ -96,6 +118,11 @@ struct AsmArgs {
   const float *ox = nullptr, *oy = nullptr;      // far points minus their element centre
   const float *nxf = nullptr, *nyf = nullptr;    // far-point normals (FP32)
   const float *nxl = nullptr, *nyl = nullptr;    // their float-float tails
+  const float *oxl = nullptr, *oyl = nullptr;    // float-float tails of the offsets
+  // FP64 factors of the FP32 far-pair path, applied once per stored entry (a
+  // constant rounded to FP32 would bias every far entry of an operator alike)
+  zd fS, fD, fDt, fN;              // S~, D, D~, N (see pair_fast_f)
+  double kk2h2 = 0.0;              // k^2 h^2 of the Maue form
   const float4* cff = nullptr;                   // element centres as float-float (x hi, x lo, y hi, y lo)
   double zfast = 1e300;
   FastConsts fk;
@@ -106,7 +133,8 @@ int assemble_dense(const AsmArgs& a, cudaStream_t s);
 int assemble_planes(const AsmArgs& a, cudaStream_t s);
 // FP32 offset tables of the far points relative to element centres.
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
-                float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float4* cff, cudaStream_t s);
+                float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float* oxl, float* oyl, float4* cff,
+                cudaStream_t s);
 // First row of the four circulant operators on the circle (row 0, N entries each).
 int assemble_circle_row(const AsmArgs& a, cudaStream_t s);
 // Sampled entries (row, col) of the four operators, computed point-wise.
@@ -144,8 +172,9 @@ struct ZView {
 int zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A, ZView B, zd beta, zd* C, int64_t ldc,
           cudaStream_t s);
 // Y = G^{-1} X for the cyclic Gram matrix of hats (h/6 [1 4 1]), column-major; may alias.
+// work: caller-owned device scratch of n * cols complex values.
 int gram_inverse(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
-                 cudaStream_t s);
+                 zd* work, cudaStream_t s);
 // Y = alpha * G X + beta * Y (cyclic tridiagonal), column-major.
 int gram_apply(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
                double alpha, double beta, cudaStream_t s);

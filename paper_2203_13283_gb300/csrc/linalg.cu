@@ -11,25 +11,32 @@ namespace wcs {
 // =========================================================================== ZGEMM (FP64 FMA pipe)
 // C (m x n, column-major) = alpha * A * B + beta * C; A (m x k), B (k x n) are
 // strided views (element (i, j) at p[i*rs + j*cs], optionally conjugated).
-constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
+// 256 threads as a TY x TX grid, each computing TM x TN outputs: tiles of
+// (TY TM) x (TX TN).  The FP64 pipe is the bound (GB300 issues ~2 DFMA per
+// clock per SM), so the tile width follows n: a block of a few right-hand
+// sides must not pay for 64 columns of zeros.
+constexpr int GB_K = 16;
 
+template <int TY, int TX, int TM, int TN>
 __global__ void __launch_bounds__(256) k_zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
                                                ZView B, zd beta, zd* __restrict__ C, int64_t ldc) {
-  __shared__ zd As[GB_K][GB_M + 1];
-  __shared__ zd Bs[GB_K][GB_N + 1];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int64_t m0 = (int64_t)blockIdx.y * GB_M, n0 = (int64_t)blockIdx.x * GB_N;
-  zd acc[4][4];
+  static_assert(TY * TX == 256, "256 threads");
+  constexpr int BM = TY * TM, BN = TX * TN;
+  __shared__ zd As[GB_K][BM + 1];
+  __shared__ zd Bs[GB_K][BN + 1];
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+  zd acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = mkz(0.0);
+    for (int j = 0; j < TN; ++j) acc[i][j] = mkz(0.0);
   const bool a_kfast = (A.cs == 1);  // walk k first when it is the contiguous index
   const bool b_kfast = (B.rs == 1);
   for (int64_t k0 = 0; k0 < k; k0 += GB_K) {
-    for (int u = threadIdx.x; u < GB_M * GB_K; u += 256) {
+    for (int u = threadIdx.x; u < BM * GB_K; u += 256) {
       int ii, kk;
-      if (a_kfast) { kk = u % GB_K; ii = u / GB_K; } else { ii = u % GB_M; kk = u / GB_M; }
+      if (a_kfast) { kk = u % GB_K; ii = u / GB_K; } else { ii = u % BM; kk = u / BM; }
       const int64_t gi = m0 + ii, gk = k0 + kk;
       zd v = mkz(0.0);
       if (gi < m && gk < k) {
@@ -38,9 +45,9 @@ __global__ void __launch_bounds__(256) k_zgemm(int64_t m, int64_t n, int64_t k, 
       }
       As[kk][ii] = v;
     }
-    for (int u = threadIdx.x; u < GB_N * GB_K; u += 256) {
+    for (int u = threadIdx.x; u < BN * GB_K; u += 256) {
       int jj, kk;
-      if (b_kfast) { kk = u % GB_K; jj = u / GB_K; } else { jj = u % GB_N; kk = u / GB_N; }
+      if (b_kfast) { kk = u % GB_K; jj = u / GB_K; } else { jj = u % BN; kk = u / BN; }
       const int64_t gj = n0 + jj, gk = k0 + kk;
       zd v = mkz(0.0);
       if (gj < n && gk < k) {
@@ -52,24 +59,24 @@ __global__ void __launch_bounds__(256) k_zgemm(int64_t m, int64_t n, int64_t k, 
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < GB_K; ++kk) {
-      zd a[4], b[4];
+      zd a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx + TX * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) zfma(acc[i][j], a[i], b[j]);
+        for (int j = 0; j < TN; ++j) zfma(acc[i][j], a[i], b[j]);
     }
     __syncthreads();
   }
   const bool beta0 = (beta.x == 0.0 && beta.y == 0.0);
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int64_t gi = m0 + ty + 16 * i, gj = n0 + tx + 16 * j;
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gi = m0 + ty + TY * i, gj = n0 + tx + TX * j;
       if (gi < m && gj < n) {
         zd r = alpha * acc[i][j];
         if (!beta0) r += beta * C[gj * ldc + gi];
@@ -78,13 +85,26 @@ __global__ void __launch_bounds__(256) k_zgemm(int64_t m, int64_t n, int64_t k, 
     }
 }
 
+template <int TY, int TX, int TM, int TN>
+static int launch_zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A, ZView B, zd beta, zd* C, int64_t ldc,
+                        cudaStream_t s) {
+  constexpr int BM = TY * TM, BN = TX * TN;
+  dim3 grid((unsigned)((n + BN - 1) / BN), (unsigned)((m + BM - 1) / BM));
+  if (grid.y > 65535) { set_error("zgemm: m too large"); return 1; }
+  k_zgemm<TY, TX, TM, TN><<<grid, 256, 0, s>>>(m, n, k, alpha, A, B, beta, C, ldc);
+  note_launch();
+  return 0;
+}
+
 int zgemm(int64_t m, int64_t n, int64_t k, zd alpha, ZView A, ZView B, zd beta, zd* C, int64_t ldc,
           cudaStream_t s) {
   if (m <= 0 || n <= 0) return 0;
-  dim3 grid((unsigned)((n + GB_N - 1) / GB_N), (unsigned)((m + GB_M - 1) / GB_M));
-  if (grid.y > 65535) { set_error("zgemm: m too large"); return 1; }
-  k_zgemm<<<grid, 256, 0, s>>>(m, n, k, alpha, A, B, beta, C, ldc);
-  note_launch();
+  int r;
+  if (n <= 8) r = launch_zgemm<32, 8, 4, 1>(m, n, k, alpha, A, B, beta, C, ldc, s);          // 128 x 8 tiles
+  else if (n <= 16) r = launch_zgemm<16, 16, 4, 1>(m, n, k, alpha, A, B, beta, C, ldc, s);   // 64 x 16
+  else if (n <= 32) r = launch_zgemm<16, 16, 4, 2>(m, n, k, alpha, A, B, beta, C, ldc, s);   // 64 x 32
+  else r = launch_zgemm<16, 16, 4, 4>(m, n, k, alpha, A, B, beta, C, ldc, s);                // 64 x 64
+  if (r) return r;
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("zgemm: ") + cudaGetErrorString(err)); return 3; }
   return 0;
@@ -135,26 +155,16 @@ __global__ void k_gram_bwd(const zd* __restrict__ U, zd* __restrict__ Y, int64_t
   }
 }
 
-static zd* g_gram_work = nullptr;
-static size_t g_gram_work_bytes = 0;
-
 int gram_inverse(const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t n, int64_t cols, double h,
-                 cudaStream_t s) {
+                 zd* work, cudaStream_t s) {
   if (cols <= 0) return 0;
-  const size_t need = sizeof(zd) * n * cols;
-  if (need > g_gram_work_bytes) {
-    cudaFree(g_gram_work);
-    g_gram_work = nullptr;
-    g_gram_work_bytes = 0;
-    if (cudaMalloc(&g_gram_work, need) != cudaSuccess) { set_error("oom (gram)"); return 4; }
-    g_gram_work_bytes = need;
-  }
+  if (!work) { set_error("gram: no work buffer"); return 1; }
   const double rho = sqrt(3.0) - 2.0;
   const int64_t tasks = ((n + GI_CH - 1) / GI_CH) * cols;
   const unsigned blocks = (unsigned)((tasks + 127) / 128);
-  k_gram_fwd<<<blocks, 128, 0, s>>>(X, ldx, g_gram_work, n, cols, rho);
+  k_gram_fwd<<<blocks, 128, 0, s>>>(X, ldx, work, n, cols, rho);
   note_launch();
-  k_gram_bwd<<<blocks, 128, 0, s>>>(g_gram_work, Y, ldy, n, cols, rho, -rho * 6.0 / h);
+  k_gram_bwd<<<blocks, 128, 0, s>>>(work, Y, ldy, n, cols, rho, -rho * 6.0 / h);
   note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("gram: ") + cudaGetErrorString(err)); return 3; }

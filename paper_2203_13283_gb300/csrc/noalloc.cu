@@ -49,12 +49,20 @@ using namespace wcs;
 extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda,
                                            const double* B, int64_t ldb, int planes, double* D, int64_t ldd,
                                            void* stream) {
-  if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (!A || lda < K)) ||
-      (Nc > 0 && (!B || ldb < K)) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
+  if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (lda < K || (K > 0 && !A))) ||
+      (Nc > 0 && (ldb < K || (K > 0 && !B))) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
     set_error("bad argument");
     return WCS_ERR_ARG;
   }
   if (M == 0 || Nc == 0) return WCS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (K == 0) {   // an empty contraction: D = 0
+    e = cudaMemset2DAsync(D, sizeof(double) * ldd, 0, sizeof(double) * Nc, M, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+    return WCS_OK;
+  }
   const int64_t ldp = ((K + 63) / 64) * 64;
   const size_t bytesA = sizeof(uint16_t) * (size_t)ldp * M * planes;
   const size_t bytesB = sizeof(uint16_t) * (size_t)ldp * Nc * planes;
@@ -73,7 +81,6 @@ extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, con
   void* base = nullptr;
   int r = noalloc_setup(&base);
   if (r) return r;
-  cudaStream_t s = (cudaStream_t)stream;
   unsigned char* p = (unsigned char*)base;
   uint16_t* pa = (uint16_t*)p;
   uint16_t* pb = (uint16_t*)(p + offB);
@@ -81,9 +88,10 @@ extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, con
   float* ws = (float*)(p + offW);
   // the array keeps the previous call's contents: clear the planes (their
   // K padding must read as zero) and the error flag
-  cudaMemsetAsync(pa, 0, bytesA, s);
-  cudaMemsetAsync(pb, 0, bytesB, s);
-  cudaMemsetAsync(err, 0, sizeof(int), s);
+  e = cudaMemsetAsync(pa, 0, bytesA, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pb, 0, bytesB, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) { set_error(std::string("gemm: clearing the scratch: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
   uint16_t* PA[3];
   uint16_t* PB[3];
   for (int q = 0; q < 3; ++q) {
@@ -106,8 +114,8 @@ extern "C" int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, con
   if (ws_elems > 0) { t.ws = ws; t.ws_elems = ws_elems; }
   if ((r = gemm_tc(oa, ob, t, s))) return r;
   int errh = 0;
-  cudaMemcpyAsync(&errh, err, sizeof(int), cudaMemcpyDeviceToHost, s);
-  cudaError_t e = cudaStreamSynchronize(s);
+  e = cudaMemcpyAsync(&errh, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
   if (errh) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
   return WCS_OK;

@@ -77,6 +77,7 @@ struct wcs_ctx {
   DevBuf U, Vw, Wt;                       // N x rank each
   DevBuf w1, w2, w3, w4, w5;              // N x chunk scratch
   DevBuf small;                           // small scratch
+  DevBuf gwork;                           // work of the Gram inverse (N x cols)
   // mixed-precision form
   bool mixed = false;
   int planes = 2, rhs_planes = 2;
@@ -142,6 +143,13 @@ static ZView blkH(const zd* X, int64_t ld) { return ZView{X, ld, 1, true}; }
     int _r = (x);           \
     if (_r) return _r;      \
   } while (0)
+
+// Y = G^{-1} X (cyclic Gram matrix) with the context's own work buffer.
+static int ginv(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols) {
+  if (cols <= 0) return 0;
+  TRY(c->gwork.ensure(sizeof(zd) * c->N * cols));
+  return gram_inverse(X, ldx, Y, ldy, c->N, cols, c->h, c->gwork.z(), c->s);
+}
 
 static int ensure_work(wcs_ctx* c, int64_t cols) {
   size_t b = sizeof(zd) * c->N * std::max<int64_t>(cols, 1);
@@ -347,8 +355,8 @@ static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ld
     TRY(tc_apply(c, 0, true, c->stage0, cols, one, zero, T2, N, acc));     // S~^H X
   }
   TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
-  TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
-  TRY(gram_inverse(T2, N, T2, N, N, cols, c->h, c->s));
+  TRY(ginv(c, T1, N, T1, N, cols));
+  TRY(ginv(c, T2, N, T2, N, cols));
   TRY(stage(c, c->stage1, T1, N, cols, cj));
   TRY(stage(c, c->stage2, T2, N, cols, cj));
   if (!adj) {
@@ -375,8 +383,8 @@ static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int
     TRY(zgemm(N, cols, N, mone, op_view(c->D, c->ld, false), blk(X, ldx), zero, T1, N, c->s));
     TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
     TRY(zgemm(N, cols, N, one, op_view(c->Nk, c->ld, false), blk(X, ldx), zero, T2, N, c->s));
-    TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
-    TRY(gram_inverse(T2, N, T2, N, N, cols, c->h, c->s));
+    TRY(ginv(c, T1, N, T1, N, cols));
+    TRY(ginv(c, T2, N, T2, N, cols));
     // Y = (G/2 + D~) T1 + S~ T2
     TRY(zgemm(N, cols, N, one, op_view(c->Dt, c->ld, false), blk(T1, N), zero, Y, ldy, c->s));
     TRY(zgemm(N, cols, N, one, op_view(c->S, c->ld, false), blk(T2, N), one, Y, ldy, c->s));
@@ -386,8 +394,8 @@ static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int
     TRY(zgemm(N, cols, N, one, op_view(c->Dt, c->ld, true), blk(X, ldx), zero, T1, N, c->s));
     TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
     TRY(zgemm(N, cols, N, one, op_view(c->S, c->ld, true), blk(X, ldx), zero, T2, N, c->s));
-    TRY(gram_inverse(T1, N, T1, N, N, cols, c->h, c->s));
-    TRY(gram_inverse(T2, N, T2, N, N, cols, c->h, c->s));
+    TRY(ginv(c, T1, N, T1, N, cols));
+    TRY(ginv(c, T2, N, T2, N, cols));
     TRY(zgemm(N, cols, N, mone, op_view(c->D, c->ld, true), blk(T1, N), zero, Y, ldy, c->s));
     TRY(zgemm(N, cols, N, one, op_view(c->Nk, c->ld, true), blk(T2, N), one, Y, ldy, c->s));
     TRY(gram_apply(T1, N, Y, ldy, N, cols, c->h, 0.5, 1.0, c->s));
@@ -694,7 +702,7 @@ int wcs_destroy(wcs_ctx* c) {
   free_mesh(c);
   c->xf.release(); c->xn.release(); c->wn.release(); c->wlog.release();
   c->w1.release(); c->w2.release(); c->w3.release(); c->w4.release(); c->w5.release();
-  c->small.release(); c->tcerr.release();
+  c->small.release(); c->tcerr.release(); c->gwork.release();
   delete c;
   return WCS_OK;
 }
@@ -853,6 +861,7 @@ static void set_fast_consts(AsmArgs& A) {
   FastConsts& F = A.fk;
   F.kf = (float)A.k;
   F.beta = (float)A.kt.y;
+  F.beta_lo = (float)(A.kt.y - (double)F.beta);
   F.ck[0] = (float)ck.real(); F.ck[1] = (float)ck.imag();
   F.ik[0] = (float)ik.real(); F.ik[1] = (float)ik.imag();
   F.kt4[0] = (float)kt4.real(); F.kt4[1] = (float)kt4.imag();
@@ -862,6 +871,15 @@ static void set_fast_consts(AsmArgs& A) {
   F.zfast2 = (A.zfast < 1e18) ? (float)(A.zfast * A.zfast) : INFINITY;
   F.k_hi = (float)A.k;
   F.k_lo = (float)(A.k - (double)F.k_hi);
+  // FP64 factors of the reduced FP32 sums (see pair_fast_f)
+  const std::complex<double> I4(0.0, 0.25);
+  const double ampk = std::sqrt(2.0 / (WCS_PI * A.k)), h2 = A.h * A.h;
+  const std::complex<double> fS = I4 * ck * h2, fD = I4 * ampk * A.k * h2, fDt = I4 * kt * ck * h2, fN = I4 * ampk;
+  A.fS = mkz(fS.real(), fS.imag());
+  A.fD = mkz(fD.real(), fD.imag());
+  A.fDt = mkz(fDt.real(), fDt.imag());
+  A.fN = mkz(fN.real(), fN.imag());
+  A.kk2h2 = A.k * A.k * h2;
   const double tp = 2.0 * WCS_PI;   // 2 pi to ~72 bits: double plus its float-float residual
   const double tp_lo = 2.4492935982947064e-16;
   F.twopi[0] = (float)tp;
@@ -922,12 +940,12 @@ int wcs_assemble(wcs_ctx* c) {
     Points cp;
     cp.x = c->centres.d(); cp.y = cp.x + N; cp.nx = cp.y + N; cp.ny = cp.nx + N; cp.kappa = nullptr; cp.n = N;
     TRY(points_build(c->contour, c->arc, N, c->h, half, 1, cp, c->s));
-    const int64_t cff_off = ((6 * N * qf + 3) / 4) * 4;   // floats; float4 table 16-byte aligned
+    const int64_t cff_off = ((8 * N * qf + 3) / 4) * 4;   // floats; float4 table 16-byte aligned
     TRY(c->offs.ensure(sizeof(float) * cff_off + sizeof(float4) * N));
     float* of = (float*)c->offs.p;
     float4* cff = (float4*)(of + cff_off);
     TRY(far_offsets(c->far, cp.x, cp.y, N, qf, of, of + N * qf, of + 2 * N * qf, of + 3 * N * qf, of + 4 * N * qf,
-                    of + 5 * N * qf, cff, c->s));
+                    of + 5 * N * qf, of + 6 * N * qf, of + 7 * N * qf, cff, c->s));
     AsmArgs A = asm_args(c, false);
     A.mixed = 1;
     A.planes = c->planes;
@@ -938,6 +956,7 @@ int wcs_assemble(wcs_ctx* c) {
     A.cx = cp.x; A.cy = cp.y;
     A.ox = of; A.oy = of + N * qf; A.nxf = of + 2 * N * qf; A.nyf = of + 3 * N * qf;
     A.nxl = of + 4 * N * qf; A.nyl = of + 5 * N * qf;
+    A.oxl = of + 6 * N * qf; A.oyl = of + 7 * N * qf;
     A.cff = cff;
     // zfast <= 0: every pair in FP64 (the FP32 path is off)
     A.zfast = (c->opt.zfast > 0.0) ? c->opt.zfast + 2.0 * c->k * c->h : 1e300;
@@ -1006,6 +1025,16 @@ int wcs_circulant_eigs(wcs_ctx* c, int op, double* out) {
   return WCS_OK;
 }
 
+// Plane-wave angles are host arrays: reject non-finite ones before any work.
+static int check_angles(int64_t B, const double* a, const char* what) {
+  for (int64_t i = 0; i < B; ++i)
+    if (!std::isfinite(a[i])) {
+      set_error(std::string(what) + ": angle " + std::to_string(i) + " is not finite");
+      return WCS_ERR_ARG;
+    }
+  return 0;
+}
+
 static int check_block(wcs_ctx* c, int64_t B, const void* p, int64_t ld) {
   if (B < 0 || (B > 0 && (!p || ld < c->N))) { set_error("bad block argument (pointer or ld < N)"); return WCS_ERR_ARG; }
   return 0;
@@ -1051,6 +1080,7 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
         TRY(zgemm(N, cc, N, mkz(1.0), op_view(c->Nk, c->ld, false), blk(xc, ldx), mkz(0.0), yc, ldy, c->s));
         break;
       case WCS_OP_G: TRY(gram_apply(xc, ldx, yc, ldy, N, cc, c->h, 1.0, 0.0, c->s)); break;
+      case WCS_OP_GINV: TRY(ginv(c, xc, ldx, yc, ldy, cc)); break;
       case WCS_OP_SKEL: {
         if (c->stage < ST_SKELETON) { set_error("skeleton first"); return WCS_ERR_STATE; }
         const int64_t r = std::max(c->rank, 0);
@@ -1292,9 +1322,16 @@ int wcs_factor(wcs_ctx* c) {
 }
 
 // ---------------------------------------------------------------- checkpoint
-// Binary file: header, then U, V_w and W~ (N x rank complex FP64 each, column
-// by column).  The operators are not stored: loading re-runs the mesh and
-// the assembly, which are deterministic, and which the refinement needs anyway.
+// Binary file (little-endian, as both supported hosts are):
+//   CkptHeader                magic, version, rank, N, k, options, contour
+//   CkptExt (version >= 3)    flags: bit 0 = the capacitance inverse follows
+//   U, V_w, W~                N x rank complex FP64 each, column by column
+//   K^-1 (version 2; version 3 with flag bit 0)   rank x rank complex FP64
+//   trailer (version >= 3)    tag "WCSFNV64" and a 64-bit FNV-1a checksum of
+//                             every byte before the trailer
+// The operators are not stored: loading re-runs the mesh and the assembly,
+// which are deterministic, and which the refinement needs anyway.  Version 3
+// files are checked (size and checksum) before any device work.
 struct CkptHeader {
   char magic[8];
   int32_t version;
@@ -1304,9 +1341,56 @@ struct CkptHeader {
   wcs_options opt;
   Contour contour;
 };
+struct CkptExt {
+  uint32_t flags;
+  uint32_t reserved;
+};
 static const char kCkptMagic[8] = {'W', 'C', 'S', 'C', 'K', 'P', 'T', '1'};
+static const char kCkptTag[8] = {'W', 'C', 'S', 'F', 'N', 'V', '6', '4'};
+constexpr int kCkptVersion = 3;
 
-static int ckpt_arrays(wcs_ctx* c, FILE* f, bool write) {
+// FNV-1a (64-bit offset basis and prime) over 8-byte little-endian words; a
+// final partial word is hashed byte by byte.  Streaming: add() any split.
+struct Fnv64 {
+  uint64_t h = 14695981039346656037ull;
+  unsigned char pend[8];
+  int np = 0;
+  static constexpr uint64_t kPrime = 1099511628211ull;
+  void word(const unsigned char* b) {
+    uint64_t w = 0;
+    for (int i = 7; i >= 0; --i) w = (w << 8) | b[i];
+    h = (h ^ w) * kPrime;
+  }
+  void add(const void* data, size_t n) {
+    const unsigned char* p = (const unsigned char*)data;
+    while (n > 0 && np > 0) {
+      pend[np++] = *p++;
+      --n;
+      if (np == 8) { word(pend); np = 0; }
+    }
+    for (; n >= 8; n -= 8, p += 8) word(p);
+    while (n > 0) { pend[np++] = *p++; --n; }
+  }
+  uint64_t finish() {
+    for (int i = 0; i < np; ++i) h = (h ^ pend[i]) * kPrime;
+    np = 0;
+    return h;
+  }
+};
+
+// Reads and writes that keep the running checksum.
+struct CkptIO {
+  FILE* f;
+  Fnv64 sum;
+  bool write;
+  bool io(void* p, size_t bytes) {
+    const bool ok = write ? (fwrite(p, 1, bytes, f) == bytes) : (fread(p, 1, bytes, f) == bytes);
+    if (ok) sum.add(p, bytes);
+    return ok;
+  }
+};
+
+static int ckpt_arrays(wcs_ctx* c, CkptIO& io) {
   const int64_t N = c->N, r = c->rank;
   if (r <= 0) return 0;
   zd* arrs[3] = {c->U.z(), c->Vw.z(), c->Wt.z()};
@@ -1316,12 +1400,12 @@ static int ckpt_arrays(wcs_ctx* c, FILE* f, bool write) {
     for (int64_t c0 = 0; c0 < r; c0 += chunk) {
       const int64_t cc = std::min(chunk, r - c0);
       const size_t n = (size_t)N * cc;
-      if (write) {
+      if (io.write) {
         cudaMemcpyAsync(host.data(), arrs[a] + c0 * N, sizeof(zd) * n, cudaMemcpyDeviceToHost, c->s);
         TRY(sync(c));
-        if (fwrite(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: write failed"); return WCS_ERR_ARG; }
+        if (!io.io(host.data(), sizeof(zd) * n)) { set_error("checkpoint: write failed"); return WCS_ERR_ARG; }
       } else {
-        if (fread(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
+        if (!io.io(host.data(), sizeof(zd) * n)) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
         cudaMemcpyAsync(arrs[a] + c0 * N, host.data(), sizeof(zd) * n, cudaMemcpyHostToDevice, c->s);
         TRY(sync(c));
       }
@@ -1330,22 +1414,70 @@ static int ckpt_arrays(wcs_ctx* c, FILE* f, bool write) {
   return 0;
 }
 
-// The r x r capacitance inverse (version 2 files; adjoint solves need it).
-static int ckpt_kinv(wcs_ctx* c, FILE* f, bool write) {
+// The r x r capacitance inverse (adjoint solves need it).
+static int ckpt_kinv(wcs_ctx* c, CkptIO& io) {
   const int64_t r = c->rank;
   if (r <= 0) return 0;
   const size_t n = (size_t)r * r;
   std::vector<zd> host(n);
-  if (write) {
+  if (io.write) {
     cudaMemcpyAsync(host.data(), c->Kinv.p, sizeof(zd) * n, cudaMemcpyDeviceToHost, c->s);
     TRY(sync(c));
-    if (fwrite(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: write failed"); return WCS_ERR_ARG; }
+    if (!io.io(host.data(), sizeof(zd) * n)) { set_error("checkpoint: write failed"); return WCS_ERR_ARG; }
     return 0;
   }
-  if (fread(host.data(), sizeof(zd), n, f) != n) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
+  if (!io.io(host.data(), sizeof(zd) * n)) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
   TRY(c->Kinv.ensure(sizeof(zd) * n));
   cudaMemcpyAsync(c->Kinv.p, host.data(), sizeof(zd) * n, cudaMemcpyHostToDevice, c->s);
   return sync(c);
+}
+
+static bool ckpt_seek(FILE* f, int64_t off, int whence) {
+#if defined(_WIN32)
+  return _fseeki64(f, off, whence) == 0;
+#else
+  return fseeko(f, (off_t)off, whence) == 0;
+#endif
+}
+static int64_t ckpt_tell(FILE* f) {
+#if defined(_WIN32)
+  return _ftelli64(f);
+#else
+  return (int64_t)ftello(f);
+#endif
+}
+
+// Version 3: the file must be exactly as long as its header says, and the
+// checksum over everything before the trailer must match.  Leaves f at the
+// first byte after the header and extension.
+static int ckpt_verify(FILE* f, const CkptHeader& hd, const CkptExt& ext) {
+  const int64_t r = hd.rank, N = hd.N;
+  const int64_t body = (int64_t)sizeof(CkptHeader) + (int64_t)sizeof(CkptExt);
+  const int64_t payload = 3 * N * r * (int64_t)sizeof(zd) + ((ext.flags & 1u) ? r * r * (int64_t)sizeof(zd) : 0);
+  const int64_t expect = body + payload + 16;
+  if (!ckpt_seek(f, 0, SEEK_END)) { set_error("checkpoint: cannot seek"); return WCS_ERR_ARG; }
+  const int64_t size = ckpt_tell(f);
+  if (size < expect) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
+  if (size > expect) { set_error("checkpoint: unexpected bytes after the trailer"); return WCS_ERR_ARG; }
+  if (!ckpt_seek(f, 0, SEEK_SET)) { set_error("checkpoint: cannot seek"); return WCS_ERR_ARG; }
+  Fnv64 sum;
+  std::vector<unsigned char> buf((size_t)64 << 20);
+  for (int64_t left = size - 16; left > 0;) {
+    const size_t n = (size_t)std::min<int64_t>(left, (int64_t)buf.size());
+    if (fread(buf.data(), 1, n, f) != n) { set_error("checkpoint: read failed"); return WCS_ERR_ARG; }
+    sum.add(buf.data(), n);
+    left -= (int64_t)n;
+  }
+  unsigned char tr[16];
+  if (fread(tr, 1, 16, f) != 16) { set_error("checkpoint: file is truncated"); return WCS_ERR_ARG; }
+  uint64_t stored = 0;
+  for (int i = 15; i >= 8; --i) stored = (stored << 8) | tr[i];
+  if (std::memcmp(tr, kCkptTag, 8) != 0 || stored != sum.finish()) {
+    set_error("checkpoint: checksum mismatch (the file is corrupted)");
+    return WCS_ERR_ARG;
+  }
+  if (!ckpt_seek(f, body, SEEK_SET)) { set_error("checkpoint: cannot seek"); return WCS_ERR_ARG; }
+  return 0;
 }
 
 int wcs_save(wcs_ctx* c, const char* path) {
@@ -1356,16 +1488,25 @@ int wcs_save(wcs_ctx* c, const char* path) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
   std::memcpy(hd.magic, kCkptMagic, 8);
-  hd.version = (c->rank > 0 && c->Kinv.p) ? 2 : 1;
+  hd.version = kCkptVersion;
   hd.rank = c->rank;
   hd.N = c->N;
   hd.k = c->k;
   hd.opt = c->opt;
   hd.contour = c->contour;
-  int r = (fwrite(&hd, sizeof(hd), 1, f) == 1) ? 0 : WCS_ERR_ARG;
+  CkptExt ext{(c->rank > 0 && c->Kinv.p) ? 1u : 0u, 0u};
+  CkptIO io{f, Fnv64{}, true};
+  int r = (io.io(&hd, sizeof(hd)) && io.io(&ext, sizeof(ext))) ? 0 : WCS_ERR_ARG;
   if (r) set_error("checkpoint: write failed");
-  if (!r) r = ckpt_arrays(c, f, true);
-  if (!r && hd.version == 2) r = ckpt_kinv(c, f, true);
+  if (!r) r = ckpt_arrays(c, io);
+  if (!r && (ext.flags & 1u)) r = ckpt_kinv(c, io);
+  if (!r) {
+    unsigned char tr[16];
+    std::memcpy(tr, kCkptTag, 8);
+    uint64_t v = io.sum.finish();
+    for (int i = 8; i < 16; ++i) { tr[i] = (unsigned char)(v & 0xFF); v >>= 8; }
+    if (fwrite(tr, 1, 16, f) != 16) { set_error("checkpoint: write failed"); r = WCS_ERR_ARG; }
+  }
   if (fclose(f) != 0 && !r) { set_error("checkpoint: write failed"); r = WCS_ERR_ARG; }
   return r;
 }
@@ -1375,12 +1516,23 @@ int wcs_load(wcs_ctx* c, const char* path) {
   FILE* f = fopen(path, "rb");
   if (!f) { set_error(std::string("checkpoint: cannot open ") + path); return WCS_ERR_ARG; }
   CkptHeader hd;
+  CkptExt ext{0u, 0u};
   int r = 0;
   if (fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kCkptMagic, 8) != 0 ||
-      (hd.version != 1 && hd.version != 2)) {
+      hd.version < 1 || hd.version > kCkptVersion) {
     set_error("checkpoint: not a checkpoint of this library");
     r = WCS_ERR_ARG;
   }
+  if (!r && hd.version >= 3 && fread(&ext, sizeof(ext), 1, f) != 1) {
+    set_error("checkpoint: file is truncated");
+    r = WCS_ERR_ARG;
+  }
+  if (!r && (hd.N < 12 || hd.N > ((int64_t)1 << 22) || hd.rank < 0 || hd.rank > hd.N)) {
+    set_error("checkpoint: bad sizes");
+    r = WCS_ERR_ARG;
+  }
+  if (!r && hd.version >= 3) r = ckpt_verify(f, hd, ext);
+  const bool has_kinv = (hd.version == 2) || (hd.version >= 3 && (ext.flags & 1u));
   // the factors only fit operators assembled the same way
   const wcs_options& o = c->opt;
   if (!r && (hd.opt.precision != o.precision || hd.opt.q_far != o.q_far || hd.opt.q_near != o.q_near ||
@@ -1389,7 +1541,6 @@ int wcs_load(wcs_ctx* c, const char* path) {
     set_error("checkpoint: made with other precision or quadrature options than this context");
     r = WCS_ERR_ARG;
   }
-  if (!r && (hd.N < 12 || hd.rank < 0 || hd.rank > hd.N)) { set_error("checkpoint: bad sizes"); r = WCS_ERR_ARG; }
   if (!r) r = set_contour(c, hd.contour);
   if (!r) r = wcs_mesh(c, hd.N, hd.k);
   if (!r) r = wcs_assemble(c);
@@ -1401,8 +1552,9 @@ int wcs_load(wcs_ctx* c, const char* path) {
   }
   if (!r) {
     c->rank = hd.rank;
-    r = ckpt_arrays(c, f, false);
-    if (!r && hd.version == 2) r = ckpt_kinv(c, f, false);
+    CkptIO io{f, Fnv64{}, false};
+    r = ckpt_arrays(c, io);
+    if (!r && has_kinv) r = ckpt_kinv(c, io);
   }
   fclose(f);
   if (r) return r;
@@ -1430,6 +1582,7 @@ int wcs_planewave_rhs(wcs_ctx* c, int64_t B, const double* angles, double* e, do
   TRY(check_block(c, B, e, ld));
   TRY(check_block(c, B, hv, ld));
   if (B == 0) return WCS_OK;
+  TRY(check_angles(B, angles, "planewave_rhs"));
   DevBuf ang;
   TRY(ang.ensure(sizeof(double) * B));
   cudaMemcpyAsync(ang.p, angles, sizeof(double) * B, cudaMemcpyHostToDevice, c->s);
@@ -1446,8 +1599,8 @@ static int precondition(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld, zd* b
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
-  TRY(gram_inverse(e, ld, T1, N, N, cc, c->h, c->s));
-  TRY(gram_inverse(hv, ld, T2, N, N, cc, c->h, c->s));
+  TRY(ginv(c, e, ld, T1, N, cc));
+  TRY(ginv(c, hv, ld, T2, N, cc));
   if (c->mixed) {
     TRY(ensure_stage(c, cc));
     TRY(stage(c, c->stage1, T1, N, cc, 0));
@@ -1478,8 +1631,8 @@ static int residual_rhs_mixed(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld,
   TRY(gram_apply(x, ldx, T1, N, N, cc, c->h, 0.5, 1.0, c->s));          // + G x / 2
   TRY(axpby(N, cc, one, hv, ld, one, T1, N, c->s));                     // + h
   TRY(axpby(N, cc, mkz(0.0, c->k), e, ld, one, T2, N, c->s));           // + i k e
-  TRY(gram_inverse(T1, N, T1, N, N, cc, c->h, c->s));
-  TRY(gram_inverse(T2, N, T2, N, N, cc, c->h, c->s));
+  TRY(ginv(c, T1, N, T1, N, cc));
+  TRY(ginv(c, T2, N, T2, N, cc));
   TRY(stage(c, c->stage1, T1, N, cc, 0));
   TRY(stage(c, c->stage2, T2, N, cc, 0));
   TRY(tc_apply(c, 2, false, c->stage1, cc, mone, zero, R, N, mode));    // -D~ T1
@@ -1491,8 +1644,10 @@ static int residual_rhs_mixed(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld,
 // x = C^{-1} b with Woodbury + iterative refinement on the exact operator.
 // Mixed form with e, hv given: b only seeds x and scales the residual norm;
 // every residual is formed from e and hv directly (residual_rhs_mixed).
+// acc gathers the statistics over the blocks of one call: steps and final
+// residual (max over blocks) and the residual history (see wcs_solve_info).
 static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx, int64_t cc,
-                       int* steps, double* relres, const zd* e = nullptr, const zd* hv = nullptr,
+                       wcs_solve_info* acc, const zd* e = nullptr, const zd* hv = nullptr,
                        int64_t ld_eh = 0, bool adj = false) {
   const int64_t N = c->N;
   // adj: solve C^H x = b (the adjoint Woodbury and C^H in every residual)
@@ -1508,13 +1663,46 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
   zd* R = c->w4.z();
   zd* dx = c->w5.z();
   zd* T = c->w3.z();
-  // largest relative residual over the block's columns
+  int it = 0;
+  // residual after each refinement step of this block (the last evaluation
+  // at a step wins: a recomputed residual replaces the carried one)
+  double hist[WCS_HISTORY];
+  int hlen = 0;
+  auto finish = [&](double final_res) {
+    acc->refine_steps = std::max(acc->refine_steps, it);
+    acc->rel_residual = std::max(acc->rel_residual, final_res);
+    if (hlen == 0) { hist[0] = final_res; hlen = 1; }
+    for (int i = 0; i < WCS_HISTORY; ++i) {
+      const double v = hist[std::min(i, hlen - 1)];   // a block that stopped keeps its last value
+      acc->history[i] = std::max(acc->history[i], v);
+    }
+    acc->history_len = std::max(acc->history_len, hlen);
+  };
+  // largest relative residual over the block's columns.  A right-hand side
+  // that is not finite is the caller's error (WCS_ERR_ARG); a residual that
+  // is not finite for a finite right-hand side ends the solve as not
+  // converged (the refinement cannot recover from it).
   auto worst_of = [&](double& worst) -> int {
     TRY(column_norms(R, N, N, cc, nb.d() + cc, c->s));
     cudaMemcpyAsync(rn.data(), nb.d() + cc, sizeof(double) * cc, cudaMemcpyDeviceToHost, c->s);
     TRY(sync(c));
     worst = 0;
-    for (int64_t j = 0; j < cc; ++j) worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
+    for (int64_t j = 0; j < cc; ++j) {
+      if (!std::isfinite(bn[j])) {
+        set_error("right-hand side column " + std::to_string(j) + " of the block is not finite");
+        return WCS_ERR_ARG;
+      }
+      if (!std::isfinite(rn[j])) {
+        set_error("solve: the residual of column " + std::to_string(j) + " of the block is not finite");
+        finish(INFINITY);
+        return WCS_ERR_NOT_CONVERGED;
+      }
+      worst = std::max(worst, bn[j] > 0 ? rn[j] / bn[j] : rn[j]);
+    }
+    if (it < WCS_HISTORY) {
+      hist[it] = worst;
+      hlen = std::max(hlen, it + 1);
+    }
     return 0;
   };
   // R = b - C x with the given precision
@@ -1527,7 +1715,6 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
     }
     return worst_of(worst);
   };
-  int it = 0;
   double worst = 0;
   if (!c->mixed) {
     // FP64 form: plain refinement on the exact residual
@@ -1580,8 +1767,7 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
     }
   }
   nb.release();
-  *steps = std::max(*steps, it);
-  *relres = std::max(*relres, worst);
+  finish(worst);
   return (worst <= c->opt.refine_tol) ? 0 : WCS_ERR_NOT_CONVERGED;
 }
 
@@ -1596,20 +1782,20 @@ int wcs_solve_rhs(wcs_ctx* c, int64_t B, const double* e, const double* hv, int6
   TRY(ensure_work(c, std::min(B, chunk)));
   DevBuf bb;
   TRY(bb.ensure(sizeof(zd) * N * std::min(B, chunk)));
-  int steps = 0, status = WCS_OK;
-  double rr = 0;
+  int status = WCS_OK;
+  wcs_solve_info acc{};
   for (int64_t c0 = 0; c0 < B; c0 += chunk) {
     const int64_t cc = std::min(chunk, B - c0);
     // mixed form: b only seeds the solution (residuals are formed from e, h)
     const zd* ec = (const zd*)e + c0 * ld;
     const zd* hc = (const zd*)hv + c0 * ld;
     TRY(precondition(c, ec, hc, ld, bb.z(), N, cc, c->mixed ? PREC_PERIODIC : PREC_ACCURATE));
-    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr, ec, hc, ld);
+    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &acc, ec, hc, ld);
     if (r == WCS_ERR_NOT_CONVERGED) status = r;
     else if (r) return r;
   }
   bb.release();
-  if (info) { info->refine_steps = steps; info->rel_residual = rr; }
+  if (info) *info = acc;
   if (status) set_error("iterative refinement did not reach refine_tol");
   return status;
 }
@@ -1624,16 +1810,16 @@ static int solve_general(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, do
   if (B == 0) return WCS_OK;
   const int64_t chunk = c->opt.rhs_chunk;
   TRY(ensure_work(c, std::min(B, chunk)));
-  int steps = 0, status = WCS_OK;
-  double rr = 0;
+  int status = WCS_OK;
+  wcs_solve_info acc{};
   for (int64_t c0 = 0; c0 < B; c0 += chunk) {
     const int64_t cc = std::min(chunk, B - c0);
-    int r = solve_block(c, (const zd*)b + c0 * ldb, ldb, (zd*)x + c0 * ldx, ldx, cc, &steps, &rr, nullptr,
+    int r = solve_block(c, (const zd*)b + c0 * ldb, ldb, (zd*)x + c0 * ldx, ldx, cc, &acc, nullptr,
                         nullptr, 0, adj);
     if (r == WCS_ERR_NOT_CONVERGED) status = r;
     else if (r) return r;
   }
-  if (info) { info->refine_steps = steps; info->rel_residual = rr; }
+  if (info) *info = acc;
   if (status) set_error("iterative refinement did not reach refine_tol");
   return status;
 }
@@ -1669,6 +1855,8 @@ int wcs_shape_gradient_range(wcs_ctx* c, int64_t B, const double* angles, int np
     set_error("shape gradient: bad argument");
     return WCS_ERR_ARG;
   }
+  TRY(check_angles(B, angles, "shape_gradient (incidences)"));
+  TRY(check_angles(nphi, phi, "shape_gradient (observation angles)"));
   if (!(delta > 0)) delta = 1e-6;
   const int64_t N = c->N;
   DevBuf j, lam, E, F, G, ang, phd, eb, hb, bb, Y, W, dots;
@@ -1767,6 +1955,7 @@ int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j,
   if (c->stage < ST_FACTORED) { set_error("factor first"); return WCS_ERR_STATE; }
   TRY(check_block(c, B, j, ldj));
   if (B == 0) return WCS_OK;
+  TRY(check_angles(B, angles, "solve_planewaves"));
   const int64_t chunk = c->opt.rhs_chunk, N = c->N;
   TRY(ensure_work(c, std::min(B, chunk)));
   DevBuf &eb = c->sol_e, &hb = c->sol_h, &bb = c->sol_b, &ang = c->sol_ang;
@@ -1776,18 +1965,18 @@ int wcs_solve_planewaves(wcs_ctx* c, int64_t B, const double* angles, double* j,
   TRY(bb.ensure(sizeof(zd) * N * cmax));
   TRY(ang.ensure(sizeof(double) * B));
   cudaMemcpyAsync(ang.p, angles, sizeof(double) * B, cudaMemcpyHostToDevice, c->s);
-  int steps = 0, status = WCS_OK;
-  double rr = 0;
+  int status = WCS_OK;
+  wcs_solve_info acc{};
   for (int64_t c0 = 0; c0 < B; c0 += chunk) {
     const int64_t cc = std::min(chunk, B - c0);
     TRY(planewave_rhs(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, N, c->h, c->k, ang.d() + c0,
                       (int)cc, eb.z(), hb.z(), N, c->s, c->mixed));
     TRY(precondition(c, eb.z(), hb.z(), N, bb.z(), N, cc, c->mixed ? PREC_PERIODIC : PREC_ACCURATE));
-    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &steps, &rr, eb.z(), hb.z(), N);
+    int r = solve_block(c, bb.z(), N, (zd*)j + c0 * ldj, ldj, cc, &acc, eb.z(), hb.z(), N);
     if (r == WCS_ERR_NOT_CONVERGED) status = r;
     else if (r) return r;
   }
-  if (info) { info->refine_steps = steps; info->rel_residual = rr; }
+  if (info) *info = acc;
   if (status) set_error("iterative refinement did not reach refine_tol");
   return status;
 }
@@ -1812,6 +2001,7 @@ int wcs_farfield(wcs_ctx* c, int64_t B, const double* j, int64_t ldj, int nphi, 
   if (c->stage < ST_MESH) { set_error("mesh first"); return WCS_ERR_STATE; }
   TRY(check_block(c, B, j, ldj));
   if (B == 0 || nphi == 0) return WCS_OK;
+  TRY(check_angles(nphi, phi, "farfield"));
   DevBuf E, ang;
   TRY(E.ensure(sizeof(zd) * (int64_t)nphi * c->N));
   TRY(ang.ensure(sizeof(double) * nphi));
@@ -1842,13 +2032,19 @@ int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A, in
 static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B,
                            int64_t ldb, int planes, int accurate, double* D, int64_t ldd, void* stream) {
   if (accurate < 0 || (accurate && planes < 2)) { set_error("accurate contraction needs 2 or 3 planes"); return WCS_ERR_ARG; }
-  if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (!A || lda < K)) ||
-      (Nc > 0 && (!B || ldb < K)) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
+  if (M < 0 || Nc < 0 || K < 0 || planes < 1 || planes > 3 || (M > 0 && (lda < K || (K > 0 && !A))) ||
+      (Nc > 0 && (ldb < K || (K > 0 && !B))) || (M > 0 && Nc > 0 && (!D || ldd < Nc))) {
     set_error("bad argument");
     return WCS_ERR_ARG;
   }
   if (M == 0 || Nc == 0) return WCS_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  if (K == 0) {   // an empty contraction: D = 0
+    cudaError_t e = cudaMemset2DAsync(D, sizeof(double) * ldd, 0, sizeof(double) * Nc, M, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+    return WCS_OK;
+  }
   const int64_t ldp = ((K + 63) / 64) * 64;
   DevBuf pa, pb, err, ws;
   TRY(pa.ensure(sizeof(uint16_t) * ldp * M * planes));
@@ -1857,9 +2053,12 @@ static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, in
   int64_t ws_need = 0;
   if (!accurate) gemm_tc_split_plan((int)M, (int)Nc, (int)K, planes, planes, EPI_RAW_F64, &ws_need);
   if (ws_need > 0) TRY(ws.ensure(sizeof(float) * (size_t)ws_need));
-  cudaMemsetAsync(pa.p, 0, pa.bytes, s);
-  cudaMemsetAsync(pb.p, 0, pb.bytes, s);
-  cudaMemsetAsync(err.p, 0, sizeof(int), s);
+  {
+    cudaError_t e = cudaMemsetAsync(pa.p, 0, pa.bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pb.p, 0, pb.bytes, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err.p, 0, sizeof(int), s);
+    if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  }
   uint16_t* PA[3];
   uint16_t* PB[3];
   for (int p = 0; p < 3; ++p) {

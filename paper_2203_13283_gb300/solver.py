@@ -19,6 +19,11 @@ def default_options(**overrides):
     return o
 
 
+def _solve_stats(si):
+    return {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual,
+            "history": [si.history[i] for i in range(si.history_len)]}
+
+
 def _ptr(t):
     return C.c_void_p(t.data_ptr())
 
@@ -174,7 +179,7 @@ class Solver:
         si = SolveInfo()
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
         check(self.lib.wcs_solve_planewaves(self.h, len(a), pa, _ptr(j), self.N, C.byref(si)), allow)
-        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        self.last_solve = _solve_stats(si)
         return j.t()
 
     def solve_planewaves_host(self, angles, allow_unconverged=False, out=None):
@@ -193,7 +198,7 @@ class Solver:
         si = SolveInfo()
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
         check(self.lib.wcs_solve_planewaves_host(self.h, na, pa, pj, self.N, C.byref(si)), allow)
-        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        self.last_solve = _solve_stats(si)
         return out.T
 
     def solve_rhs(self, e, hv, allow_unconverged=False):
@@ -203,7 +208,7 @@ class Solver:
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
         check(self.lib.wcs_solve_rhs(self.h, ec.shape[0], _ptr(ec), _ptr(hc), self.N, _ptr(j), self.N,
                                      C.byref(si)), allow)
-        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        self.last_solve = _solve_stats(si)
         return j.t()
 
     def _solve_general(self, fn, b, allow_unconverged):
@@ -212,7 +217,7 @@ class Solver:
         si = SolveInfo()
         allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
         check(fn(self.h, bc.shape[0], _ptr(bc), self.N, _ptr(x), self.N, C.byref(si)), allow)
-        self.last_solve = {"refine_steps": si.refine_steps, "rel_residual": si.rel_residual}
+        self.last_solve = _solve_stats(si)
         return x.t()
 
     def solve(self, b, allow_unconverged=False):

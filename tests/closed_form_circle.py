@@ -29,13 +29,16 @@ import scipy.special as sp
 def _products(z, nmax, n_direct=None):
     """J_n H_n, J_n H_n', J_n' H_n', for n = 0..nmax at argument z (complex ok).
 
-    Direct scipy evaluation for n <= n_direct; for larger n, ratios and the
-    Wronskian J_n Y_{n-1} - J_{n-1} Y_n = 2 / (pi z), with J_n^2 dropped
-    (relative size |J_n / Y_n| < 1e-17 there).
+    Direct scipy evaluation for n <= n_direct (about |z| + 40, where Y_n is
+    still far from overflow); for larger n, from ratios: rho_n = J_n / J_{n-1}
+    by backward recurrence, tau_n = Y_{n-1} / Y_n by forward recurrence, the
+    Wronskian J_n Y_{n-1} - J_{n-1} Y_n = 2 / (pi z) for the products J Y, and
+    J_{n-1}^2 continued from the last direct value by the product of the
+    rho's (in logarithms, so it underflows gracefully to 0 far above |z|).
     """
     z = complex(z)
     if n_direct is None:
-        n_direct = int(min(nmax, max(40, 2 * abs(z) + 40)))
+        n_direct = int(min(nmax, max(40, abs(z) + 40)))
     n = np.arange(n_direct + 1)
     J = sp.jv(n, z)
     H = sp.hankel1(n, z)
@@ -61,10 +64,12 @@ def _products(z, nmax, n_direct=None):
     base = 2.0 / (np.pi * z * (r * t - 1.0))        # J_{n-1} Y_n
     Jp_over = 1.0 - m * r / z                        # J_n' / J_{n-1}
     Yp_over = t - m / z                              # Y_n' / Y_n
-    JY = r * base
-    JYp = r * base * Yp_over
-    JpYp = base * Jp_over * Yp_over
-    JH[m], JHp[m], JpHp[m] = 1j * JY, 1j * JYp, 1j * JpYp
+    # J_{n-1}^2 for n = n_direct + 1 .. nmax
+    logJ = np.log(complex(J[n_direct])) + np.concatenate([[0.0], np.cumsum(np.log(r[:-1]))])
+    J2 = np.exp(2.0 * logJ)
+    JH[m] = r * r * J2 + 1j * (r * base)
+    JHp[m] = r * J2 * Jp_over + 1j * (r * base * Yp_over)
+    JpHp[m] = J2 * Jp_over * Jp_over + 1j * (base * Jp_over * Yp_over)
     return JH, JHp, JpHp
 
 

@@ -61,3 +61,36 @@ def test_load_rejects_other_options(tmp_path):
     with pytest.raises(WCSError):
         b.load(tmp_path / "missing.wcs")
     b.close()
+
+
+def test_load_rejects_corrupted_or_truncated_file_and_keeps_context(tmp_path):
+    # a real checkpoint with one payload byte flipped, and one cut short: both
+    # rejected (WCS_ERR_ARG) before any device work; the context that refused
+    # them still solves exactly as before, and the intact file still loads
+    built()
+    from paper_2203_13283_gb300 import Solver
+    from paper_2203_13283_gb300._lib import WCS_ERR_ARG, WCSError
+    w = workloads.SMALL["ellipse_n200"]
+    a = Solver(precision=0, refine_tol=1e-10)
+    a.contour(w["family"], **w["params"]).mesh(w["N"], w["k"]).assemble()
+    a.skeleton(1e-8, seed=4)
+    a.factor()
+    ang = w["angles"][:3]
+    ja = a.solve_planewaves(ang).clone()
+    path = tmp_path / "ctx.wcs"
+    a.save(path)
+    data = path.read_bytes()
+    bad = bytearray(data)
+    bad[len(data) // 2] ^= 0x01
+    (tmp_path / "flip.wcs").write_bytes(bytes(bad))
+    (tmp_path / "cut.wcs").write_bytes(data[:-1000])
+    for name, word in (("flip.wcs", "checksum"), ("cut.wcs", "truncated")):
+        with pytest.raises(WCSError) as ei:
+            a.load(tmp_path / name)
+        assert ei.value.status == WCS_ERR_ARG and word in str(ei.value), str(ei.value)
+    assert torch.equal(a.solve_planewaves(ang), ja)
+    a.close()
+    b = Solver(precision=0, refine_tol=1e-10)
+    b.load(path)
+    assert torch.equal(b.solve_planewaves(ang), ja)
+    b.close()

@@ -54,3 +54,37 @@ def test_solve_rhs_matches_planewaves():
     j2 = to_np(s.solve_rhs(e, hv))
     assert np.max(np.abs(j1 - j2)) <= 1e-11 * np.max(np.abs(j1))
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_non_finite_inputs_are_rejected(precision):
+    # a NaN injected on the host into an angle, a general right-hand side or
+    # the Galerkin data e/eta must give WCS_ERR_ARG (not a "converged" NaN
+    # current), and the context must solve normally afterwards
+    from paper_2203_13283_gb300._lib import WCS_ERR_ARG, WCSError
+    w = workloads.SMALL["ellipse_n200"]
+    s = _factored(w, precision=precision, refine_tol=1e-10 if precision == 0 else 1e-7)
+    ang = np.array([0.0, 0.5, 1.0])
+    good = to_np(s.solve_planewaves(ang, allow_unconverged=True))
+    bad = ang.copy()
+    bad[1] = np.nan
+    with pytest.raises(WCSError) as ei:
+        s.solve_planewaves(bad)
+    assert ei.value.status == WCS_ERR_ARG and "angle 1" in str(ei.value)
+    b = np.ones((w["N"], 2), dtype=complex)
+    b[17, 1] = np.inf
+    with pytest.raises(WCSError) as ei:
+        s.solve(b)
+    assert ei.value.status == WCS_ERR_ARG and "not finite" in str(ei.value)
+    with pytest.raises(WCSError) as ei:
+        s.solve_adjoint(b)
+    assert ei.value.status == WCS_ERR_ARG
+    e, hv = s.planewave_rhs(ang)
+    e = e.clone()
+    e[5, 2] = complex(float("nan"), 0.0)
+    with pytest.raises(WCSError) as ei:
+        s.solve_rhs(e, hv)
+    assert ei.value.status == WCS_ERR_ARG
+    again = to_np(s.solve_planewaves(ang, allow_unconverged=True))
+    assert np.array_equal(good, again)
+    s.close()

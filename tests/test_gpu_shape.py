@@ -67,3 +67,50 @@ def test_shape_objective_autograd():
     s.close()
     assert abs(J.item() - J_ref) <= 1e-12 * J_ref
     assert np.max(np.abs(p.grad.numpy() - 3.0 * g_ref)) <= 1e-10 * np.max(np.abs(g_ref))
+
+
+def _factored(fam, base, p, Mp, k):
+    from paper_2203_13283_gb300 import Solver
+    s = Solver(refine_tol=1e-12, max_refine=16)
+    s.contour(fam, **base).perturb(p[:Mp], p[Mp:]).mesh(N, k).assemble()
+    s.skeleton(1e-10, max_rank=N // 2, seed=1, allow_cap=True)
+    s.factor()
+    return s
+
+
+def test_shape_gradient_beta_vs_oracle():
+    # sine parameters at a point without any symmetry (alpha_3 = beta_2 =
+    # 0.01), where their derivatives are genuinely non-zero
+    built()
+    w = workloads.WORKLOADS["ellipse_n8192"]
+    fam, base = w["family"], w["params"]
+    k = 2.0 * np.pi * (N / 10.0) / geometry.Contour(fam, base).L
+    p = np.zeros(2 * M)
+    p[3] = 0.01
+    p[M + 1] = 0.01
+    s = _factored(fam, base, p, M, k)
+    J, g = s.shape_gradient(INC, OBS, M)
+    s.close()
+    idx = [M + 1, M + 2, M + 4]                    # beta_2, beta_3, beta_5
+    g_ref = shape.gradient_fd(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    scale = np.max(np.abs(g_ref))
+    assert np.min(np.abs(g_ref)) > 1e-3 * scale
+    assert np.max(np.abs(g[idx] - g_ref)) <= 1e-6 * scale
+
+
+def test_shape_gradient_beta_rotation_identity():
+    # on the circle, turning everything by psi = -pi / (2m) maps sin(m theta)
+    # onto cos(m theta): dJ/d beta_m at (I, O) = dJ/d alpha_m at (I + psi, O + psi)
+    built()
+    Mr, k = 4, 8.0
+    inc = np.array([0.3, 1.7, 4.0])
+    obs = np.deg2rad(np.arange(0.0, 360.0, 20.0))
+    p = np.zeros(2 * Mr)
+    for m in (2, 3):
+        psi = -np.pi / (2 * m)
+        s = _factored("circle", {"a": 1.0}, p, Mr, k)
+        _, gb = s.shape_gradient(inc, obs, Mr)
+        _, ga = s.shape_gradient(inc + psi, obs + psi, Mr)
+        s.close()
+        assert abs(ga[m]) > 1e-2
+        assert abs(gb[Mr + m - 1] - ga[m]) <= 1e-6 * abs(ga[m]), (m, gb[Mr + m - 1], ga[m])

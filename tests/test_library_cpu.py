@@ -130,3 +130,98 @@ def test_header_is_plain_c(tmp_path):
     if gxx:
         subprocess.run([gxx, "-std=c++17", "-Wall", "-Werror", "-fsyntax-only", "-I", inc, "-x", "c++", str(src)],
                        check=True)
+
+
+# ---- checkpoint file format (version 3), checked on the host ------------------
+def _ckpt_structs():
+    import ctypes as C
+    from paper_2203_13283_gb300._lib import Options
+
+    class Contour(C.Structure):
+        _fields_ = [("family", C.c_int), ("a", C.c_double), ("ax", C.c_double), ("ay", C.c_double),
+                    ("p", C.c_double), ("nf", C.c_int), ("fc", C.c_double * 64), ("fs", C.c_double * 64),
+                    ("np", C.c_int), ("pc", C.c_double * 33), ("ps", C.c_double * 33)]
+
+    class Header(C.Structure):
+        _fields_ = [("magic", C.c_char * 8), ("version", C.c_int32), ("rank", C.c_int32), ("N", C.c_int64),
+                    ("k", C.c_double), ("opt", Options), ("contour", Contour)]
+
+    return Header
+
+
+def _fnv64_words(data):
+    """FNV-1a, 64-bit basis and prime, over 8-byte little-endian words; the
+    final partial word byte by byte (the checkpoint trailer's checksum)."""
+    h, prime, mask = 14695981039346656037, 1099511628211, (1 << 64) - 1
+    n8 = len(data) // 8
+    for w in np.frombuffer(data[:8 * n8], dtype="<u8").tolist():
+        h = ((h ^ w) * prime) & mask
+    for b in data[8 * n8:]:
+        h = ((h ^ b) * prime) & mask
+    return h
+
+
+def _write_ckpt(path, lib, N=16, rank=2, kinv=True, corrupt_at=None, cut=0):
+    import ctypes as C
+    from paper_2203_13283_gb300.solver import default_options
+    Header = _ckpt_structs()
+    hd = Header()
+    hd.magic = b"WCSCKPT1"
+    hd.version, hd.rank, hd.N, hd.k = 3, rank, N, 4.0
+    hd.opt = default_options()
+    lib.wcs_default_options(C.byref(hd.opt))
+    hd.opt.q_far, hd.opt.q_near = 6, 12          # as wcs_create resolves the automatic choice
+    hd.opt.sample_planes = 2
+    hd.contour.family, hd.contour.ax, hd.contour.ay = 1, 1.0, 0.5
+    ext = np.array([1 if kinv else 0, 0], dtype="<u4").tobytes()
+    rng = np.random.default_rng(5)
+    payload = rng.standard_normal(2 * (3 * N * rank + (rank * rank if kinv else 0))).tobytes()
+    body = bytes(hd) + ext + payload
+    data = bytearray(body + b"WCSFNV64" + _fnv64_words(body).to_bytes(8, "little"))
+    if corrupt_at is not None:
+        data[corrupt_at] ^= 0x10
+    if cut:
+        data = data[:-cut]
+    path.write_bytes(bytes(data))
+    return len(bytes(hd)) + len(ext)
+
+
+def test_checkpoint_checksum_and_size_are_checked_before_device_work(lib, tmp_path):
+    """Version-3 checkpoints carry an FNV-1a checksum; wcs_load rejects a
+    corrupted or truncated file with WCS_ERR_ARG before any device work (a
+    valid file gets past the check and fails later, here for want of a GPU)."""
+    import ctypes as C
+    from paper_2203_13283_gb300._lib import WCS_ERR_ARG
+    h = C.c_void_p()
+    assert lib.wcs_create(C.byref(h), None, None) == 0
+    good = tmp_path / "good.wcs"
+    off = _write_ckpt(good, lib)
+    cases = {"corrupt": dict(corrupt_at=off + 100), "header": dict(corrupt_at=12),
+             "truncated": dict(cut=9), "no_kinv_flag_mismatch": dict(kinv=False, cut=0)}
+    for name, kw in cases.items():
+        p = tmp_path / f"{name}.wcs"
+        _write_ckpt(p, lib, **kw)
+        if name == "no_kinv_flag_mismatch":
+            # flip the flag word without fixing the checksum
+            d = bytearray(p.read_bytes())
+            d[off - 8] ^= 1
+            p.write_bytes(bytes(d))
+        st = lib.wcs_load(h, str(p).encode())
+        assert st == WCS_ERR_ARG, name
+        msg = lib.wcs_last_error().decode()
+        assert ("checksum" in msg) or ("truncated" in msg) or ("bad sizes" in msg) or ("after the trailer" in msg), \
+            (name, msg)
+    garbage = tmp_path / "garbage.wcs"
+    garbage.write_bytes(b"not a checkpoint at all" * 10)
+    assert lib.wcs_load(h, str(garbage).encode()) == WCS_ERR_ARG
+    st = lib.wcs_load(h, str(good).encode())
+    msg = lib.wcs_last_error().decode()
+    assert "checksum" not in msg and "truncated" not in msg, msg
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except Exception:
+        has_gpu = False
+    if not has_gpu:
+        assert st != 0           # got past the file checks, then needed a device
+    assert lib.wcs_destroy(h) == 0

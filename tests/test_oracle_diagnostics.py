@@ -72,3 +72,16 @@ def test_rank_grows_slower_than_k():
     r128, e128, k128 = diagnostics.rank_and_error(CURVE, 128, 0.015, [0.0, 1.0])
     assert 0 < r64 < r128 < (k128 / k64) * r64
     assert max(e64, e128) < 1e-2       # eps = 0.015 of ||C_c||: a percent-level solve
+
+
+def test_frequency_response_is_the_eigenvalue_ratio_on_the_circle():
+    # pin of diagnostics.frequency_response: on the circle G^-1 C is circulant,
+    # so its response to the Fourier vector of frequency m is |mu_C / mu_G|
+    # (closed form, no quadrature)
+    N, k = 128, 8.0
+    C, Cc, G, k, a, _ = diagnostics.operators(geometry.Circle(2.0 * np.pi), N, k)
+    mu = cf.galerkin_eigs(1.0, N, k, k + 0.4j * k ** (1.0 / 3.0))
+    ref = np.abs(cf.c_eigs(mu) / mu["G"])
+    resp = diagnostics.frequency_response(C, G)
+    assert np.max(np.abs(resp - ref)) <= 1e-10 * np.max(ref)
+    assert np.max(diagnostics.frequency_response(C - Cc, G)) <= 1e-10 * np.max(ref)

@@ -8,6 +8,15 @@
    y -> -y and rotation by pi: J(beta) = J(-beta) and J(alpha_odd) =
    J(-alpha_odd), so those derivatives vanish; a swapped cos/sin index or a
    wrong parameter map fails here.
+4. Rotation covariance on the circle: turning the whole configuration by
+   psi = -pi / (2m) maps the perturbation sin(m theta) onto cos(m theta), so
+   dJ/d beta_m at incidence and observation sets (I, O) equals dJ/d alpha_m at
+   (I + psi, O + psi).  This pins the sine map by itself (an index off by one
+   changes the value by ~100%, a sign slip by 200%), independently of the
+   finite-difference and adjoint routes, which share the parameter map.
+5. The adjoint route against central differences at a point without
+   symmetry (alpha_3 = beta_2 = 0.01 breaks both mirrors and the half turn),
+   on sine parameters whose derivative is not zero.
 """
 
 import numpy as np
@@ -88,3 +97,29 @@ def test_product_rule_bilinear_forms(ellipse):
     assert np.max(np.abs(dG - (L_p - L) / (1e-6 * L) * ops["G"])) <= 1e-12 * np.max(np.abs(ops["G"])) / 1e-6
     for t in terms:
         assert all(np.isfinite(t[key]) for key in ("Dt", "D", "S", "N"))
+
+
+def test_beta_rotation_identity_on_circle():
+    Mr, Nr, k = 4, 64, 8.0
+    inc = np.array([0.3, 1.7, 4.0])
+    obs = np.deg2rad(np.arange(0.0, 360.0, 20.0))
+    p = np.zeros(2 * Mr)
+    for m in (2, 3):
+        psi = -np.pi / (2 * m)
+        _, gb = shape.gradient_adjoint("circle", {"a": 1.0}, p, Mr, Nr, k, inc, obs, [Mr + m - 1], delta=1e-6)
+        ga = shape.gradient_fd("circle", {"a": 1.0}, p, Mr, Nr, k, inc + psi, obs + psi, [m], delta=1e-5)[0]
+        assert abs(ga) > 1e-2
+        assert abs(gb[0] - ga) <= 1e-8 * abs(ga), (m, gb[0], ga)
+
+
+def test_adjoint_matches_central_differences_beta(ellipse):
+    fam, base, k = ellipse
+    p = np.zeros(2 * M)
+    p[3] = 0.01                       # alpha_3: breaks the y-axis mirror and the half turn
+    p[M + 1] = 0.01                   # beta_2: breaks the x-axis mirror
+    idx = [M + 1, M + 2, M + 4]       # beta_2, beta_3, beta_5
+    _, g_adj = shape.gradient_adjoint(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    g_fd = shape.gradient_fd(fam, base, p, M, N, k, INC, OBS, idx, delta=1e-6)
+    scale = np.max(np.abs(g_fd))
+    assert np.min(np.abs(g_fd)) > 1e-3 * scale      # all three are genuinely non-zero
+    assert np.max(np.abs(g_adj - g_fd)) <= 1e-8 * scale

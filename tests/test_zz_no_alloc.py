@@ -59,3 +59,17 @@ def test_noalloc_rejects_oversize():
                                               C.c_void_p(A.data_ptr()), 4096, 3, C.c_void_p(A.data_ptr()),
                                               4096, C.c_void_p(torch.cuda.current_stream().cuda_stream)))
     assert "32 MiB" in str(ei.value)
+
+
+def test_noalloc_empty_contraction_zeroes_output():
+    # K = 0: D = A B^T is the zero matrix; the call must write it (the output
+    # buffer starts as NaN) for both entry points, twice in a row
+    built()
+    from paper_2203_13283_gb300._lib import load
+    lib = load()
+    A = torch.zeros((1, 1), dtype=torch.float64, device="cuda")
+    for fn in (lib.wcs_gemm_split_bf16_noalloc, lib.wcs_gemm_split_bf16, lib.wcs_gemm_split_bf16_noalloc):
+        D = _call(fn, A[:, :0].expand(37, 0), A[:, :0].expand(19, 0), 2)
+        torch.cuda.synchronize()
+        assert D.shape == (37, 19)
+        assert (D == 0).all()
