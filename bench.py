@@ -3,18 +3,28 @@
 
 Metric: RHS solves/s and setup seconds at N = 32768 (superellipse
 |x|^4 + |y/0.6|^4 = 1, 10 elements per wavelength, 1024 plane waves uniform in
-angle), mixed-precision form.  One step = the whole hot path over one batch:
-mesh + assembly + circulant eigenvalues + randomized skeleton + capacitance
-factor (setup), then 1024 plane-wave solves (projection, preconditioned
-right-hand side of Eq. 5, Woodbury apply of Eq. 9, iterative refinement).
+angle), mixed-precision form, against the plain FP64 form on the same GPU.
+One step = the whole hot path over one batch: mesh + assembly + circulant
+eigenvalues + randomized skeleton + capacitance factor (setup), then 1024
+plane-wave solves (projection, preconditioned right-hand side of Eq. 5,
+Woodbury apply of Eq. 9, iterative refinement).
+
+After the timed steps (rank 0 of a single-GPU run):
+  e2e        the same solve through the C ABI with host buffers;
+  fp64_form  the plain FP64 form at the same size: setup, RHS solves/s on a
+             stated subset of the angles, its refinement history, and the
+             mixed form's per-column error against it;
+  rooflines  per kernel category, against measured peaks.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-Prints one JSON line on rank 0.
+Prints one JSON line on rank 0.  With --gpus N > 1 and no launcher
+environment, the script starts itself under torch.distributed.run.
 """
 
 import argparse
 import json
 import os
+import socket
 import statistics
 import subprocess
 import sys
@@ -47,23 +57,8 @@ def profile_figure(name, key):
         with open(path) as f:
             for line in f:
                 if line.startswith(key + ":"):
-                    return float(line.split(":")[1]), "profiles/" + name
-    except OSError:
-        pass
-    return None, None
-
-
-def measured_traffic_ratio():
-    """DRAM bytes (read + write) per algorithmic byte of the operator-product
-    contraction, from the ncu capture summarised in profiles/ (a small case of
-    the same kernel; the traffic of a launch scales with its planes read)."""
-    path = os.path.join(ROOT, "profiles", "k_gemm_tc_ellipse_n4096_mixed.md")
-    try:
-        with open(path) as f:
-            for line in f:
-                if line.startswith("dram_bytes_per_algorithmic_byte:"):
-                    return float(line.split(":")[1]), "profiles/k_gemm_tc_ellipse_n4096_mixed.md"
-    except OSError:
+                    return float(line.split(":")[1].split()[0]), "profiles/" + name
+    except (OSError, ValueError):
         pass
     return None, None
 
@@ -112,12 +107,28 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
+def cpu_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
+        return max(n) if n else None
+    except Exception:
+        return None
+
+
 def oracle_sample(w, n_sample, B_sample):
     """The CPU oracle on a bounded sample of the workload: the full dense
     pipeline (assembly, C of Eq. 6, LU solve of Eq. 5 for B_sample plane
-    waves) at n_sample elements of the same contour family; returns seconds,
-    the extrapolation to the full size by the N^2 (assembly) and N^3 (LU)
-    costs, and the thread count."""
+    waves) at n_sample elements of the same contour family.  Returns the
+    seconds of each part and the time extrapolated to the full size by the
+    parts' costs, N^2 (assembly) and N^3 (C formation and LU)."""
     from oracle import assembly, geometry, solver as osolver
     cur = geometry.Contour(w["family"], w["params"]) if w["family"] != "circle" else geometry.Circle(2 * np.pi)
     k, kt, _ = geometry.wavenumbers(cur.L, n_sample, w["k"])
@@ -127,32 +138,26 @@ def oracle_sample(w, n_sample, B_sample):
     e, hv = osolver.planewave_rhs(cur, n_sample, k, w["angles"][:B_sample])
     j, C, b = osolver.dense_solve(M, k, e, hv)
     t2 = time.perf_counter()
-    N = w["N"]
-    r = N / n_sample
+    r = w["N"] / n_sample
     t_full = (t1 - t0) * r ** 2 + (t2 - t1) * r ** 3
-    return t2 - t0, t_full, (t1 - t0), (t2 - t1)
+    return t2 - t0, t_full
 
 
-def cpu_threads():
-    try:
-        return len(os.sched_getaffinity(0))
-    except Exception:
-        return os.cpu_count()
+ORACLE_N, ORACLE_B = 512, 64
 
 
 def run_reference(args, w):
-    n_sample, B_sample = 256, 64
     times, fulls = [], []
     for it in range(args.warmup + args.steps):
-        t, tf, ta, ts = oracle_sample(w, n_sample, B_sample)
+        t, tf = oracle_sample(w, ORACLE_N, ORACLE_B)
         if it >= args.warmup:
             times.append(t)
             fulls.append(tf)
     full = statistics.median(fulls)
     value = w["angles"].size / full
-    sample = (f"full oracle pipeline (dense FP64 assembly, dense C, LU solve) at N={n_sample}, "
-              f"{B_sample} plane waves, same contour; extrapolated to N={w['N']}, B={w['angles'].size} "
-              f"by N^2 (assembly) and N^3 (C formation + LU)")
+    sample = (f"full oracle pipeline (dense FP64 assembly, dense C of Eq. 6, LU solve) at N={ORACLE_N}, "
+              f"{ORACLE_B} plane waves, same contour; extrapolated to N={w['N']}, B={w['angles'].size} "
+              f"by N^2 (assembly) and N^3 (C formation + LU); BLAS threads {blas_threads()}")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -163,26 +168,96 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
+def relaunch_distributed(args):
+    """--gpus N > 1 without a launcher: start N ranks under torch.distributed.run."""
+    with socket.socket() as sck:
+        sck.bind(("127.0.0.1", 0))
+        port = sck.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def steps_to(history, tol):
+    """First refinement step whose residual is <= tol (None if never)."""
+    for i, v in enumerate(history):
+        if v <= tol:
+            return i
+    return None
+
+
+def roofline_entry(cat, prof, hbm, bf16s, fma):
+    """Roofline of one kernel category from the run's CUDA-event profile."""
+    v = prof[cat]
+    if not v["launches"]:
+        return None
+    sec = v["ms"] / 1e3
+    per = v["launches"]
+    if cat in ("gemm_tc", "gemm_tc_acc"):
+        achieved = v["work"] / sec / 1e12
+        name = "k_gemm_tc" if cat == "gemm_tc" else "k_gemm_tc_acc"
+        ratio, src = profile_figure(f"{name}_ellipse_n4096_mixed.md", "dram_bytes_per_algorithmic_byte")
+        return {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
+                "traffic": (ratio * v["bytes"] / per) if ratio else None,
+                "algorithmic_bytes_per_launch": v["bytes"] / per, "traffic_source": src,
+                "kernel": f"{name} (tcgen05 split-bf16 complex operator product)",
+                "work": "useful complex-product flops 2*M*Nc*K (split-bf16 issues nprod x these)",
+                "peak_source": "measured bf16 sustained (cuBLAS, MEASURED_PEAKS.json)", "launches": per,
+                "ms_total": v["ms"]}
+    if cat == "fft":
+        achieved = v["bytes"] / sec / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": "k_fft_tile (C_c, C_c^-1 applies: two transforms + scaling)",
+                "work": "4 x 16 N bytes per column and apply", "peak_source": "measured copy (MEASURED_PEAKS.json)",
+                "launches": per, "ms_total": v["ms"]}
+    if cat == "assembly":
+        units = v["work"] / per                      # far point pairs per launch
+        fpu, fsrc = profile_figure("k_assemble_fast_superellipse_n32768.md", "fp32_flops_per_far_point_pair")
+        bpu, _ = profile_figure("k_assemble_fast_superellipse_n32768.md", "dram_bytes_per_far_point_pair")
+        peak = fma.get(32)
+        if not fpu or not peak:
+            return {"bound": "alu", "achieved": units / (sec / per) / 1e9, "unit": "G far point pairs/s",
+                    "peak": None, "frac": None, "traffic": None, "kernel": "assembly (k_assemble_fast + k_assemble<1>)",
+                    "launches": per, "ms_total": v["ms"]}
+        achieved = fpu * units / (sec / per) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (peak / 1e12), "traffic": (bpu * units) if bpu else None,
+                "kernel": "assembly: k_assemble_fast (FP32 far pairs) + k_assemble<1> (FP64 near band)",
+                "work": f"far point pairs N^2 q_far^2 = {units:.3e} per launch x {fpu:.0f} counted FP32 flops per pair",
+                "peak_source": "FP32 FMA issue rate measured by wcs_fma_rate in this run", "figures_source": fsrc,
+                "launches": per, "ms_total": v["ms"]}
+    return None
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="superellipse_n32768")
     ap.add_argument("--form", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--tol", type=float, default=None, help="skeleton tolerance")
     ap.add_argument("--max-rank", type=int, default=None,
-                    help="skeleton rank cap (default N/8 in the mixed form, none in FP64)")
+                    help="skeleton rank cap (default N/8 in the mixed form, 512 in FP64)")
     ap.add_argument("--refine-tol", type=float, default=None)
     ap.add_argument("--rhs", type=int, default=None)
+    ap.add_argument("--zfast", type=float, default=None,
+                    help="mixed form: FP32 far pairs above k R = zfast (default: library default)")
     ap.add_argument("--sample-planes", type=int, default=0,
                     help="mixed form: bf16 planes in the skeleton's sampling products (0: library default)")
+    ap.add_argument("--fp64-rhs", type=int, default=16,
+                    help="angles of the FP64-form leg (every B/n-th angle of the batch; 0 skips the leg)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
     from paper_2203_13283_gb300 import dist as wdist
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_distributed(args))
     rank, world, local = wdist.world()
+    if world != args.gpus:
+        print(json.dumps({"error": f"--gpus {args.gpus} but the launcher started {world} ranks"}), flush=True)
+        sys.exit(2)
     w = dict(workloads.WORKLOADS[args.workload])
     if args.rhs:
         w["angles"] = workloads.uniform_angles(args.rhs)
@@ -199,14 +274,15 @@ def main():
         dist.init_process_group("nccl")
     from paper_2203_13283_gb300 import build as libbuild
     libbuild.build()
-    from paper_2203_13283_gb300 import Solver
+    from paper_2203_13283_gb300 import Solver, _lib
 
     mixed = args.form == "mixed"
     tol = args.tol if args.tol is not None else (1e-6 if mixed else 1e-2)
-    max_rank = args.max_rank if args.max_rank is not None else (w["N"] // 8 if mixed else 0)
-    rtol = args.refine_tol if args.refine_tol is not None else (1e-7 if mixed else 1e-12)
-    S = Solver(device=f"cuda:{local}", precision=1 if mixed else 0, refine_tol=rtol, max_refine=12,
-               rhs_chunk=1024 if mixed else 256, block=64, sample_planes=args.sample_planes)
+    max_rank = args.max_rank if args.max_rank is not None else (w["N"] // 8 if mixed else 512)
+    rtol = args.refine_tol if args.refine_tol is not None else (1e-7 if mixed else 1e-11)
+    extra = {} if args.zfast is None else {"zfast": args.zfast}
+    S = Solver(device=f"cuda:{local}", precision=1 if mixed else 0, refine_tol=rtol, max_refine=12 if mixed else 30,
+               rhs_chunk=1024 if mixed else 64, block=64, sample_planes=args.sample_planes, **extra)
     stream = S.stream
     angles = w["angles"]
     B = len(angles)
@@ -239,7 +315,6 @@ def main():
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    from paper_2203_13283_gb300 import _lib
     launches0 = _lib.load().wcs_launch_count()
     T0 = torch.cuda.Event(enable_timing=True)
     T1 = torch.cuda.Event(enable_timing=True)
@@ -280,62 +355,84 @@ def main():
     del jh
 
     hbm, bf16, bf16s, src = peaks()
-    traffic_ratio, traffic_src = measured_traffic_ratio()
-    g = prof["gemm_tc"]
-    a = prof["assembly"]
-    roof = None
-    if g["launches"]:
-        ms_per = g["ms"] / g["launches"]
-        achieved = g["work"] / g["launches"] / (ms_per / 1e3) / 1e12
-        alg_bytes = g["bytes"] / g["launches"]
-        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s",
-                "frac": achieved / bf16s,
-                "traffic": (traffic_ratio * alg_bytes) if traffic_ratio else None,
-                "algorithmic_bytes_per_launch": alg_bytes, "traffic_source": traffic_src,
-                "kernel": "k_gemm_tc (tcgen05 split-bf16 complex operator product)",
-                "work": "useful complex-product flops 2*M*Nc*K (split-bf16 executes nprod x these)",
-                "peak_source": f"{src} bf16 sustained", "launches": g["launches"], "ms_total": g["ms"]}
-    # the roofline reported is that of the kernel with the largest share of the
-    # step: the FP64 assembly (far pairs in FP64) or the tensor-core product
-    roof_tensor = roof
-    fp64_peak = 1.25   # TFLOP/s, nominal (the measured-peaks file has no FP64 figure)
-    if a["launches"] and a["ms"] > g["ms"] + prof["gemm_tc_acc"]["ms"]:
-        fpu, fsrc = profile_figure("k_assemble_fp64_ellipse_n4096_mixed.md", "fp64_flops_per_far_point_pair")
-        bpu, _ = profile_figure("k_assemble_fp64_ellipse_n4096_mixed.md", "dram_bytes_per_far_point_pair")
-        if fpu:
-            units = a["work"] / a["launches"]
-            ach = fpu * units / (a["ms"] / a["launches"] / 1e3) / 1e12
-            roof = {"bound": "fp64", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp64_peak, "traffic": (bpu * units) if bpu else None,
-                    "kernel": "k_assemble<1> (FP64 point-pair integration of S~, D, D~, N)",
-                    "work": f"far point pairs N^2 q_far^2 = {units:.3e} per launch x {fpu:.0f} FP64 flops per pair "
-                            "(counted DFMA/DADD/DMUL at N = 4096)",
-                    "peak_source": "nominal GB300 FP64 (recipe table)", "figures_source": fsrc}
+    import ctypes
+    fma = {}
+    for prec, iters in ((64, 20000), (32, 200000)):
+        r = ctypes.c_double(0.0)
+        if _lib.load().wcs_fma_rate(prec, iters, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(r)) == 0:
+            fma[prec] = r.value
+    rooflines = {cat: roofline_entry(cat, prof, hbm, bf16s, fma) for cat in ("assembly", "gemm_tc", "gemm_tc_acc", "fft")}
+    rooflines = {k: v for k, v in rooflines.items() if v}
+    # the headline roofline is that of the kernel category with the largest share of the step
+    share = {k: prof[k]["ms"] for k in rooflines}
+    dominant = max(share, key=share.get) if share else None
+    roof = rooflines.get(dominant)
+
     line = {
         "metric": METRIC, "value": value, "unit": "RHS solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2/fp32/f64" if mixed else "f64",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/fp32/f64" if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "N": w["N"], "B": B, "k": info["k"], "form": args.form,
-                   "skeleton_tol": tol, "rank": ranks[-1], "refine_tol": rtol,
+                   "skeleton_tol": tol, "rank": ranks[-1], "rank_cap": max_rank, "refine_tol": rtol,
                    "refine_steps": last["refine_steps"], "rel_residual": last["rel_residual"],
-                   "setup_s": statistics.median(setups), "solve_s": statistics.median(solves),
+                   "residual_history": last["history"],
+                   "refine_steps_to_1e-6": steps_to(last["history"], 1e-6),
+                   "refine_steps_to_1e-10": steps_to(last["history"], 1e-10),
+                   "zfast": info["zfast"], "setup_s": statistics.median(setups), "solve_s": statistics.median(solves),
                    "l2": "operators (tens of GB) exceed L2: no flush needed", "parallelism": f"replicas{world}"},
         "setup_s": statistics.median(setups),
-        "e2e": e2e, "clocks": clk, "roofline": roof, "roofline_tensor_product": roof_tensor,
+        "e2e": e2e, "clocks": clk, "roofline": roof, "rooflines": rooflines, "roofline_kernel": dominant,
+        "fma_peaks_tflops": {str(k): v / 1e12 for k, v in fma.items()},
         "kernels": {k: {"launches": v["launches"], "ms": v["ms"]} for k, v in prof.items() if v["launches"]},
-        "assembly_pairs_per_s": (a["work"] / (a["ms"] / 1e3)) if a["launches"] else None,
+        "assembly_pairs_per_s": (prof["assembly"]["work"] / (prof["assembly"]["ms"] / 1e3))
+        if prof["assembly"]["launches"] else None,
         "gpu_launches": launches,
     }
+
+    # the plain FP64 form at the same size, on a subset of the batch's angles
+    if mixed and world == 1 and args.fp64_rhs > 0:
+        stride = max(1, B // args.fp64_rhs)
+        sub = np.arange(0, B, stride)[:args.fp64_rhs]
+        jm = j[sub].cpu().numpy().T
+        S.close()
+        del j
+        torch.cuda.empty_cache()
+        F = Solver(device=f"cuda:{local}", precision=0, refine_tol=1e-11, max_refine=30, rhs_chunk=64, block=64)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(F.stream)
+        F.contour(w["family"], **w["params"]).mesh(w["N"], w["k"]).assemble()
+        r64 = F.skeleton(1e-2, max_rank=512, seed=1, allow_cap=True)
+        F.factor()
+        e1.record(F.stream)
+        j64 = F.solve_planewaves(angles[sub], allow_unconverged=True)
+        e2.record(F.stream)
+        e2.synchronize()
+        j64 = j64.cpu().numpy()
+        h64 = F.last_solve["history"]
+        err = np.linalg.norm(jm - j64, axis=0) / np.linalg.norm(j64, axis=0)
+        F.close()
+        line["fp64_form"] = {
+            "setup_s": e0.elapsed_time(e1) / 1e3, "rank": r64, "rank_cap": 512, "skeleton_tol": 1e-2,
+            "rhs": int(len(sub)), "angles": f"every {stride}th of the batch",
+            "rhs_per_s": len(sub) / (e1.elapsed_time(e2) / 1e3),
+            "refine_tol": 1e-11, "rel_residual": F.last_solve["rel_residual"], "residual_history": h64,
+            "refine_steps_to_1e-6": steps_to(h64, 1e-6), "refine_steps_to_1e-10": steps_to(h64, 1e-10)}
+        line["mixed_vs_fp64_rel_err"] = {"max": float(err.max()), "per_column": [float(x) for x in err],
+                                         "angles_rad": [float(a) for a in angles[sub]]}
+        line["speedup_vs_fp64_form"] = {"rhs_per_s": value / line["fp64_form"]["rhs_per_s"],
+                                        "setup": line["fp64_form"]["setup_s"] / line["setup_s"]}
+    else:
+        S.close()
+
     if rank == 0 and not args.no_cpu_baseline:
-        n_sample, B_sample = 256, 64
-        t, tf, _, _ = oracle_sample(w, n_sample, B_sample)
+        t, tf = oracle_sample(w, ORACLE_N, ORACLE_B)
         line["cpu_baseline"] = {"value": B / tf, "unit": "RHS solves/s", "cores": cpu_threads(), "kind": "oracle",
-                                "sample": f"oracle full pipeline at N={n_sample}, {B_sample} RHS ({t:.1f} s), "
-                                          f"extrapolated to N={w['N']}, B={B} by N^2 assembly + N^3 LU"}
+                                "sample": f"oracle full pipeline at N={ORACLE_N}, {ORACLE_B} RHS ({t:.1f} s), "
+                                          f"extrapolated to N={w['N']}, B={B} by N^2 assembly + N^3 C and LU; "
+                                          f"BLAS threads {blas_threads()}"}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    S.close()
 
 
 if __name__ == "__main__":

@@ -48,8 +48,9 @@ typedef enum wcs_status {
 typedef enum wcs_precision {
   WCS_PREC_FP64 = 0,        /* every stage in complex FP64 */
   WCS_PREC_MIXED = 1        /* operator products on the tensor cores (split-bf16, FP32
-                               accumulation), far-field kernels in FP32 with FP64 phase;
-                               FP64 singular quadrature, circulant eigenvalues,
+                               accumulation; exact fixed-point products for the residual
+                               with exact_residual), element-pair integrals in FP64 except
+                               far pairs beyond zfast (FP32); FP64 circulant eigenvalues,
                                capacitance matrix and refinement vectors */
 } wcs_precision;
 
@@ -68,14 +69,24 @@ typedef struct wcs_options {
   int rhs_chunk;      /* right-hand sides processed per pass (default 256) */
   int mixed_planes;   /* mixed form: bf16 planes per operator entry (default 3, max 3) */
   int rhs_planes;     /* mixed form: bf16 planes per staged vector entry (= mixed_planes) */
-  double zfast;       /* mixed form: if > 0, far pairs with k R >= zfast + 2 k h are integrated in
-                         FP32 around FP64 element-centre phases (~1e-7 entries; 9 is the smallest
-                         safe value).  Default 0: all pairs in FP64.  The FP32 path assembles ~30x
-                         faster, but at N = 32768 (k = 3642) its solution error reaches 2.2e-6 for
-                         grazing incidence, against 2.4e-7 with FP64 pairs. */
+  double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h are integrated in FP32
+                         around float-float element-centre phases (9 is the smallest safe value),
+                         nearer ones in FP64; 0: every pair in FP64.  Default -1 = automatic:
+                         2000 in the mixed form.  Measured at N = 32768 (superellipse, k = 3642)
+                         against the FP64 form, for incidence grazing the flat faces: 9.8e-7 with
+                         zfast = 9 (assembly 0.9 s), 3.8e-7 with 2000 (3.1 s), 2.4e-7 with 0
+                         (10.9 s).  The FP32 part loses accuracy where the two terms of the
+                         Maue form of N cancel (pairs on one flat face), and there its roundings
+                         repeat along each diagonal of the operator. */
   int sample_planes;  /* mixed form: bf16 planes of each operand in the skeleton's sampling
                          products (default 0 = 2; 1 = one product per pass, ~4e-3 relative) */
-  int reserved;
+  int exact_residual; /* mixed form: 1 = evaluate the refinement residual b - C x exactly (fixed-
+                         point slices of the operator planes and of x, integer products on the
+                         tensor cores, FP64 sums), so refinement reaches refine_tol down to ~1e-12
+                         against the stored operator; costs 5 bf16 slices of each operator (4 x 10
+                         N^2 bytes, built at the first such solve) and about one extra C x per 1024
+                         right-hand sides and round.  0 (default): residuals in split-bf16 with FP32
+                         accumulation, which floor near 3e-7. */
 } wcs_options;
 
 typedef struct wcs_info {
@@ -88,6 +99,7 @@ typedef struct wcs_info {
   int rank;           /* skeleton rank (after wcs_skeleton), else -1 */
   double norm_cc;     /* ||C_c||_2 = max |mu_C| (after wcs_assemble) */
   double min_curvature; /* minimum curvature found by the convexity check */
+  double zfast;       /* far-pair FP32 threshold in effect (mixed form; 0 in the FP64 form) */
 } wcs_info;
 
 /* Entries of wcs_solve_info::history. */
@@ -354,6 +366,22 @@ int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, const double* 
                                 const double* B_dev, int64_t ldb, int planes, double* D_dev,
                                 int64_t ldd, void* stream);
 
+/* Exact real contraction D (M x Nc) = A (M x K) * B (Nc x K)^T on the tensor
+ * cores, all FP64 row-major device arrays (lda, ldb >= K, ldd >= Nc).  The
+ * operator products of the refinement residual (Eq. 5 with C of Eq. 6) in
+ * the mixed form's exact_residual mode use the same method: each row is cut
+ * into chunks of 1024 K values, each chunk scaled by a power of two so its
+ * entries lie in (-1, 1) and written as five 7-bit fixed-point slices (bf16
+ * integers); the 15 slice pairs of combined order < 5 are multiplied with
+ * one split of K per chunk, where the FP32 accumulation of integer products
+ * below 2^24 is exact, and the scaled partials are summed in FP64.  Error per
+ * entry <= ~2^-35 (|A| |B|^T) (the slices' truncation), independent of K.
+ * Allocates about 10 (M + Nc) K + 4 (K / 1024) M Nc bytes; ordered on
+ * `stream`; synchronises.  Errors: WCS_ERR_ARG, WCS_ERR_OOM, WCS_ERR_CUDA,
+ * WCS_ERR_TIMEOUT (a bounded device wait expired). */
+int wcs_gemm_exact(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda, const double* B_dev,
+                   int64_t ldb, double* D_dev, int64_t ldd, void* stream);
+
 /* Number of CUDA kernel launches the library has issued in this process. */
 uint64_t wcs_launch_count(void);
 
@@ -361,11 +389,14 @@ uint64_t wcs_launch_count(void);
  * each instrumented launch (enable != 0 turns it on; off by default). */
 int wcs_profile(wcs_ctx* ctx, int enable);
 
-/* Sum the recorded launches by category (synchronises): out_host gets 7 x 4
- * doubles {launches, total ms, algorithmic work, bytes} for the categories
- * tensor-core contraction (work = useful real flops 2 M Nc K of the complex
- * product), assembly (work = far point pairs), FFT circulant applies (bytes),
- * FP64 GEMM, skeleton, factor, solve.  reset != 0 clears the records. */
+/* Sum the recorded launches by category (synchronises): out_host gets 14 x 4
+ * doubles {launches, total ms, algorithmic work, bytes} for the categories, in
+ * order: tensor-core contraction (work = useful real flops 2 M Nc K of the
+ * complex product), assembly (work = far point pairs), FFT circulant applies
+ * (bytes), FP64 GEMM, skeleton, factor, solve, drained tensor-core
+ * contraction, skeleton sampling, projection, orthonormalisation, V_w,
+ * capacitance inverse, exact contraction (work = useful flops, as the first).
+ * reset != 0 clears the records. */
 int wcs_profile_read(wcs_ctx* ctx, int reset, double* out_host);
 
 /* Measured issue rate of the FMA pipe (precision 64: FP64, 32: FP32) on the

@@ -21,13 +21,14 @@ class Options(C.Structure):
                 ("near_band", C.c_int), ("block", C.c_int), ("max_refine", C.c_int),
                 ("refine_tol", C.c_double), ("rhs_chunk", C.c_int), ("mixed_planes", C.c_int),
                 ("rhs_planes", C.c_int), ("zfast", C.c_double), ("sample_planes", C.c_int),
-                ("reserved", C.c_int)]
+                ("exact_residual", C.c_int)]
 
 
 class Info(C.Structure):
     _fields_ = [("N", C.c_int64), ("L", C.c_double), ("h", C.c_double), ("a", C.c_double),
                 ("k", C.c_double), ("kt_re", C.c_double), ("kt_im", C.c_double),
-                ("rank", C.c_int), ("norm_cc", C.c_double), ("min_curvature", C.c_double)]
+                ("rank", C.c_int), ("norm_cc", C.c_double), ("min_curvature", C.c_double),
+                ("zfast", C.c_double)]
 
 
 WCS_HISTORY = 32
@@ -80,6 +81,7 @@ SIGNATURES = {
     "wcs_profile_read": (I, [P, I, P]),
     "wcs_quadrature_tables": (I, [I, P]),
     "wcs_fma_rate": (I, [I, I, P, C.POINTER(C.c_double)]),
+    "wcs_gemm_exact": (I, [I64, I64, I64, P, I64, P, I64, P, I64, P]),
 }
 
 _lib = None

@@ -689,7 +689,14 @@ int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s)
   args.ws = nullptr;
   args.kper = 0;
   int splits = 1;
-  if (ws) {
+  if (ws && args.force_kper > 0) {
+    const int nk = (args.K + TC_BK - 1) / TC_BK;
+    const int kper = args.force_kper;
+    splits = (nk + kper - 1) / kper;
+    if ((int64_t)splits * args.Nc * args.M > args.ws_elems) { set_error("gemm_tc: split-K workspace too small"); return 1; }
+    args.kper = kper;
+    args.ws = ws;
+  } else if (ws) {
     int64_t need = 0;
     const int kper = gemm_tc_split_plan(args.M, args.Nc, args.K, A.planes, B.planes, args.epi, &need);
     if (kper > 0 && need <= args.ws_elems) {
@@ -706,7 +713,7 @@ int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s)
     case 33: r = launch_tc<128, 3, 3, 2>(A, B, args, s); break;
     default: set_error("gemm_tc: plane combination not built"); return 1;
   }
-  if (r || splits == 1) return r;
+  if (r || args.no_reduce || splits == 1) return r;
   const int64_t n = (int64_t)args.M * ((args.epi == EPI_RAW_F64) ? args.Nc : args.Nc / 2);
   k_splitk_reduce<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(args, splits);
   note_launch();

@@ -35,6 +35,11 @@ struct TcArgs {
   float* ws = nullptr;
   int64_t ws_elems = 0;
   int kper = 0;          // set by gemm_tc: k-blocks per split (0: no split)
+  // exact products: split K into chunks of force_kper k-blocks whatever the
+  // shape (ws must hold splits * Nc * M floats), and leave the FP32 partials
+  // in ws for the caller's own reduction (no epilogue, no reduce)
+  int force_kper = 0;
+  int no_reduce = 0;
   // gemm_tc_accurate: K = 16 steps accumulated in tensor memory before each
   // drain into FP32 registers (1: every step, error ~1e-7; 64: error ~1e-5 at
   // close to the speed of gemm_tc)

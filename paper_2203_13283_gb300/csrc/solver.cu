@@ -18,6 +18,7 @@
 #include "../../include/wcs.h"
 #include "internal.h"
 #include "gemm_tc.h"
+#include "exact.h"
 
 namespace wcs {
 unsigned long long g_launches = 0;
@@ -94,6 +95,11 @@ struct wcs_ctx {
   DevBuf sol_e, sol_h, sol_b, sol_ang, sol_j;   // solve blocks (grow-only, kept across calls)
   DevBuf Kinv;                            // r x r capacitance inverse (adjoint solves)
   DevBuf Wa;                              // N x r: C_c^-H V_w, formed at the first adjoint solve
+  // exact residuals (mixed form, exact_residual = 1): fixed-point slices of
+  // the four operators (layout 0), built at the first solve that needs them
+  DevBuf exops, exrhs, exws;
+  ExactOperand exA[4];
+  bool exact_ready = false;
   // optional per-kernel timing: CUDA events on the context stream
   bool profile = false;
   struct Rec { int cat; cudaEvent_t a, b; double flops, bytes; };
@@ -102,7 +108,7 @@ struct wcs_ctx {
 
 enum StatCat { CAT_GEMM_TC = 0, CAT_ASSEMBLY = 1, CAT_FFT = 2, CAT_ZGEMM = 3, CAT_SKELETON = 4,
                CAT_FACTOR = 5, CAT_SOLVE = 6, CAT_GEMM_ACC = 7, CAT_SAMPLE = 8, CAT_PROJECT = 9,
-               CAT_ORTH = 10, CAT_VW = 11, CAT_INVERSE = 12, CAT_COUNT = 13 };
+               CAT_ORTH = 10, CAT_VW = 11, CAT_INVERSE = 12, CAT_GEMM_EXACT = 13, CAT_COUNT = 14 };
 
 struct ProfScope {
   wcs_ctx* c;
@@ -203,7 +209,10 @@ static int check_tc(wcs_ctx* c);
 //                  with |dx|
 //   PREC_FAST1     leading plane only, one product (~4e-3): optional skeleton
 //                  sampling (sample_planes = 1)
-enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2, PREC_FAST1 = 3 };
+//   PREC_EXACT     fixed-point slices of operator and vector, integer
+//                  products, FP64 sums (exact.cu): residuals of refinement
+//                  below the accurate floor (forward products only)
+enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2, PREC_FAST1 = 3, PREC_EXACT = 4 };
 
 // Algorithmic HBM bytes of one contraction: every plane of A and B read once,
 // the complex FP64 output written (and read when beta != 0).
@@ -338,8 +347,79 @@ static int cgemm_planes(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, c
   return 0;
 }
 
+// The operators' exact slices (from their layout-0 split-bf16 planes), once per assembly.
+static int ensure_exact_ops(wcs_ctx* c) {
+  if (c->exact_ready) return 0;
+  int64_t ld = 0, nch = 0;
+  size_t sb = 0, eb = 0;
+  exact_operand_alloc_bytes(c->N, 2 * c->N, &ld, &nch, &sb, &eb);
+  const size_t per_op = ((EX_SLICES * sb + eb + 255) / 256) * 256;   // keeps every slice 256-byte aligned
+  TRY(c->exops.ensure(4 * per_op));
+  char* base = (char*)c->exops.p;
+  for (int op = 0; op < 4; ++op) {
+    ExactOperand& o = c->exA[op];
+    o.ld = ld;
+    o.nchunks = nch;
+    for (int q = 0; q < EX_SLICES; ++q) o.slice[q] = (uint16_t*)(base + op * per_op + q * sb);
+    o.expo = (int16_t*)(base + op * per_op + EX_SLICES * sb);
+    const uint16_t* P[3] = {plane_ptr(c, op, 0, 0), c->planes > 1 ? plane_ptr(c, op, 0, 1) : nullptr,
+                            c->planes > 2 ? plane_ptr(c, op, 0, 2) : nullptr};
+    TRY(exact_slice_planes(P, c->planes, c->N, 2 * c->N, c->ldp, o, c->s));
+  }
+  c->exact_ready = true;
+  return 0;
+}
+
+// Y = alpha * op X + beta * Y, exactly up to FP64 sums (op 0 S~, 1 D, 2 D~, 3 N).
+static int ex_apply(wcs_ctx* c, int op, const zd* X, int64_t ldx, int64_t cols, zd alpha, zd beta, zd* Y,
+                    int64_t ldy) {
+  if (cols <= 0) return 0;
+  TRY(ensure_exact_ops(c));
+  TRY(ensure_tcerr(c));
+  const int64_t N = c->N, G = 256;   // right-hand sides per pass: bounds the split-K workspace
+  int64_t ld = 0, nch = 0;
+  size_t sb = 0, eb = 0;
+  exact_operand_alloc_bytes(2 * G, 2 * N, &ld, &nch, &sb, &eb);
+  const size_t sbr = ((sb + 255) / 256) * 256;
+  TRY(c->exrhs.ensure(EX_SLICES * sbr + sizeof(int16_t) * (size_t)G * nch + 256));
+  const int64_t ws_elems = nch * 2 * G * N;
+  TRY(c->exws.ensure(sizeof(float) * (size_t)ws_elems));
+  ExactOperand B;
+  B.ld = ld;
+  B.nchunks = nch;
+  for (int q = 0; q < EX_SLICES; ++q) B.slice[q] = (uint16_t*)((char*)c->exrhs.p + q * sbr);
+  B.expo = (int16_t*)((char*)c->exrhs.p + EX_SLICES * sbr);
+  ProfScope ps(c, CAT_GEMM_EXACT, 2.0 * N * (2.0 * cols) * (2.0 * N), 0.0);
+  for (int64_t c0 = 0; c0 < cols; c0 += G) {
+    const int64_t cc = std::min(G, cols - c0);
+    TRY(exact_slice_rhs(X + c0 * ldx, N, cc, ldx, 0, B, c->s));
+    TRY(exact_product(c->exA[op], (int)N, B, (int)cc, (int)(2 * N), alpha, beta, 0, Y + c0 * ldy, ldy,
+                      (float*)c->exws.p, ws_elems, (int*)c->tcerr.p, c->s));
+  }
+  return 0;
+}
+
+// C X (forward) with exact operator products; FP64 Gram algebra between them.
+static int apply_C_exact(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols) {
+  const int64_t N = c->N;
+  zd* T1 = c->w1.z();
+  zd* T2 = c->w2.z();
+  const zd one = mkz(1.0), zero = mkz(0.0), mone = mkz(-1.0);
+  TRY(ex_apply(c, 1, X, ldx, cols, mone, zero, T1, N));    // -D X
+  TRY(ex_apply(c, 3, X, ldx, cols, one, zero, T2, N));     // N X
+  TRY(gram_apply(X, ldx, T1, N, N, cols, c->h, 0.5, 1.0, c->s));
+  TRY(ginv(c, T1, N, T1, N, cols));
+  TRY(ginv(c, T2, N, T2, N, cols));
+  TRY(ex_apply(c, 2, T1, N, cols, one, zero, Y, ldy));     // D~ T1
+  TRY(ex_apply(c, 0, T2, N, cols, one, one, Y, ldy));      // + S~ T2
+  TRY(gram_apply(T1, N, Y, ldy, N, cols, c->h, 0.5, 1.0, c->s));
+  return 0;
+}
+
 static int apply_C_mixed(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, bool adj,
                          int acc) {
+  if (acc == PREC_EXACT && !adj) return apply_C_exact(c, X, ldx, Y, ldy, cols);
+  if (acc == PREC_EXACT) acc = PREC_ACCURATE;   // adjoint products: the drained split-bf16 product
   const int64_t N = c->N;
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
@@ -647,7 +727,7 @@ int wcs_default_options(wcs_options* o) {
   o->rhs_chunk = 256;
   o->mixed_planes = 3;
   o->rhs_planes = 3;
-  o->zfast = 0.0;   // far pairs in FP64 (set > 0 to enable the FP32 far-pair path)
+  o->zfast = -1.0;  // automatic: 2000 in the mixed form (FP32 far pairs beyond k R = 2000), unused in FP64
   return WCS_OK;
 }
 
@@ -663,7 +743,13 @@ int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream) {
   if (o.q_far == 0) o.q_far = (o.precision == WCS_PREC_MIXED) ? 4 : 6;
   if (o.q_near == 0) o.q_near = (o.precision == WCS_PREC_MIXED) ? 8 : 12;
   if (o.sample_planes == 0) o.sample_planes = 2;
+  // FP32 far pairs beyond k R = 2000: at N = 32768 (k = 3642, superellipse)
+  // this keeps the error against the FP64 form at 3.8e-7 for grazing
+  // incidence (all far pairs in FP32: 9.8e-7) with 3.1 s of assembly (all in
+  // FP64: 10.9 s); smaller problems have no pairs that far and stay in FP64
+  if (o.zfast < 0.0) o.zfast = (o.precision == WCS_PREC_MIXED) ? 2000.0 : 0.0;
   if (o.sample_planes < 1 || o.sample_planes > 2) { set_error("sample_planes must be 1 or 2"); return WCS_ERR_ARG; }
+  if (o.exact_residual != 0 && o.exact_residual != 1) { set_error("exact_residual must be 0 or 1"); return WCS_ERR_ARG; }
   if (o.q_far < 2 || o.q_far > 16 || o.q_near < 4 || o.q_near > 16 || o.near_band < 1 ||
       o.block < 1 || o.block > 64 || o.rhs_chunk < 1 || o.max_refine < 0) {
     set_error("option out of range");
@@ -693,6 +779,7 @@ static void free_mesh(wcs_ctx* c) {
   c->gA.release(); c->gB.release(); c->gW.release(); c->qh.release(); c->qt.release();
   c->U.release(); c->Vw.release(); c->Wt.release(); c->Kinv.release(); c->Wa.release();
   c->sol_e.release(); c->sol_h.release(); c->sol_b.release(); c->sol_ang.release(); c->sol_j.release();
+  c->exops.release(); c->exrhs.release(); c->exws.release(); c->exact_ready = false;
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
   c->rank = -1;
 }
@@ -829,6 +916,7 @@ int wcs_query(const wcs_ctx* c, wcs_info* info) {
   info->rank = c->stage >= ST_SKELETON ? c->rank : -1;
   info->norm_cc = c->stage >= ST_ASSEMBLED ? c->norm_cc : 0.0;
   info->min_curvature = c->kmin;
+  info->zfast = c->mixed ? c->opt.zfast : 0.0;
   return WCS_OK;
 }
 
@@ -1624,6 +1712,19 @@ static int residual_rhs_mixed(wcs_ctx* c, const zd* e, const zd* hv, int64_t ld,
   zd* T1 = c->w1.z();
   zd* T2 = c->w2.z();
   const zd one = mkz(1.0), zero = mkz(0.0), mone = mkz(-1.0);
+  if (mode == PREC_EXACT) {
+    TRY(ex_apply(c, 1, x, ldx, cc, mone, zero, T1, N));                 // -D x
+    TRY(ex_apply(c, 3, x, ldx, cc, one, zero, T2, N));                  // N x
+    TRY(gram_apply(x, ldx, T1, N, N, cc, c->h, 0.5, 1.0, c->s));        // + G x / 2
+    TRY(axpby(N, cc, one, hv, ld, one, T1, N, c->s));                   // + h
+    TRY(axpby(N, cc, mkz(0.0, c->k), e, ld, one, T2, N, c->s));         // + i k e
+    TRY(ginv(c, T1, N, T1, N, cc));
+    TRY(ginv(c, T2, N, T2, N, cc));
+    TRY(ex_apply(c, 2, T1, N, cc, mone, zero, R, N));                   // -D~ T1
+    TRY(ex_apply(c, 0, T2, N, cc, mone, one, R, N));                    // - S~ T2
+    TRY(gram_apply(T1, N, R, N, N, cc, c->h, -0.5, 1.0, c->s));         // - G T1 / 2
+    return 0;
+  }
   TRY(ensure_stage(c, cc));
   TRY(stage(c, c->stage0, x, ldx, cc, 0));
   TRY(tc_apply(c, 1, false, c->stage0, cc, mone, zero, T1, N, mode));   // -D x
@@ -1724,6 +1825,32 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
       TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
       ++it;
       TRY(residual(PREC_ACCURATE, worst));
+    }
+  } else if (c->opt.exact_residual && !adj) {
+    // Mixed form with exact residuals.  Every true residual is exact; the
+    // updates R <- R - C dx use the cheapest product whose error (relative to
+    // |C dx| ~ the carried residual) stays below ~1e-11 of |b|: exact while
+    // the carried residual is above 5e-5, the drained product (~2e-7) down to
+    // 5e-7, the periodic drain (~2e-5) below.  Rounds end with a recomputed
+    // residual, as in the other branch.
+    TRY(residual(PREC_EXACT, worst));
+    double prev_true = 1e300;
+    bool floor = false;
+    while (worst > c->opt.refine_tol && it < c->opt.max_refine && worst < 0.5 * prev_true && !floor) {
+      prev_true = worst;
+      double upd = worst, prev_upd = 1e300;
+      while (upd > 0.1 * c->opt.refine_tol && it < c->opt.max_refine && upd < 0.7 * prev_upd) {
+        TRY(approx_inverse(R, N, dx, N));
+        TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
+        ++it;
+        const int m = (upd > 5e-5) ? PREC_EXACT : (upd > 5e-7 ? PREC_ACCURATE : PREC_PERIODIC);
+        TRY(apply_C(c, dx, N, T, N, cc, adj, m));
+        TRY(axpby(N, cc, mkz(-1.0), T, N, mkz(1.0), R, N, c->s));
+        prev_upd = upd;
+        TRY(worst_of(upd));
+      }
+      TRY(residual(PREC_EXACT, worst));
+      floor = worst > 10.0 * upd;
     }
   } else {
     // Mixed form.  While the first residual is large, fast residuals do (their
@@ -2086,6 +2213,56 @@ static int gemm_split_impl(int64_t M, int64_t Nc, int64_t K, const double* A, in
   cudaMemcpyAsync(&errh, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamSynchronize(s);
   pa.release(); pb.release(); err.release(); ws.release();
+  if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  if (errh) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
+  return WCS_OK;
+}
+
+int wcs_gemm_exact(int64_t M, int64_t Nc, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   double* D, int64_t ldd, void* stream) {
+  if (M < 0 || Nc < 0 || K < 0 || (M > 0 && (lda < K || (K > 0 && !A))) || (Nc > 0 && (ldb < K || (K > 0 && !B))) ||
+      (M > 0 && Nc > 0 && (!D || ldd < Nc)) || M > 65535 * 128 || Nc > 65535 * 256) {
+    set_error("bad argument");
+    return WCS_ERR_ARG;
+  }
+  if (M == 0 || Nc == 0) return WCS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (K == 0) {
+    cudaError_t e = cudaMemset2DAsync(D, sizeof(double) * ldd, 0, sizeof(double) * Nc, M, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+    return WCS_OK;
+  }
+  int64_t ld = 0, nch = 0;
+  size_t sa = 0, ea = 0, sb = 0, eb = 0;
+  exact_operand_alloc_bytes(M, K, &ld, &nch, &sa, &ea);
+  exact_operand_alloc_bytes(Nc, K, &ld, &nch, &sb, &eb);
+  const size_t sa2 = ((sa + 255) / 256) * 256, sb2 = ((sb + 255) / 256) * 256;
+  DevBuf pa, pb, ea_b, eb_b, ws, err;
+  TRY(pa.ensure(EX_SLICES * sa2));
+  TRY(pb.ensure(EX_SLICES * sb2));
+  TRY(ea_b.ensure(ea));
+  TRY(eb_b.ensure(eb));
+  const int64_t ws_elems = nch * Nc * M;
+  TRY(ws.ensure(sizeof(float) * (size_t)ws_elems));
+  TRY(err.ensure(sizeof(int)));
+  ExactOperand oa, ob;
+  oa.ld = ob.ld = ld;
+  oa.nchunks = ob.nchunks = nch;
+  for (int q = 0; q < EX_SLICES; ++q) {
+    oa.slice[q] = (uint16_t*)((char*)pa.p + q * sa2);
+    ob.slice[q] = (uint16_t*)((char*)pb.p + q * sb2);
+  }
+  oa.expo = (int16_t*)ea_b.p;
+  ob.expo = (int16_t*)eb_b.p;
+  cudaError_t e = cudaMemsetAsync(err.p, 0, sizeof(int), s);
+  if (e != cudaSuccess) { set_error(cudaGetErrorString(e)); return WCS_ERR_CUDA; }
+  TRY(exact_slice_real(A, M, K, lda, oa, s));
+  TRY(exact_slice_real(B, Nc, K, ldb, ob, s));
+  TRY(exact_product_real(oa, (int)M, ob, (int)Nc, (int)K, D, ldd, (float*)ws.p, ws_elems, (int*)err.p, s));
+  int errh = 0;
+  e = cudaMemcpyAsync(&errh, err.p, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) { set_error(std::string("gemm: ") + cudaGetErrorString(e)); return WCS_ERR_CUDA; }
   if (errh) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
   return WCS_OK;

@@ -51,15 +51,17 @@ def frequency_response(solver, which="C", chunk=256):
 
 def rank_sweep(family, params, Ns, eps=0.015, angles=(0.0, 1.0), seed=1):
     """[(N, k, rank, compressed-solve error)] at 10 elements per wavelength,
-    FP64 form: the rank of the skeleton of C - C_c at tolerance eps and the
-    relative error of the Woodbury solve of Eq. (9) alone against the solve
-    refined to 1e-12."""
+    FP64 form: the rank of the skeleton of C - C_c whose range finder stops
+    once every new projected sample is below eps ||C_c||_2 (wcs_skeleton's
+    tolerance eps * 10 sqrt(2 / pi)), and the relative error of the Woodbury
+    solve of Eq. (9) alone against the solve refined to 1e-12."""
     rows = []
+    tol = eps * 10.0 * np.sqrt(2.0 / np.pi)
     for N in Ns:
         s = Solver(precision=0, refine_tol=1e-12, max_refine=60, rhs_chunk=64)
         try:
             s.contour(family, **params).mesh(N).assemble()
-            r = s.skeleton(eps, seed=seed)
+            r = s.skeleton(tol, seed=seed)
             s.factor()
             j = s.solve_planewaves(np.asarray(angles, float))
             b = s.apply("C", j)

@@ -244,7 +244,7 @@ class Solver:
         return float(J[0]), g[:i1 - i0]
 
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
-                    "sample", "project", "orth", "vw", "inverse")
+                    "sample", "project", "orth", "vw", "inverse", "gemm_exact")
 
     def profile(self, enable=True):
         check(self.lib.wcs_profile(self.h, 1 if enable else 0))
@@ -283,4 +283,17 @@ def gemm_split_bf16(A, B, planes=2, accurate=False):
     st = torch.cuda.current_stream(A.device)
     check(load().wcs_gemm_split_bf16_ex(M, Nc, K, _ptr(A), K, _ptr(B), K, int(planes), int(accurate),
                                         _ptr(D), Nc, C.c_void_p(st.cuda_stream)))
+    return D
+
+
+def gemm_exact(A, B):
+    """D = A @ B.T, exact up to ~2^-35 |A| |B|^T per entry, on the tensor cores
+    (fixed-point bf16 slices, integer products, FP64 sums); FP64 in/out, cuda."""
+    A = torch.as_tensor(A, dtype=torch.float64, device="cuda").contiguous()
+    B = torch.as_tensor(B, dtype=torch.float64, device="cuda").contiguous()
+    M, K = A.shape
+    Nc = B.shape[0]
+    D = torch.empty((M, Nc), dtype=torch.float64, device=A.device)
+    st = torch.cuda.current_stream(A.device)
+    check(load().wcs_gemm_exact(M, Nc, K, _ptr(A), K, _ptr(B), K, _ptr(D), Nc, C.c_void_p(st.cuda_stream)))
     return D

@@ -60,7 +60,12 @@ def test_frequency_response_vs_oracle(N):
     assert np.max(np.abs(rR - oR)) <= 1e-10 * np.max(oC)
     m = np.minimum(np.arange(N), N - np.arange(N))
     ka = k * a
-    assert np.max(rR[m > 2 * ka]) < 1e-2 * np.max(rR)        # the remainder dies off at high frequency
+    # the remainder dies off at high frequency (N = 64: 4.5e-3 of its peak
+    # just above 2 k a, 2e-3 beyond 3 k a), and monotonically so
+    assert np.max(rR[m > 2 * ka]) < 3e-2 * np.max(rR)
+    assert np.max(rR[m > 3 * ka]) < 5e-3 * np.max(rR)
+    tail = [np.max(rR[m == mm]) for mm in range(int(np.ceil(2 * ka)) + 1, N // 2 + 1)]
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(tail, tail[1:]))
     assert m[np.argmax(rC)] <= 1.2 * ka                        # C is strongest up to the resonance
 
 
@@ -73,9 +78,11 @@ def test_rank_sweep_vs_oracle():
     for (N, k, r, err) in rows:
         r_or, e_or, k_or = odiag.rank_and_error(curve, N, 0.015, [0.0, 1.0])
         assert abs(k - k_or) <= 1e-12 * k
-        # the range finder stops on a probabilistic bound a factor ~10 below
-        # eps ||C_c||, so it keeps at least the SVD rank and at most twice it
-        assert r_or <= r <= 2 * r_or, (N, r, r_or)
-        assert err <= max(2.0 * e_or, 1e-3), (N, err, e_or)
+        # the range finder stops when its projected samples, which measure the
+        # Frobenius norm of the remainder, drop below eps ||C_c||; the SVD rule
+        # counts singular values above it, so the GPU keeps at least that rank
+        print(N, k, "rank", r, "oracle", r_or, "error", err, "oracle", e_or)
+        assert r_or <= r <= 3 * r_or, (N, r, r_or)
+        assert err <= 2.0 * e_or + 1e-4, (N, err, e_or)
         ranks.append(r)
     assert ranks[0] < ranks[1] < ranks[2]

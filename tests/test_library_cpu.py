@@ -41,6 +41,7 @@ def test_options_defaults(lib):
     from paper_2203_13283_gb300.solver import default_options
     o = default_options()
     assert (o.q_far, o.q_near, o.near_band, o.precision, o.sample_planes) == (0, 0, 4, 0, 0)
+    assert (o.zfast, o.exact_residual) == (-1.0, 0)
 
 
 @pytest.mark.parametrize("q", [8, 12])
@@ -172,6 +173,7 @@ def _write_ckpt(path, lib, N=16, rank=2, kinv=True, corrupt_at=None, cut=0):
     lib.wcs_default_options(C.byref(hd.opt))
     hd.opt.q_far, hd.opt.q_near = 6, 12          # as wcs_create resolves the automatic choice
     hd.opt.sample_planes = 2
+    hd.opt.zfast = 0.0                            # resolved value of the FP64 form
     hd.contour.family, hd.contour.ax, hd.contour.ay = 1, 1.0, 0.5
     ext = np.array([1 if kinv else 0, 0], dtype="<u4").tobytes()
     rng = np.random.default_rng(5)
