@@ -82,11 +82,12 @@ typedef struct wcs_options {
                          products (default 0 = 2; 1 = one product per pass, ~4e-3 relative) */
   int exact_residual; /* mixed form: 1 = evaluate the refinement residual b - C x exactly (fixed-
                          point slices of the operator planes and of x, integer products on the
-                         tensor cores, FP64 sums), so refinement reaches refine_tol down to ~1e-12
-                         against the stored operator; costs 5 bf16 slices of each operator (4 x 10
-                         N^2 bytes, built at the first such solve) and about one extra C x per 1024
-                         right-hand sides and round.  0 (default): residuals in split-bf16 with FP32
-                         accumulation, which floor near 3e-7. */
+                         tensor cores, float-float and FP64 sums; see wcs_gemm_exact), so
+                         refinement reaches refine_tol down to ~1e-11 against the stored operator;
+                         costs 6 bf16 slices of each operator (96 N^2 bytes in all, built at the
+                         first such solve).  Adjoint solves keep the drained residual.  0
+                         (default): residuals in split-bf16 with FP32 accumulation, which floor
+                         near 3e-7. */
 } wcs_options;
 
 typedef struct wcs_info {
@@ -268,16 +269,20 @@ int wcs_contour_perturb(wcs_ctx* ctx, int M, const double* alpha, const double* 
  * context's current contour: grad[m] = dJ/d alpha_m (m < M), grad[M+m-1] =
  * dJ/d beta_m (m = 1..M).  N and k stay fixed; the mesh, k~ (Sec. III) and
  * everything else follow the contour.  Adjoint route: one forward solve
- * (Eq. 5 through Eq. 9), one adjoint solve lam = C^-H E^H F, then per
- * parameter 2 Re sum_b [F_b^H dE j_b + lam_b^H (db_b - dC j_b)] with dE, db, dC
- * central differences (step delta; delta <= 0 means 1e-6) of the far-field
- * map, the preconditioned right-hand side and C, assembled in FP64 at the
- * perturbed contours.  angles_host (B), phi_host (nphi) and the outputs
- * J_host (1) and grad_host (2M) are host memory.  Needs a factored context;
- * device scratch about 2 N^2 complex FP64 plus a few N x B blocks.
- * Synchronises the stream.  Errors: WCS_ERR_STATE, WCS_ERR_ARG,
- * WCS_ERR_NOT_CONVEX (a perturbed contour), WCS_ERR_NOT_CONVERGED (a solve
- * missed refine_tol; outputs still written). */
+ * (Eq. 5 through Eq. 9), one adjoint solve lam = C^-H E^H F, then
+ * dJ/dp = 2 Re sum_b [F_b^H dE j_b + lam_b^H dR_b] with R = b - C j written
+ * through the four operators (Eq. 5, 6).  The derivatives of S~, D, D~, N
+ * enter as bilinear forms evaluated for all parameters in one pass over the
+ * far element pairs (analytic derivatives of the Hankel kernels with respect
+ * to the points, normals and k~, contracted with the motion of the
+ * arc-length mesh); the near band (log-singular rules), the mesh motion, the
+ * right-hand sides and the far-field map are central differences with step
+ * delta (delta <= 0 means 1e-6), all O(N) per parameter.  angles_host (B),
+ * phi_host (nphi) and the outputs J_host (1) and grad_host (2M) are host
+ * memory.  Needs a factored context; device scratch 4 N^2 complex FP64 plus
+ * a few N x B blocks.  Synchronises the stream.  Errors: WCS_ERR_STATE,
+ * WCS_ERR_ARG, WCS_ERR_NOT_CONVEX (a perturbed contour), WCS_ERR_NOT_CONVERGED
+ * (a solve missed refine_tol; outputs still written). */
 int wcs_shape_gradient(wcs_ctx* ctx, int64_t B, const double* angles_host, int nphi, const double* phi_host,
                        int M, double delta, double* J_host, double* grad_host);
 
@@ -289,6 +294,20 @@ int wcs_shape_gradient(wcs_ctx* ctx, int64_t B, const double* angles_host, int n
 int wcs_shape_gradient_range(wcs_ctx* ctx, int64_t B, const double* angles_host, int nphi,
                              const double* phi_host, int M, double delta, int i0, int i1, double* J_host,
                              double* grad_host);
+
+/* Shape derivatives of one Galerkin operator as bilinear forms:
+ * out[2 (i - i0) + {0, 1}] = (re, im) of sum_b u_b^H (dX / dp_i) v_b for the
+ * shape parameters i0 <= i < i1 of wcs_contour_perturb (numbering as in
+ * wcs_shape_gradient), X = op (0 S~, 1 D, 2 D~, 3 N; Sec. II Eq. 4 and the
+ * S~ of Eq. 5).  The derivative moves the arc-length mesh with the contour
+ * at fixed N and k (k~ follows a = L / 2 pi).  Far pairs: one pass of the
+ * analytic derivative kernel; near band: central differences (step delta,
+ * <= 0 means 1e-6).  u_dev, v_dev: complex FP64 device blocks N x B
+ * (column-major, ld >= N).  Needs wcs_assemble.  Device scratch 4 N^2
+ * complex FP64; synchronises.  The terms of wcs_shape_gradient's adjoint
+ * formula, offered separately for checks and for other objectives. */
+int wcs_shape_operator_forms(wcs_ctx* ctx, int op, int64_t B, const double* u_dev, const double* v_dev, int64_t ld,
+                             int M, double delta, int i0, int i1, double* out_host);
 
 /* Solve C x = b for B general right-hand sides b of Eq. (5)'s preconditioned
  * system (device, complex FP64, column-major N x B, ldb, ldx >= N): Eq. (9)
@@ -371,16 +390,52 @@ int wcs_gemm_split_bf16_noalloc(int64_t M, int64_t Nc, int64_t K, const double* 
  * operator products of the refinement residual (Eq. 5 with C of Eq. 6) in
  * the mixed form's exact_residual mode use the same method: each row is cut
  * into chunks of 1024 K values, each chunk scaled by a power of two so its
- * entries lie in (-1, 1) and written as five 7-bit fixed-point slices (bf16
- * integers); the 15 slice pairs of combined order < 5 are multiplied with
+ * entries lie in (-1, 1) and written as six 7-bit fixed-point slices (bf16
+ * integers); the 21 slice pairs of combined order < 6 are multiplied with
  * one split of K per chunk, where the FP32 accumulation of integer products
- * below 2^24 is exact, and the scaled partials are summed in FP64.  Error per
- * entry <= ~2^-35 (|A| |B|^T) (the slices' truncation), independent of K.
- * Allocates about 10 (M + Nc) K + 4 (K / 1024) M Nc bytes; ordered on
- * `stream`; synchronises.  Errors: WCS_ERR_ARG, WCS_ERR_OOM, WCS_ERR_CUDA,
+ * below 2^24 is exact, and the scaled partials are summed in float-float and
+ * FP64.  Error of D_ij <= 2^-40 sum_k (cmax_A |B_jk| + |A_ik| cmax_B +
+ * cmax_A cmax_B), cmax the largest magnitude in the value's chunk of 1024;
+ * for data of similar size within each chunk that is ~2^-40 (|A| |B|^T),
+ * independent of K.  Values must lie within 2^-100 .. 2^100.  Allocates
+ * about 12 (M + Nc) K + 4 (K / 1024) M Nc bytes; ordered on `stream`;
+ * synchronises.  Errors: WCS_ERR_ARG, WCS_ERR_OOM, WCS_ERR_CUDA,
  * WCS_ERR_TIMEOUT (a bounded device wait expired). */
 int wcs_gemm_exact(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda, const double* B_dev,
                    int64_t ldb, double* D_dev, int64_t ldd, void* stream);
+
+/* Per-contour outcome of wcs_batch_solve_fourier. */
+typedef struct wcs_batch_stats {
+  int status;         /* wcs_status of the contour's setup and solve (WCS_ERR_NOT_CONVERGED: solved,
+                         refine_tol missed) */
+  int rank;           /* skeleton rank */
+  int refine_steps;   /* iterative-refinement steps of its solve */
+  double rel_residual;/* max over its columns of ||b - C x|| / ||b|| */
+  double setup_s;     /* wall-clock seconds of mesh, assembly, skeleton and factor */
+  double solve_s;     /* wall-clock seconds of the plane-wave solve, including the copy to the host */
+  int worker;         /* host worker (stream) that took it */
+} wcs_batch_stats;
+
+/* Batched form: `count` contours solved for the same B plane waves (Sec. V:
+ * any number of right-hand sides per contour; here also many contours).
+ * Contour c has radial function rho(theta) = sum_{m<nf} cos_c[c nf + m]
+ * cos(m theta) + sin_c[c nf + m] sin(m theta) (sin_c may be NULL), N[c]
+ * elements and wavenumber k[c] (<= 0: 10 elements per wavelength), with the
+ * options `opt` (NULL: defaults).  Each contour is meshed, assembled,
+ * skeletonised at tolerance tol with rank cap N[c] / rank_div (rank_div <= 0:
+ * no cap; WCS_ERR_RANK_CAP is accepted), factored and solved; its current
+ * (N[c] x B complex FP64, column-major, ld N[c]) is written to host memory at
+ * j_host + 2 B sum_{c' < c} N[c'] doubles.  `workers` (1..8) host threads
+ * each drive one context on its own stream and take contours from a queue
+ * ordered by decreasing N, so the GPU overlaps one contour's setup with
+ * another's solve and device memory holds at most `workers` contours.  stats
+ * (optional, count entries) receives each contour's outcome.  Returns the
+ * first hard error (after finishing the other contours), else
+ * WCS_ERR_NOT_CONVERGED if a contour missed refine_tol, else WCS_OK.
+ * Errors before any work: WCS_ERR_ARG. */
+int wcs_batch_solve_fourier(const wcs_options* opt, int count, int nf, const double* cos_c, const double* sin_c,
+                            const int64_t* N, const double* k, int64_t B, const double* angles_host, double tol,
+                            int rank_div, uint64_t seed, int workers, double* j_host, wcs_batch_stats* stats);
 
 /* Number of CUDA kernel launches the library has issued in this process. */
 uint64_t wcs_launch_count(void);
@@ -389,13 +444,15 @@ uint64_t wcs_launch_count(void);
  * each instrumented launch (enable != 0 turns it on; off by default). */
 int wcs_profile(wcs_ctx* ctx, int enable);
 
-/* Sum the recorded launches by category (synchronises): out_host gets 14 x 4
+/* Sum the recorded launches by category (synchronises): out_host gets 15 x 4
  * doubles {launches, total ms, algorithmic work, bytes} for the categories, in
  * order: tensor-core contraction (work = useful real flops 2 M Nc K of the
  * complex product), assembly (work = far point pairs), FFT circulant applies
  * (bytes), FP64 GEMM, skeleton, factor, solve, drained tensor-core
  * contraction, skeleton sampling, projection, orthonormalisation, V_w,
- * capacitance inverse, exact contraction (work = useful flops, as the first).
+ * capacitance inverse, exact contraction (work = useful flops, as the first),
+ * FP32 far-pair assembly kernel (work = far point pairs of its tiles; the
+ * assembly category then counts the FP64 kernel over the other tiles).
  * reset != 0 clears the records. */
 int wcs_profile_read(wcs_ctx* ctx, int reset, double* out_host);
 

@@ -39,6 +39,11 @@ class SolveInfo(C.Structure):
                 ("history", C.c_double * WCS_HISTORY)]
 
 
+class BatchStats(C.Structure):
+    _fields_ = [("status", C.c_int), ("rank", C.c_int), ("refine_steps", C.c_int), ("rel_residual", C.c_double),
+                ("setup_s", C.c_double), ("solve_s", C.c_double), ("worker", C.c_int)]
+
+
 # exported symbol -> (restype, argtypes); mirrors include/wcs.h
 P, I, I64, D, U64 = C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_uint64
 SIGNATURES = {
@@ -82,6 +87,9 @@ SIGNATURES = {
     "wcs_quadrature_tables": (I, [I, P]),
     "wcs_fma_rate": (I, [I, I, P, C.POINTER(C.c_double)]),
     "wcs_gemm_exact": (I, [I64, I64, I64, P, I64, P, I64, P, I64, P]),
+    "wcs_shape_operator_forms": (I, [P, I, I64, P, P, I64, I, C.c_double, I, I, P]),
+    "wcs_batch_solve_fourier": (I, [C.POINTER(Options), I, I, P, P, P, P, I64, P, C.c_double, I, U64, I, P,
+                                    P]),
 }
 
 _lib = None

@@ -19,6 +19,7 @@
 
 #include <complex>
 #include <cstring>
+#include <vector>
 
 #include "hankel.cuh"
 #include "internal.h"
@@ -544,11 +545,11 @@ __global__ void k_entries(AsmArgs A, int64_t count, const int64_t* rows, const i
   for (int op = 0; op < 4; ++op) out4[op * count + t] = sum[op];
 }
 
-// Coefficient tables of hankel01_asymptotic_fixed for this run's k~ = k (1 + i t)
-static int upload_asymptotic(const AsmArgs& A) {
-  AsymCoef h;
+// Coefficient tables of hankel01_asymptotic_fixed for k~ = k (1 + i t)
+void fill_asymptotic(KtPair& kp) {
+  AsymCoef& h = kp.asym;
   std::memset(&h, 0, sizeof(h));
-  const std::complex<double> c1 = std::complex<double>(1.0, 0.0) / std::complex<double>(1.0, A.ktp.t);
+  const std::complex<double> c1 = std::complex<double>(1.0, 0.0) / std::complex<double>(1.0, kp.t);
   for (int nu = 0; nu < 2; ++nu) {
     double a = 1.0;
     std::complex<double> cp = 1.0;   // c1^k
@@ -564,11 +565,9 @@ static int upload_asymptotic(const AsmArgs& A) {
       else { h.ro[nu][m] = sg * a; h.co[nu][m] = mkz(b.real(), b.imag()); }
     }
   }
-  return cudaMemcpyToSymbol(c_asym, &h, sizeof(h)) == cudaSuccess ? 0 : 3;
 }
 
 static int upload_rules(const AsmArgs& A) {
-  if (upload_asymptotic(A)) return 3;
   double xf[16], wf[16], xn[16], wn[16];
   gauss_legendre01(A.q_far, xf, wf);
   gauss_legendre01(A.q_near, xn, wn);
@@ -734,7 +733,7 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_
   }
 }
 
-int assemble_planes(const AsmArgs& A, cudaStream_t s) {
+int assemble_planes(const AsmArgs& A, cudaStream_t s, cudaEvent_t* mid, int64_t* fp64_tiles, int64_t* tiles) {
   if (upload_rules(A) || upload_hankel_coefficients()) { set_error("uploading quadrature rules failed"); return 3; }
   const size_t smem = sizeof(zd) * 4 * TILE * TILE;
   cudaFuncSetAttribute(k_assemble<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -746,10 +745,20 @@ int assemble_planes(const AsmArgs& A, cudaStream_t s) {
   dim3 grid((unsigned)nt, (unsigned)nt);
   k_assemble_fast<<<grid, ASM_THREADS, 0, s>>>(A, nt, flag);
   note_launch();
+  if (mid) { cudaEventRecord(mid[0], s); cudaEventRecord(mid[1], s); }
   AsmArgs B = A;
   B.tile_flags = flag;
   k_assemble<1><<<grid, ASM_THREADS, smem, s>>>(B);
   note_launch();
+  if (fp64_tiles) {   // the tiles that took the FP64 kernel (for the work count of each kernel)
+    std::vector<uint8_t> h((size_t)(nt * nt));
+    cudaMemcpyAsync(h.data(), flag, h.size(), cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    int64_t n = 0;
+    for (uint8_t v : h) n += v;
+    *fp64_tiles = n;
+    *tiles = nt * nt;
+  }
   cudaStreamSynchronize(s);
   cudaFree(flag);
   cudaError_t err = cudaGetLastError();
@@ -816,6 +825,224 @@ int assemble_entries(const AsmArgs& A, int64_t count, const int64_t* rows, const
   note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("entries: ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+
+// ---------------------------------------------------------------------------
+// Shape derivatives of the Galerkin entries (differentiation of Sec. II Eq. 4
+// with respect to the contour).  A far entry is h^2 sum w_p w_r phi_a phi_b K
+// over point pairs; moving the contour moves the points (r, r'), turns the
+// normals (n, n'), changes k~ through a = L / 2 pi (Sec. III) and scales h^2.
+// For the forms T = sum_ij W_ij X_ij the derivative with respect to any
+// parameter is therefore
+//   sum_P (dT/dr_P . dr_P/dp + dT/dn_P . dn_P/dp) + dT/dk~ dk~/dp + 2 (dh/h) T_h2,
+// and one pass over the point pairs gathers dT/dr_P, dT/dn_P (per point),
+// dT/dk~ and T_h2 for all parameters at once.  Kernel derivatives, with
+// d = r - r', R = |d|, d^ = d / R, g = d.n' / R, z = kappa R,
+// H1'(z) = H0(z) - H1(z) / z:
+//   S~ = (i/4) H0(k~R):      d/dd = -(i/4) k~ H1 d^,   d/dk~ = -(i/4) R H1
+//   D  = (i k/4) H1(kR) g:   d/dd = (i k/4) [k H1' g d^ + H1 (n' - g d^) / R],
+//                            d/dn' = (i k/4) H1 d^
+//   D~ likewise with k~, and d/dk~ = (i/4) k~ R H0(k~R) g
+//   N  (Maue form): [s_a s_b - k^2 h^2 (n.n') phi_a phi_b] (i/4) H0(kR):
+//                            d/dd = -(i/4) k H1 d^ (both parts),
+//                            d/dn = (i/4) H0 n' and d/dn' = (i/4) H0 n (second part)
+// Only far pairs are differentiated here; the near band keeps its singular
+// product rules and is differenced (shape_near_forms).
+// ---------------------------------------------------------------------------
+constexpr int SH_E = 8;       // element rows per block
+constexpr int SH_F = 256;     // element columns per block (8 warps x 32 lanes)
+
+__device__ __forceinline__ zd i4(double s, zd H) { return mkz(-0.25 * s * H.y, 0.25 * s * H.x); }   // (i/4) s H
+
+__global__ void __launch_bounds__(256) k_shape_far(ShapeArgs S) {
+  const AsmArgs& A = S.A;
+  const int64_t N = A.N;
+  const int q = A.q_far;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e0 = (int64_t)blockIdx.y * SH_E;
+  const int64_t f = (int64_t)blockIdx.x * SH_F + warp * 32 + lane;
+  const bool fvalid = f < N;
+  __shared__ double rowacc[SH_E][16][8];
+  __shared__ double red[8][4];
+  for (int t = threadIdx.x; t < SH_E * 16 * 8; t += blockDim.x) (&rowacc[0][0][0])[t] = 0.0;
+  __syncthreads();
+  const double h = A.h, k = A.k, h2 = h * h, kk2h2 = k * k * h2;
+  const zd kt = A.kt;
+  double sc[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t f1 = fvalid ? (f + 1) % N : 0;
+  for (int r = 0; r < q; ++r) {
+    double col[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    const int64_t iq = fvalid ? f * q + r : 0;
+    const double xq = A.far.x[iq], yq = A.far.y[iq], nxq = A.far.nx[iq], nyq = A.far.ny[iq];
+    const double eta = c_xf[r], wr = c_wf[r];
+    const double pb0 = 1.0 - eta, pb1 = eta;
+    for (int el = 0; el < SH_E; ++el) {
+      const int64_t e = e0 + el;
+      const bool ok = fvalid && e < N && periodic_dist(e, f, N) > A.near_band;
+      // per operator: sum_b W(e + a, f + b) phi_b(eta_r) for a = 0, 1; and for
+      // the derivative part of N, sum_b s_b W_N(e + a, f + b)
+      zd cw[4][2], cwd[2];
+      if (ok) {
+        const int64_t ea[2] = {e, (e + 1) % N};
+#pragma unroll
+        for (int X = 0; X < 4; ++X)
+#pragma unroll
+          for (int a = 0; a < 2; ++a) {
+            const zd w0 = S.W[X][ea[a] * N + f], w1 = S.W[X][ea[a] * N + f1];
+            cw[X][a] = pb0 * w0 + pb1 * w1;
+            if (X == 3) cwd[a] = w1 - w0;          // s_0 = -1, s_1 = +1
+          }
+      } else {
+#pragma unroll
+        for (int X = 0; X < 4; ++X) cw[X][0] = cw[X][1] = mkz(0.0);
+        cwd[0] = cwd[1] = mkz(0.0);
+      }
+      for (int p = 0; p < q; ++p) {
+        double rowc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (ok) {
+          const int64_t ip = e * q + p;
+          const double xp = A.far.x[ip], yp = A.far.y[ip], nxp = A.far.nx[ip], nyp = A.far.ny[ip];
+          const double xi = c_xf[p], ww = c_wf[p] * wr;
+          const double pa0 = 1.0 - xi, pa1 = xi;
+          // point-pair coefficients of the four operators
+          const zd cS = (h2 * ww) * (pa0 * cw[0][0] + pa1 * cw[0][1]);
+          const zd cD = (h2 * ww) * (pa0 * cw[1][0] + pa1 * cw[1][1]);
+          const zd cDt = (h2 * ww) * (pa0 * cw[2][0] + pa1 * cw[2][1]);
+          const zd cNn = (-kk2h2 * ww) * (pa0 * cw[3][0] + pa1 * cw[3][1]);
+          const zd cNd = ww * (cwd[1] - cwd[0]);   // s_a: -1 for a = 0, +1 for a = 1
+          const double dx = xp - xq, dy = yp - yq;
+          const double R = sqrt(dx * dx + dy * dy), iR = 1.0 / R;
+          const double ux = dx * iR, uy = dy * iR;
+          const double g = (dx * nxq + dy * nyq) * iR;
+          const double nd = nxp * nxq + nyp * nyq;
+          Hankel01 Hk, Ht;
+          hankel_k_kt(A, R, Hk, Ht);
+          const double z = k * R;
+          const zd zt = kt * R;
+          const zd H1pk = Hk.H0 - (1.0 / z) * Hk.H1;              // H1'(kR)
+          const zd H1pt = Ht.H0 - zdiv(Ht.H1, zt);               // H1'(k~R)
+          // S~
+          const zd aS = cS * i4(-1.0, kt * Ht.H1);               // coefficient of d^ in dK/dd
+          // D: (ik/4)[k H1' g d^ + H1 (n' - g d^)/R]
+          const zd Dd = cD * i4(k, k * g * H1pk - (g * iR) * Hk.H1);   // along d^
+          const zd Dn = cD * i4(k * iR, Hk.H1);                  // along n'
+          // D~
+          const zd Dtd = cDt * (i4(1.0, kt) * (kt * g * H1pt - (g * iR) * Ht.H1));
+          const zd Dtn = cDt * (i4(iR, kt) * Ht.H1);
+          // N
+          const zd cN = cNd + nd * cNn;
+          const zd aN = cN * i4(-k, Hk.H1);
+          const zd uR = aS + Dd + Dtd + aN;                       // dT/dd = uR d^ + (Dn + Dtn) n'
+          const zd un = Dn + Dtn;
+          const double gdx[4] = {uR.x * ux + un.x * nxq, uR.y * ux + un.y * nxq,
+                                 uR.x * uy + un.x * nyq, uR.y * uy + un.y * nyq};
+          // dT/dn' = (D + D~ terms) d^ + N: cNn (i/4) H0 n ; dT/dn = cNn (i/4) H0 n'
+          const zd vq = cD * i4(k, Hk.H1) + cDt * (i4(1.0, kt) * Ht.H1);
+          const zd wn = cNn * i4(1.0, Hk.H0);
+          // d/dk~: S~ and D~
+          const zd dkt = cS * i4(-R, Ht.H1) + cDt * (i4(R, kt) * (Ht.H0 * g));
+          // h^2-scaled part of T (all of S~, D, D~ and the k^2 h^2 part of N)
+          const zd val = cS * i4(1.0, Ht.H0) + cD * i4(k * g, Hk.H1) + cDt * (i4(g, kt) * Ht.H1) +
+                         nd * (cNn * i4(1.0, Hk.H0));
+          rowc[0] = gdx[0]; rowc[1] = gdx[1]; rowc[2] = gdx[2]; rowc[3] = gdx[3];
+          rowc[4] = wn.x * nxq; rowc[5] = wn.y * nxq; rowc[6] = wn.x * nyq; rowc[7] = wn.y * nyq;
+          col[0] -= gdx[0]; col[1] -= gdx[1]; col[2] -= gdx[2]; col[3] -= gdx[3];
+          col[4] += vq.x * ux + wn.x * nxp;
+          col[5] += vq.y * ux + wn.y * nxp;
+          col[6] += vq.x * uy + wn.x * nyp;
+          col[7] += vq.y * uy + wn.y * nyp;
+          sc[0] += dkt.x; sc[1] += dkt.y; sc[2] += val.x; sc[3] += val.y;
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          for (int o = 16; o > 0; o >>= 1) rowc[i] += __shfl_xor_sync(0xffffffffu, rowc[i], o);
+        if (lane == 0) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) atomicAdd(&rowacc[el][p][i], rowc[i]);
+        }
+      }
+    }
+    if (fvalid) {
+      double* gr = S.Gr + 4 * iq;
+      double* gn = S.Gn + 4 * iq;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) { atomicAdd(gr + i, col[i]); atomicAdd(gn + i, col[4 + i]); }
+    }
+  }
+  // block sums of the scalars, then the row accumulators
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    for (int o = 16; o > 0; o >>= 1) sc[i] += __shfl_xor_sync(0xffffffffu, sc[i], o);
+  if (lane == 0)
+    for (int i = 0; i < 4; ++i) red[warp][i] = sc[i];
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w][threadIdx.x];
+    atomicAdd(S.scal + threadIdx.x, t);
+  }
+  for (int t = threadIdx.x; t < SH_E * q * 8; t += blockDim.x) {
+    const int el = t / (q * 8), rem = t - el * q * 8, p = rem / 8, i = rem - p * 8;
+    const int64_t e = e0 + el;
+    if (e < N) atomicAdd((i < 4 ? S.Gr : S.Gn) + 4 * (e * q + p) + (i & 3), rowacc[el][p][i]);
+  }
+}
+
+// Near band: sum over element pairs with distance <= near_band of the W-weighted
+// pair integrals of A's geometry (one thread per pair, block partial sums).
+__global__ void __launch_bounds__(128) k_shape_near(AsmArgs A, const zd* W0, const zd* W1, const zd* W2,
+                                                    const zd* W3, double* part) {
+  const int64_t N = A.N;
+  const int span = 2 * A.near_band + 1;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  zd acc = mkz(0.0);
+  if (t < N * span) {
+    const int64_t e = t / span;
+    const int64_t f = ((e + (t - e * span) - A.near_band) % N + N) % N;
+    PairOut o;
+    pair_integrals(A, e, f, o);
+    const zd* W[4] = {W0, W1, W2, W3};
+#pragma unroll
+    for (int X = 0; X < 4; ++X)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) acc += W[X][((e + a) % N) * N + (f + b) % N] * o.v[X][a * 2 + b];
+  }
+  __shared__ double red[2][4];
+  double v[2] = {acc.x, acc.y};
+  for (int i = 0; i < 2; ++i)
+    for (int o2 = 16; o2 > 0; o2 >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o2);
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = v[0]; red[1][threadIdx.x >> 5] = v[1]; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = red[0][0] + red[0][1] + red[0][2] + red[0][3];
+    part[2 * blockIdx.x + 1] = red[1][0] + red[1][1] + red[1][2] + red[1][3];
+  }
+}
+
+int shape_far_forms(const ShapeArgs& a, cudaStream_t s) {
+  if (a.A.q_far > 16) { set_error("shape derivative: q_far <= 16"); return 1; }
+  if (upload_rules(a.A)) { set_error("uploading quadrature rules failed"); return 3; }
+  dim3 grid((unsigned)((a.A.N + SH_F - 1) / SH_F), (unsigned)((a.A.N + SH_E - 1) / SH_E));
+  k_shape_far<<<grid, 256, 0, s>>>(a);
+  note_launch();
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("shape (far): ") + cudaGetErrorString(err)); return 3; }
+  return 0;
+}
+
+int shape_near_forms(const AsmArgs& A, const zd* const* W, double* part, int* nparts, cudaStream_t s) {
+  if (upload_rules(A)) { set_error("uploading quadrature rules failed"); return 3; }
+  const int64_t n = A.N * (2 * A.near_band + 1);
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  k_shape_near<<<blocks, 128, 0, s>>>(A, W[0], W[1], W[2], W[3], part);
+  note_launch();
+  *nparts = (int)blocks;
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess) { set_error(std::string("shape (near): ") + cudaGetErrorString(err)); return 3; }
   return 0;
 }
 

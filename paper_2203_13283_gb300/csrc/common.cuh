@@ -18,12 +18,24 @@ struct __align__(8) zf {
   float x, y;
 };
 
+// Coefficients of the fixed-length Hankel expansion for x >= 20 (see
+// hankel01_asymptotic_fixed): (-1)^m a_k(nu) for the real argument and
+// (-1)^m a_k(nu) (1 + i t)^-k for x (1 + i t), k = 2m (re, ce) and 2m + 1 (ro, co).
+constexpr int ASYM_M = 10;
+struct AsymCoef {
+  double re[2][ASYM_M], ro[2][ASYM_M];
+  zd ce[2][ASYM_M], co[2][ASYM_M];
+};
+
 // k~ = k (1 + i t): per-run constants for evaluating both wavenumbers of a
-// point pair from one real argument x = k R.
+// point pair from one real argument x = k R.  Passed to the kernels by value
+// (not as __constant__ data), so contexts on different streams can assemble
+// different contours at the same time.
 struct KtPair {
   double t = 0.0;
   zd c1;   // 1 / (1 + i t)
   zd c2;   // (1 + i t)^(-1/2), principal branch
+  AsymCoef asym;
 };
 
 
@@ -74,11 +86,12 @@ __host__ __device__ __forceinline__ void zfmas(zd& acc, double s, zd b) {
 // Error plumbing shared by the host-side translation units.
 // ---------------------------------------------------------------------------
 #ifndef __CUDACC_RTC__
+#include <atomic>
 #include <string>
 namespace wcs {
 void set_error(const std::string& msg);
-// host-side count of kernel launches issued by the library
-extern unsigned long long g_launches;
+// host-side count of kernel launches issued by the library (any thread)
+extern std::atomic<unsigned long long> g_launches;
 inline void note_launch() { ++g_launches; }
 }
 #define WCS_CUDA_TRY(expr)                                                        \

@@ -15,12 +15,18 @@
 //    over one chunk of 1024 terms it stays below 2^24, where the tensor core's
 //    FP32 accumulation is exact, so the contraction runs split-K with one
 //    split per chunk and returns exact integer partial sums;
-//  * the partials are scaled by 2^(E_A + E_B - 7(s+t+2)) and summed in FP64.
+//  * the partials are scaled by 2^(E_A + E_B) and summed over the chunks in
+//    float-float (an exact integer below 2^24 times a power of two is exact
+//    in FP32, and TwoSum keeps ~48 bits of the running sum on the FP32 pipe,
+//    which runs at 64 times the FP64 rate of this GPU); each pair's sum, times
+//    2^-7(s+t+2), is added to the FP64 output.
 //
-// Pairs with s + t < EX_LEVELS are formed (15 of the 25); the dropped ones are
-// below 2^-49 of the chunk scales.  The operator's slices describe its
-// split-bf16 planes (the operator of the rest of the mixed form) to ~2^-36 of
-// each chunk's largest entry.
+// Pairs with s + t < EX_LEVELS are formed (21 of the 36); the dropped ones are
+// below 2^-56 of the chunk scales.  The operator's slices describe its
+// split-bf16 planes (the operator of the rest of the mixed form) to ~2^-42 of
+// each chunk's largest entry.  With five slices the chunk that holds the
+// log-singular diagonal left its ~500 far entries at ~2^-35 of the diagonal,
+// a residual floor near 7e-10 at N = 32768; six put it below 1e-11.
 #include <cuda_bf16.h>
 
 #include "gemm_tc.h"
@@ -33,6 +39,23 @@ __device__ __forceinline__ uint16_t int_bf16(double v) {
 }
 
 constexpr int EX_PER = EX_CHUNK / 256;   // values per thread of a 256-thread block
+
+// 2^e as a float for the normal range (e in [-126, 127]); scaled partials of
+// the residual products stay far inside it (operator entries and currents
+// between ~1e-12 and ~1e3, partial sums below 2^24)
+__device__ __forceinline__ float pow2f(int e) {
+  e = max(-126, min(127, e));
+  return __int_as_float((e + 127) << 23);
+}
+
+// (hi, lo) += v with TwoSum (Knuth): hi + lo carries the sum to ~2^-48
+__device__ __forceinline__ void ff_acc(float2& a, float v) {
+  const float s = a.x + v;
+  const float bb = s - a.x;
+  const float err = (a.x - (s - bb)) + (v - bb);
+  a.x = s;
+  a.y += err;
+}
 
 // Exponent E of a chunk held by the block (EX_PER values per thread):
 // max |v| < 2^E, or 0 for an all-zero chunk.  Written to *expo by thread 0.
@@ -154,11 +177,12 @@ __global__ void k_exact_reduce_real(const float* __restrict__ P, int splits, int
   if (t >= (int64_t)M * Nc) return;
   const int i = (int)(t % M), j = (int)(t / M);
   const int64_t plane = (int64_t)Nc * M;
-  double acc = 0.0;
+  float2 sum = make_float2(0.f, 0.f);
   for (int c = 0; c < splits; ++c) {
-    const int e = (int)EA[(int64_t)i * nchunks + c] + (int)EB[(int64_t)j * nchunks + c];
-    acc += ldexp((double)P[c * plane + (int64_t)j * M + i], e);
+    const float sc = pow2f((int)EA[(int64_t)i * nchunks + c] + (int)EB[(int64_t)j * nchunks + c]);
+    ff_acc(sum, P[c * plane + (int64_t)j * M + i] * sc);
   }
+  const double acc = (double)sum.x + (double)sum.y;
   double* o = D + (int64_t)i * ldd + j;
   *o = first ? weight * acc : *o + weight * acc;
 }
@@ -173,13 +197,14 @@ __global__ void k_exact_reduce(const float* __restrict__ P, int splits, int M, i
   if (t >= (int64_t)M * ncols) return;
   const int i = (int)(t % M), j = (int)(t / M);
   const int64_t plane = (int64_t)2 * ncols * M;
-  double re = 0.0, im = 0.0;
+  float2 re = make_float2(0.f, 0.f), im = make_float2(0.f, 0.f);
   for (int c = 0; c < splits; ++c) {
-    const int e = (int)EA[(int64_t)i * nchunks + c] + (int)EB[(int64_t)j * nchunks + c];
-    re += ldexp((double)P[c * plane + (int64_t)(2 * j) * M + i], e);
-    im += ldexp((double)P[c * plane + (int64_t)(2 * j + 1) * M + i], e);
+    const float sc = pow2f((int)EA[(int64_t)i * nchunks + c] + (int)EB[(int64_t)j * nchunks + c]);
+    ff_acc(re, P[c * plane + (int64_t)(2 * j) * M + i] * sc);
+    ff_acc(im, P[c * plane + (int64_t)(2 * j + 1) * M + i] * sc);
   }
-  zd p = mkz(weight * re, weight * (conj_out ? -im : im));
+  const double dre = (double)re.x + (double)re.y, dim = (double)im.x + (double)im.y;
+  zd p = mkz(weight * dre, weight * (conj_out ? -dim : dim));
   p = alpha * p;
   zd* o = out + (int64_t)j * ldo + i;
   if (first) {

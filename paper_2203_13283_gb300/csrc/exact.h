@@ -5,16 +5,16 @@
 
 namespace wcs {
 
-constexpr int EX_SLICES = 5;      // 7-bit slices per value (36 bits below each chunk's scale)
+constexpr int EX_SLICES = 6;      // 7-bit slices per value (43 bits below each chunk's scale)
 constexpr int EX_CHUNK = 1024;    // K elements per scale chunk and per split of the contraction
-constexpr int EX_LEVELS = 5;      // slice pairs (s, t) with s + t < EX_LEVELS are formed
+constexpr int EX_LEVELS = 6;      // slice pairs (s, t) with s + t < EX_LEVELS are formed
 
 // A K-major real operand (rows x K, leading dimension ld) as EX_SLICES bf16
 // planes of integers plus a power-of-two exponent per (row, chunk); for a
 // right-hand block the exponent is stored once per complex column (rows 2j
 // and 2j + 1 of the real view share it).
 struct ExactOperand {
-  uint16_t* slice[EX_SLICES] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  uint16_t* slice[EX_SLICES] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   int64_t ld = 0;
   int16_t* expo = nullptr;
   int64_t nchunks = 0;

@@ -317,26 +317,20 @@ __device__ inline void hankel01_asymptotic_pair(double x, const KtPair& kp, Hank
 // orders and both arguments.  Even and odd powers of u = 1/x are summed by
 // Horner's rule in u^2 with per-run coefficient tables: (-1)^m a_k(nu) for the
 // real argument and (-1)^m a_k(nu) (1 + i t)^-k for x (1 + i t).
-constexpr int ASYM_M = 10;
-struct AsymCoef {
-  double re[2][ASYM_M], ro[2][ASYM_M];   // order nu, k = 2m and k = 2m + 1
-  zd ce[2][ASYM_M], co[2][ASYM_M];
-};
-__constant__ AsymCoef c_asym;
 
 __device__ inline void hankel01_asymptotic_fixed(double x, const KtPair& kp, Hankel01& hk, Hankel01& ht) {
   const double u = 1.0 / x, u2 = u * u;
   zd S[2], St[2];
 #pragma unroll
   for (int nu = 0; nu < 2; ++nu) {
-    double e = c_asym.re[nu][ASYM_M - 1], o = c_asym.ro[nu][ASYM_M - 1];
-    zd ce = c_asym.ce[nu][ASYM_M - 1], co = c_asym.co[nu][ASYM_M - 1];
+    double e = kp.asym.re[nu][ASYM_M - 1], o = kp.asym.ro[nu][ASYM_M - 1];
+    zd ce = kp.asym.ce[nu][ASYM_M - 1], co = kp.asym.co[nu][ASYM_M - 1];
 #pragma unroll
     for (int m = ASYM_M - 2; m >= 0; --m) {
-      e = fma(e, u2, c_asym.re[nu][m]);
-      o = fma(o, u2, c_asym.ro[nu][m]);
-      ce = mkz(fma(ce.x, u2, c_asym.ce[nu][m].x), fma(ce.y, u2, c_asym.ce[nu][m].y));
-      co = mkz(fma(co.x, u2, c_asym.co[nu][m].x), fma(co.y, u2, c_asym.co[nu][m].y));
+      e = fma(e, u2, kp.asym.re[nu][m]);
+      o = fma(o, u2, kp.asym.ro[nu][m]);
+      ce = mkz(fma(ce.x, u2, kp.asym.ce[nu][m].x), fma(ce.y, u2, kp.asym.ce[nu][m].y));
+      co = mkz(fma(co.x, u2, kp.asym.co[nu][m].x), fma(co.y, u2, kp.asym.co[nu][m].y));
     }
     S[nu] = mkz(e, u * o);                             // sum a_k (i u)^k
     St[nu] = mkz(ce.x - u * co.y, ce.y + u * co.x);    // sum a_k (i u / (1 + i t))^k

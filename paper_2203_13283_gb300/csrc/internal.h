@@ -128,9 +128,15 @@ struct AsmArgs {
   FastConsts fk;
   const uint8_t* tile_flags = nullptr;           // mixed tile kernel: only flagged tiles
 };
+// Fill kp.asym for kp.t (host).
+void fill_asymptotic(KtPair& kp);
 int assemble_dense(const AsmArgs& a, cudaStream_t s);
-// Mixed form: the same operators written as split-bf16 planes (see AsmArgs).
-int assemble_planes(const AsmArgs& a, cudaStream_t s);
+// Mixed form: the same operators written as split-bf16 planes (see AsmArgs):
+// the FP32 far-pair kernel over the tiles it can take, then the FP64 kernel
+// over the rest.  mid (optional, two events) is recorded between the two;
+// fp64_tiles and tiles (optional) receive the tile counts.
+int assemble_planes(const AsmArgs& a, cudaStream_t s, cudaEvent_t* mid = nullptr, int64_t* fp64_tiles = nullptr,
+                    int64_t* tiles = nullptr);
 // FP32 offset tables of the far points relative to element centres.
 int far_offsets(const Points& far, const double* cx, const double* cy, int64_t N, int q, float* ox,
                 float* oy, float* nxf, float* nyf, float* nxl, float* nyl, float* oxl, float* oyl, float4* cff,
@@ -140,6 +146,24 @@ int assemble_circle_row(const AsmArgs& a, cudaStream_t s);
 // Sampled entries (row, col) of the four operators, computed point-wise.
 int assemble_entries(const AsmArgs& a, int64_t count, const int64_t* rows, const int64_t* cols,
                      zd* out4, cudaStream_t s);
+
+// Shape derivative of bilinear forms (the gradient of Sec. II-V with respect
+// to the contour).  W[X] (row-major N x N, X = S~, D, D~, N) are node-pair
+// coefficients; the forms are T = sum_X sum_ij W[X]_ij X_ij.
+struct ShapeArgs {
+  AsmArgs A;                       // base geometry, rules and wavenumbers (far tables used)
+  const zd* W[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* Gr = nullptr;            // per far point: dT/dr (complex x, complex y) as 4 doubles
+  double* Gn = nullptr;            // per far point: dT/dn (4 doubles)
+  double* scal = nullptr;          // dT/dk~ (2 doubles), sum of the h^2-scaled far terms (2 doubles)
+};
+// Far element pairs (periodic distance > near_band), one pass for every
+// parameter: accumulates Gr, Gn (zeroed by the caller) and scal.
+int shape_far_forms(const ShapeArgs& a, cudaStream_t s);
+// sum over near element pairs (distance <= near_band) of sum_X sum_ab
+// W[X](e + a, f + b) X_ef,ab with the pair integrals of A's geometry;
+// part holds per-block partial sums (2 doubles each), *nparts set.
+int shape_near_forms(const AsmArgs& A, const zd* const* W, double* part, int* nparts, cudaStream_t s);
 
 // ---------------------------------------------------------------- FFT
 struct FFTPlan {

@@ -21,7 +21,7 @@
 #include "exact.h"
 
 namespace wcs {
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
 static thread_local std::string g_err;
 void set_error(const std::string& m) { g_err = m; }
 }  // namespace wcs
@@ -108,7 +108,8 @@ struct wcs_ctx {
 
 enum StatCat { CAT_GEMM_TC = 0, CAT_ASSEMBLY = 1, CAT_FFT = 2, CAT_ZGEMM = 3, CAT_SKELETON = 4,
                CAT_FACTOR = 5, CAT_SOLVE = 6, CAT_GEMM_ACC = 7, CAT_SAMPLE = 8, CAT_PROJECT = 9,
-               CAT_ORTH = 10, CAT_VW = 11, CAT_INVERSE = 12, CAT_GEMM_EXACT = 13, CAT_COUNT = 14 };
+               CAT_ORTH = 10, CAT_VW = 11, CAT_INVERSE = 12, CAT_GEMM_EXACT = 13, CAT_ASSEMBLY_FAST = 14,
+               CAT_COUNT = 15 };
 
 struct ProfScope {
   wcs_ctx* c;
@@ -780,6 +781,7 @@ static void free_mesh(wcs_ctx* c) {
   c->U.release(); c->Vw.release(); c->Wt.release(); c->Kinv.release(); c->Wa.release();
   c->sol_e.release(); c->sol_h.release(); c->sol_b.release(); c->sol_ang.release(); c->sol_j.release();
   c->exops.release(); c->exrhs.release(); c->exws.release(); c->exact_ready = false;
+  c->first_accurate = false;   // per-contour refinement state
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
   c->rank = -1;
 }
@@ -937,6 +939,7 @@ static AsmArgs asm_args(wcs_ctx* c, bool circle) {
     A.ktp.t = t;
     A.ktp.c1 = mkz(c1.real(), c1.imag());
     A.ktp.c2 = mkz(c2.real(), c2.imag());
+    fill_asymptotic(A.ktp);
   }
   return A;
 }
@@ -1049,8 +1052,24 @@ int wcs_assemble(wcs_ctx* c) {
     // zfast <= 0: every pair in FP64 (the FP32 path is off)
     A.zfast = (c->opt.zfast > 0.0) ? c->opt.zfast + 2.0 * c->k * c->h : 1e300;
     set_fast_consts(A);
-    ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * qf * qf, 0.0);   // units: far point pairs
-    TRY(assemble_planes(A, c->s));
+    if (!c->profile) {
+      TRY(assemble_planes(A, c->s));
+    } else {
+      // two records: the FP32 far-pair kernel, then the FP64 kernel over the
+      // remaining tiles; units: element pairs of each kernel's tiles x q_far^2
+      cudaEvent_t a0, mid[2], b0;
+      cudaEventCreate(&a0);
+      cudaEventCreate(&mid[0]);
+      cudaEventCreate(&mid[1]);
+      cudaEventCreate(&b0);
+      cudaEventRecord(a0, c->s);
+      int64_t nf64 = 0, nt = 0;
+      TRY(assemble_planes(A, c->s, mid, &nf64, &nt));
+      cudaEventRecord(b0, c->s);
+      const double per_tile = 33.0 * 33.0 * qf * qf;
+      c->recs.push_back({CAT_ASSEMBLY_FAST, a0, mid[0], per_tile * (double)(nt - nf64), 0.0});
+      c->recs.push_back({CAT_ASSEMBLY, mid[1], b0, per_tile * (double)nf64, 0.0});
+    }
   }
   // circle: first rows -> eigenvalues
   TRY(c->mu.ensure(sizeof(zd) * 6 * N));
@@ -1961,18 +1980,156 @@ int wcs_solve_adjoint(wcs_ctx* c, int64_t B, const double* b, int64_t ldb, doubl
   return solve_general(c, B, b, ldb, x, ldx, info, true);
 }
 
-// Far-field shape gradient by the adjoint route.  With j = C^-1 b (forward
-// solve), F = E j and lam = C^-H E^H F (one adjoint solve),
-//   dJ/dp = 2 Re sum_b [F_b^H (dE j_b) + lam_b^H (db_b - dC j_b)],
-// where dE, db and dC are central differences of the far-field map, the
-// preconditioned right-hand side (Eq. 5) and C (Eq. 6) at fixed j: each
-// parameter re-meshes and re-assembles the perturbed contour (FP64 form) in
-// a scratch context, applies it to j and reduces on the device.
+}  // extern "C"
+
+// ---------------------------------------------------------------- shape derivatives
+// The contour of parameter i at offset d: the current contour with the Fourier
+// perturbation alpha_i (i < M) or beta_{i-M+1} moved by d.
+static Contour perturbed_contour(const Contour& base, int M, int i, double d) {
+  Contour k = base;
+  if (k.np == 0)
+    for (int m = 0; m < kMaxPerturb; ++m) { k.pc[m] = 0.0; k.ps[m] = 0.0; }
+  k.np = std::max(k.np, M + 1);
+  if (i < M) k.pc[i] += d;
+  else k.ps[i - M + 1] += d;
+  return k;
+}
+
 struct CtxGuard {
   wcs_ctx* t = nullptr;
   ~CtxGuard() { if (t) wcs_destroy(t); }
 };
 
+// Scratch context meshing the perturbed contours (geometry only, no assembly):
+// same N, k and quadrature rules as c.
+static int make_scratch(wcs_ctx* c, CtxGuard& g) {
+  wcs_options o = c->opt;
+  o.precision = WCS_PREC_FP64;
+  o.zfast = 0.0;
+  o.exact_residual = 0;
+  return wcs_create(&g.t, &o, (void*)c->s);
+}
+
+__global__ void k_geo_dot(const double* Gr, const double* Gn, Points pp, Points pm, int64_t n, double* part) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double re = 0.0, im = 0.0;
+  if (t < n) {
+    const double dr[2] = {pp.x[t] - pm.x[t], pp.y[t] - pm.y[t]};
+    const double dn[2] = {pp.nx[t] - pm.nx[t], pp.ny[t] - pm.ny[t]};
+    const double* g = Gr + 4 * t;
+    const double* h = Gn + 4 * t;
+    re = g[0] * dr[0] + g[2] * dr[1] + h[0] * dn[0] + h[2] * dn[1];
+    im = g[1] * dr[0] + g[3] * dr[1] + h[1] * dn[0] + h[3] * dn[1];
+  }
+  __shared__ double red[2][8];
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = re; red[1][threadIdx.x >> 5] = im; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int w = 0; w < 8; ++w) { a += red[0][w]; b += red[1][w]; }
+    part[2 * blockIdx.x] = a;
+    part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Sum of `n` partial (re, im) pairs in device memory, in a fixed order on the host.
+static int sum_parts(wcs_ctx* c, const double* part, int n, zd* out) {
+  std::vector<double> h(2 * (size_t)n);
+  cudaMemcpyAsync(h.data(), part, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, c->s);
+  TRY(sync(c));
+  double re = 0.0, im = 0.0;
+  for (int i = 0; i < n; ++i) { re += h[2 * i]; im += h[2 * i + 1]; }
+  *out = mkz(re, im);
+  return 0;
+}
+
+// One assembled operator applied alone: Y = op X or op^H X (0 S~, 1 D, 2 D~, 3 N).
+static int op_apply(wcs_ctx* c, int which, bool adj, const zd* X, int64_t ldx, int64_t cols, zd* Y, int64_t ldy) {
+  if (!c->mixed) {
+    const zd* ops[4] = {c->S, c->D, c->Dt, c->Nk};
+    return zgemm(c->N, cols, c->N, mkz(1.0), op_view(ops[which], c->ld, adj), blk(X, ldx), mkz(0.0), Y, ldy, c->s);
+  }
+  TRY(ensure_stage(c, cols));
+  TRY(stage(c, c->stage0, X, ldx, cols, adj ? 1 : 0));
+  return tc_apply(c, which, adj, c->stage0, cols, mkz(1.0), mkz(0.0), Y, ldy, PREC_ACCURATE);
+}
+
+// T_i = sum_X sum_ij W[X]_ij dX_ij / dp_i for parameters i0 <= i < i1 (out[i - i0]):
+// the far pairs by the one-pass derivative kernel (per-point gradients
+// contracted with the point motion, k~ and h^2 terms), the near band by
+// central differences of its pair integrals (step delta).  W: four row-major
+// N x N device matrices (S~, D, D~, N); points move as the arc-length mesh
+// of the perturbed contour dictates (central differences of the geometry).
+// Scratch contexts tp, tm are meshed on the perturbed contours of parameter i
+// and left there for the caller (per_param is called after each).
+template <typename F>
+static int shape_forms(wcs_ctx* c, const zd* const* W, int M, int i0, int i1, double delta, zd* out, CtxGuard& tp,
+                       CtxGuard& tm, F per_param) {
+  const int64_t N = c->N, nq = N * c->opt.q_far;
+  DevBuf gr, gn, sc, part;
+  TRY(gr.ensure(sizeof(double) * 4 * nq));
+  TRY(gn.ensure(sizeof(double) * 4 * nq));
+  TRY(sc.ensure(sizeof(double) * 4));
+  const int64_t nblk_geo = (nq + 255) / 256, nblk_near = (N * (2 * c->opt.near_band + 1) + 127) / 128;
+  TRY(part.ensure(sizeof(double) * 2 * std::max(nblk_geo, nblk_near)));
+  cudaMemsetAsync(gr.p, 0, gr.bytes, c->s);
+  cudaMemsetAsync(gn.p, 0, gn.bytes, c->s);
+  cudaMemsetAsync(sc.p, 0, sc.bytes, c->s);
+  ShapeArgs sa;
+  sa.A = asm_args(c, false);
+  for (int X = 0; X < 4; ++X) sa.W[X] = W[X];
+  sa.Gr = gr.d();
+  sa.Gn = gn.d();
+  sa.scal = sc.d();
+  {
+    ProfScope ps(c, CAT_ASSEMBLY, (double)N * N * c->opt.q_far * c->opt.q_far, 0.0);
+    TRY(shape_far_forms(sa, c->s));
+  }
+  double scal[4];
+  cudaMemcpyAsync(scal, sc.p, sizeof(scal), cudaMemcpyDeviceToHost, c->s);
+  TRY(sync(c));
+  const zd s_kt = mkz(scal[0], scal[1]), s_h2 = mkz(scal[2], scal[3]);
+  for (int i = i0; i < i1; ++i) {
+    TRY(set_contour(tp.t, perturbed_contour(c->contour, M, i, delta)));
+    TRY(wcs_mesh(tp.t, N, c->k));
+    TRY(set_contour(tm.t, perturbed_contour(c->contour, M, i, -delta)));
+    TRY(wcs_mesh(tm.t, N, c->k));
+    zd geo, np_, nm_;
+    k_geo_dot<<<(unsigned)nblk_geo, 256, 0, c->s>>>(gr.d(), gn.d(), tp.t->far, tm.t->far, nq, part.d());
+    note_launch();
+    TRY(sum_parts(c, part.d(), (int)nblk_geo, &geo));
+    int nb = 0;
+    TRY(shape_near_forms(asm_args(tp.t, false), W, part.d(), &nb, c->s));
+    TRY(sum_parts(c, part.d(), nb, &np_));
+    TRY(shape_near_forms(asm_args(tm.t, false), W, part.d(), &nb, c->s));
+    TRY(sum_parts(c, part.d(), nb, &nm_));
+    const double dL = (tp.t->L - tm.t->L) / (2.0 * delta);
+    const zd dkt = (1.0 / (2.0 * delta)) * (tp.t->kt - tm.t->kt);
+    const zd far = (1.0 / (2.0 * delta)) * geo + s_kt * dkt + (2.0 * dL / c->L) * s_h2;
+    const zd near = (1.0 / (2.0 * delta)) * (np_ - nm_);
+    out[i - i0] = far + near;
+    TRY(per_param(i, dL));
+  }
+  return 0;
+}
+
+extern "C" {
+
+// Far-field shape gradient by the adjoint route.  With j = C^-1 b (forward
+// solve), F = E j and lam = C^-H E^H F (one adjoint solve),
+//   dJ/dp = 2 Re sum_b [F_b^H dE j_b + lam_b^H dR_b],  R = b - C j,
+// and R = -(G/2 + D~) q1 - S~ q2 with q1 = G^-1 (h + (G/2 - D) j),
+// q2 = G^-1 (i k e + N j) (Eq. 5 with C of Eq. 6), so with
+// w1 = G^-1 (G/2 + D~)^H lam, w2 = G^-1 S~^H lam and dG = (dL/L) G,
+//   lam^H dR = -lam^H dD~ q1 - lam^H dS~ q2 + w1^H dD j - w2^H dN j
+//              + (dL/L) [-lam^H G q1 / 2 - w1^H G j / 2 + w1^H G q1 + w2^H G q2]
+//              - w1^H dh - i k w2^H de.
+// The operator terms come from shape_forms (one pass over the far pairs for
+// every parameter); dE, de, dh (O(N) per parameter) are central differences.
 int wcs_shape_gradient_range(wcs_ctx* c, int64_t B, const double* angles, int nphi, const double* phi, int M,
                              double delta, int i0, int i1, double* J_out, double* grad) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
@@ -1986,16 +2143,15 @@ int wcs_shape_gradient_range(wcs_ctx* c, int64_t B, const double* angles, int np
   TRY(check_angles(nphi, phi, "shape_gradient (observation angles)"));
   if (!(delta > 0)) delta = 1e-6;
   const int64_t N = c->N;
-  DevBuf j, lam, E, F, G, ang, phd, eb, hb, bb, Y, W, dots;
+  DevBuf j, lam, E, F, G, ang, phd, dots;
   TRY(j.ensure(sizeof(zd) * N * B));
   TRY(lam.ensure(sizeof(zd) * N * B));
   TRY(G.ensure(sizeof(zd) * N * B));
   TRY(E.ensure(sizeof(zd) * N * nphi));
   TRY(F.ensure(sizeof(zd) * nphi * B));
-  TRY(W.ensure(sizeof(zd) * nphi * B));
   TRY(ang.ensure(sizeof(double) * B));
   TRY(phd.ensure(sizeof(double) * nphi));
-  TRY(dots.ensure(sizeof(zd) * 2 * B));
+  TRY(dots.ensure(sizeof(zd) * 4 * B));
   cudaMemcpyAsync(ang.p, angles, sizeof(double) * B, cudaMemcpyHostToDevice, c->s);
   cudaMemcpyAsync(phd.p, phi, sizeof(double) * nphi, cudaMemcpyHostToDevice, c->s);
   // forward: j, F = E j, J
@@ -2007,7 +2163,7 @@ int wcs_shape_gradient_range(wcs_ctx* c, int64_t B, const double* angles, int np
   TRY(farfield_matrix(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, N, c->h, c->k, phd.d(), nphi, E.z(),
                       nphi, c->s));
   TRY(zgemm(nphi, B, N, mkz(1.0), ZView{E.z(), 1, nphi, false}, blk(j.z(), N), mkz(0.0), F.z(), nphi, c->s));
-  std::vector<zd> hd(2 * B);
+  std::vector<zd> hd(4 * B);
   TRY(column_dotc(F.z(), nphi, F.z(), nphi, nphi, B, dots.z(), c->s));
   cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * B, cudaMemcpyDeviceToHost, c->s);
   TRY(sync(c));
@@ -2020,55 +2176,121 @@ int wcs_shape_gradient_range(wcs_ctx* c, int64_t B, const double* angles, int np
   r = solve_general(c, B, G.d(), N, lam.d(), N, &si, true);
   if (r == WCS_ERR_NOT_CONVERGED) status = r;
   else if (r) return r;
-  G.release();
-  // perturbed operators in a scratch FP64 context on the same stream
-  wcs_options o;
-  wcs_default_options(&o);
-  o.precision = WCS_PREC_FP64;
-  CtxGuard guard;
-  TRY(wcs_create(&guard.t, &o, (void*)c->s));
-  wcs_ctx* t = guard.t;
-  TRY(eb.ensure(sizeof(zd) * N * B));
-  TRY(hb.ensure(sizeof(zd) * N * B));
-  TRY(bb.ensure(sizeof(zd) * N * B));
-  TRY(Y.ensure(sizeof(zd) * N * B));
-  for (int i = i0; i < i1; ++i) {
-    zd side[2];
-    for (int sgn = 0; sgn < 2; ++sgn) {
-      Contour k = c->contour;
-      if (k.np == 0) {
-        for (int m = 0; m < kMaxPerturb; ++m) { k.pc[m] = 0.0; k.ps[m] = 0.0; }
-      }
-      k.np = std::max(k.np, M + 1);
-      const double d = sgn == 0 ? delta : -delta;
-      if (i < M) k.pc[i] += d;            // alpha_i
-      else k.ps[i - M + 1] += d;          // beta_{i-M+1}
-      TRY(set_contour(t, k));
-      TRY(wcs_mesh(t, N, c->k));
-      TRY(wcs_assemble(t));
-      TRY(ensure_work(t, B));
-      // R = b(p) - C(p) j
-      TRY(planewave_rhs(t->near, t->quad.wn, t->quad.xn, t->opt.q_near, N, t->h, t->k, ang.d(), (int)B,
-                        eb.z(), hb.z(), N, c->s));
-      TRY(precondition(t, eb.z(), hb.z(), N, bb.z(), N, B, PREC_ACCURATE));
-      TRY(apply_C(t, j.z(), N, Y.z(), N, B, false, PREC_ACCURATE));
-      TRY(axpby(N, B, mkz(1.0), bb.z(), N, mkz(-1.0), Y.z(), N, c->s));
-      TRY(column_dotc(lam.z(), N, Y.z(), N, N, B, dots.z(), c->s));
-      // E(p) j
-      TRY(farfield_matrix(t->near, t->quad.wn, t->quad.xn, t->opt.q_near, N, t->h, t->k, phd.d(), nphi,
-                          E.z(), nphi, c->s));
-      TRY(zgemm(nphi, B, N, mkz(1.0), ZView{E.z(), 1, nphi, false}, blk(j.z(), N), mkz(0.0), W.z(), nphi,
-                c->s));
-      TRY(column_dotc(F.z(), nphi, W.z(), nphi, nphi, B, dots.z() + B, c->s));
-      cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * 2 * B, cudaMemcpyDeviceToHost, c->s);
+  // q1, q2, w1, w2 of the base contour
+  DevBuf eb, hb, q1, q2, w1, w2, T, gq;
+  for (DevBuf* b : {&eb, &hb, &q1, &q2, &w1, &w2, &T, &gq}) TRY(b->ensure(sizeof(zd) * N * B));
+  TRY(planewave_rhs(c->near, c->quad.wn, c->quad.xn, c->opt.q_near, N, c->h, c->k, ang.d(), (int)B, eb.z(), hb.z(),
+                    N, c->s));
+  TRY(op_apply(c, 1, false, j.z(), N, B, T.z(), N));                         // D j
+  TRY(axpby(N, B, mkz(1.0), hb.z(), N, mkz(-1.0), T.z(), N, c->s));         // h - D j
+  TRY(gram_apply(j.z(), N, T.z(), N, N, B, c->h, 0.5, 1.0, c->s));          // + G j / 2
+  TRY(ginv(c, T.z(), N, q1.z(), N, B));
+  TRY(op_apply(c, 3, false, j.z(), N, B, T.z(), N));                         // N j
+  TRY(axpby(N, B, mkz(0.0, c->k), eb.z(), N, mkz(1.0), T.z(), N, c->s));    // + i k e
+  TRY(ginv(c, T.z(), N, q2.z(), N, B));
+  TRY(op_apply(c, 2, true, lam.z(), N, B, T.z(), N));                        // D~^H lam
+  TRY(gram_apply(lam.z(), N, T.z(), N, N, B, c->h, 0.5, 1.0, c->s));        // + G lam / 2
+  TRY(ginv(c, T.z(), N, w1.z(), N, B));
+  TRY(op_apply(c, 0, true, lam.z(), N, B, T.z(), N));                        // S~^H lam
+  TRY(ginv(c, T.z(), N, w2.z(), N, B));
+  // Gram term: -lam^H G q1 / 2 - w1^H G j / 2 + w1^H G q1 + w2^H G q2
+  zd gam = mkz(0.0);
+  {
+    const zd* pairs[4][2] = {{lam.z(), q1.z()}, {w1.z(), j.z()}, {w1.z(), q1.z()}, {w2.z(), q2.z()}};
+    const double wts[4] = {-0.5, -0.5, 1.0, 1.0};
+    for (int t = 0; t < 4; ++t) {
+      TRY(gram_apply(pairs[t][1], N, gq.z(), N, N, B, c->h, 1.0, 0.0, c->s));
+      TRY(column_dotc(pairs[t][0], N, gq.z(), N, N, B, dots.z(), c->s));
+      cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * B, cudaMemcpyDeviceToHost, c->s);
       TRY(sync(c));
-      zd acc = mkz(0.0);
-      for (int64_t b = 0; b < 2 * B; ++b) acc += hd[b];
-      side[sgn] = acc;
+      for (int64_t b = 0; b < B; ++b) gam += wts[t] * hd[b];
     }
-    grad[i - i0] = (side[0].x - side[1].x) / delta;    // 2 Re(t+ - t-) / (2 delta)
   }
+  // node-pair coefficients W (row-major): W_S = -sum conj(lam) q2^T, W_D~ =
+  // -sum conj(lam) q1^T, W_D = sum conj(w1) j^T, W_N = -sum conj(w2) j^T
+  DevBuf Wb;
+  TRY(Wb.ensure(sizeof(zd) * 4 * N * N));
+  const zd* W[4];
+  {
+    const zd* U[4] = {lam.z(), w1.z(), lam.z(), w2.z()};
+    const zd* V[4] = {q2.z(), j.z(), q1.z(), j.z()};
+    const double sgn[4] = {-1.0, 1.0, -1.0, -1.0};
+    for (int X = 0; X < 4; ++X) {
+      zd* Wx = Wb.z() + (int64_t)X * N * N;
+      TRY(zgemm(N, N, B, mkz(sgn[X]), ZView{V[X], 1, N, false}, ZView{U[X], N, 1, true}, mkz(0.0), Wx, N, c->s));
+      W[X] = Wx;
+    }
+  }
+  eb.release(); hb.release(); T.release(); gq.release(); G.release();
+  // per parameter: the operator terms (shape_forms) plus the O(N) terms
+  CtxGuard tp, tm;
+  TRY(make_scratch(c, tp));
+  TRY(make_scratch(c, tm));
+  DevBuf ep, hp, em, hm, Wf;
+  for (DevBuf* b : {&ep, &hp, &em, &hm}) TRY(b->ensure(sizeof(zd) * N * B));
+  TRY(Wf.ensure(sizeof(zd) * nphi * B));
+  std::vector<zd> T_ops(i1 - i0);
+  auto per_param = [&](int i, double dL) -> int {
+    // far field: F^H (E+ - E-) j
+    zd ff = mkz(0.0);
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      wcs_ctx* t = sgn == 0 ? tp.t : tm.t;
+      TRY(farfield_matrix(t->near, t->quad.wn, t->quad.xn, t->opt.q_near, N, t->h, t->k, phd.d(), nphi, E.z(),
+                          nphi, c->s));
+      TRY(zgemm(nphi, B, N, mkz(1.0), ZView{E.z(), 1, nphi, false}, blk(j.z(), N), mkz(0.0), Wf.z(), nphi, c->s));
+      TRY(column_dotc(F.z(), nphi, Wf.z(), nphi, nphi, B, dots.z(), c->s));
+      cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * B, cudaMemcpyDeviceToHost, c->s);
+      TRY(sync(c));
+      for (int64_t b = 0; b < B; ++b) ff += (sgn == 0 ? 1.0 : -1.0) * hd[b];
+    }
+    // right-hand sides: w1^H (h+ - h-) + i k w2^H (e+ - e-)
+    TRY(planewave_rhs(tp.t->near, tp.t->quad.wn, tp.t->quad.xn, tp.t->opt.q_near, N, tp.t->h, tp.t->k, ang.d(),
+                      (int)B, ep.z(), hp.z(), N, c->s));
+    TRY(planewave_rhs(tm.t->near, tm.t->quad.wn, tm.t->quad.xn, tm.t->opt.q_near, N, tm.t->h, tm.t->k, ang.d(),
+                      (int)B, em.z(), hm.z(), N, c->s));
+    TRY(axpby(N, B, mkz(-1.0), hm.z(), N, mkz(1.0), hp.z(), N, c->s));
+    TRY(axpby(N, B, mkz(-1.0), em.z(), N, mkz(1.0), ep.z(), N, c->s));
+    TRY(column_dotc(w1.z(), N, hp.z(), N, N, B, dots.z(), c->s));
+    TRY(column_dotc(w2.z(), N, ep.z(), N, N, B, dots.z() + B, c->s));
+    cudaMemcpyAsync(hd.data(), dots.p, sizeof(zd) * 2 * B, cudaMemcpyDeviceToHost, c->s);
+    TRY(sync(c));
+    zd rhs = mkz(0.0);
+    for (int64_t b = 0; b < B; ++b) rhs += hd[b] + mkz(0.0, c->k) * hd[B + b];
+    const double inv = 1.0 / (2.0 * delta);
+    const zd total = inv * ff + T_ops[i - i0] + (dL / c->L) * gam - inv * rhs;
+    grad[i - i0] = 2.0 * total.x;
+    return 0;
+  };
+  TRY(shape_forms(c, W, M, i0, i1, delta, T_ops.data(), tp, tm, per_param));
   return status;
+}
+
+// T_i = sum_b u_b^H (dX / dp_i) v_b for one operator X (0 S~, 1 D, 2 D~, 3 N).
+int wcs_shape_operator_forms(wcs_ctx* c, int op, int64_t B, const double* u_dev, const double* v_dev, int64_t ld,
+                             int M, double delta, int i0, int i1, double* out_host) {
+  if (!c) { set_error("null context"); return WCS_ERR_ARG; }
+  if (c->stage < ST_ASSEMBLED) { set_error("assemble first"); return WCS_ERR_STATE; }
+  if (op < 0 || op > 3 || B < 1 || !u_dev || !v_dev || ld < c->N || M < 0 || M > kMaxPerturb - 1 || i0 < 0 ||
+      i1 < i0 || i1 > 2 * M || (i1 > i0 && !out_host)) {
+    set_error("shape operator forms: bad argument");
+    return WCS_ERR_ARG;
+  }
+  if (!(delta > 0)) delta = 1e-6;
+  const int64_t N = c->N;
+  DevBuf Wb;
+  TRY(Wb.ensure(sizeof(zd) * 4 * N * N));
+  cudaMemsetAsync(Wb.p, 0, Wb.bytes, c->s);
+  const zd* W[4];
+  for (int X = 0; X < 4; ++X) W[X] = Wb.z() + (int64_t)X * N * N;
+  TRY(zgemm(N, N, B, mkz(1.0), ZView{(const zd*)v_dev, 1, ld, false}, ZView{(const zd*)u_dev, ld, 1, true}, mkz(0.0),
+            Wb.z() + (int64_t)op * N * N, N, c->s));
+  CtxGuard tp, tm;
+  TRY(make_scratch(c, tp));
+  TRY(make_scratch(c, tm));
+  std::vector<zd> T(i1 - i0);
+  TRY(shape_forms(c, W, M, i0, i1, delta, T.data(), tp, tm, [](int, double) { return 0; }));
+  for (int i = 0; i < i1 - i0; ++i) { out_host[2 * i] = T[i].x; out_host[2 * i + 1] = T[i].y; }
+  return WCS_OK;
 }
 
 int wcs_shape_gradient(wcs_ctx* c, int64_t B, const double* angles, int nphi, const double* phi, int M,

@@ -243,8 +243,19 @@ class Solver:
               allow)
         return float(J[0]), g[:i1 - i0]
 
+    def shape_operator_forms(self, op, u, v, M, delta=1e-6, params=None):
+        """sum_b u_b^H (dX/dp_i) v_b for operator op in ("S", "D", "DT", "N") and
+        the shape parameters i (all 2M, or range params = (i0, i1)); u, v: N x B."""
+        which = {"S": 0, "D": 1, "DT": 2, "Dt": 2, "N": 3}[op]
+        uc, vc = self._as_cols(u), self._as_cols(v)
+        i0, i1 = (0, 2 * int(M)) if params is None else (int(params[0]), int(params[1]))
+        out = np.zeros(2 * max(i1 - i0, 1))
+        check(self.lib.wcs_shape_operator_forms(self.h, which, uc.shape[0], _ptr(uc), _ptr(vc), self.N, int(M),
+                                                float(delta), i0, i1, out.ctypes.data_as(C.c_void_p)))
+        return (out[0::2] + 1j * out[1::2])[:i1 - i0]
+
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
-                    "sample", "project", "orth", "vw", "inverse", "gemm_exact")
+                    "sample", "project", "orth", "vw", "inverse", "gemm_exact", "assembly_fast")
 
     def profile(self, enable=True):
         check(self.lib.wcs_profile(self.h, 1 if enable else 0))
@@ -297,3 +308,37 @@ def gemm_exact(A, B):
     st = torch.cuda.current_stream(A.device)
     check(load().wcs_gemm_exact(M, Nc, K, _ptr(A), K, _ptr(B), K, _ptr(D), Nc, C.c_void_p(st.cuda_stream)))
     return D
+
+
+def batch_solve_fourier(contours, angles, tol=1e-6, rank_div=8, seed=1, workers=2, allow_unconverged=False,
+                        **options):
+    """Batched form: contours is a list of dicts {"cos": [...], "sin": [...], "N": int, "k": float or None}
+    (Fourier radial functions); every contour is solved for the same plane waves.
+    Returns (list of N_c x B complex128 host arrays, list of per-contour stats dicts)."""
+    lib = load()
+    opt = default_options(**options)
+    nf = max(len(c["cos"]) for c in contours)
+    count = len(contours)
+    cs = np.zeros((count, nf))
+    sn = np.zeros((count, nf))
+    for i, c in enumerate(contours):
+        cs[i, :len(c["cos"])] = c["cos"]
+        sn[i, :len(c.get("sin", []))] = c.get("sin", [])
+    Ns = np.array([int(c["N"]) for c in contours], dtype=np.int64)
+    ks = np.array([float(c.get("k") or 0.0) for c in contours])
+    a = np.ascontiguousarray(angles, dtype=np.float64)
+    B = len(a)
+    out = np.zeros(int(Ns.sum()) * B, dtype=np.complex128)
+    stats = (_lib.BatchStats * max(count, 1))()
+    allow = (_lib.WCS_ERR_NOT_CONVERGED,) if allow_unconverged else ()
+    check(lib.wcs_batch_solve_fourier(C.byref(opt), count, nf, cs.ctypes.data_as(C.c_void_p),
+                                      sn.ctypes.data_as(C.c_void_p), Ns.ctypes.data_as(C.c_void_p),
+                                      ks.ctypes.data_as(C.c_void_p), B, a.ctypes.data_as(C.c_void_p), float(tol),
+                                      int(rank_div), int(seed), int(workers), out.ctypes.data_as(C.c_void_p),
+                                      stats), allow)
+    js, o = [], 0
+    for n in Ns:
+        js.append(out[o:o + n * B].reshape(B, n).T)
+        o += n * B
+    st = [{f: getattr(stats[i], f) for f, _ in _lib.BatchStats._fields_} for i in range(count)]
+    return js, st

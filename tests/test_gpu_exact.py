@@ -2,11 +2,11 @@
 residual (wcs_options.exact_residual).
 
 * wcs_gemm_exact against the FP64 product, entry by entry.  The slices of a
-  value are exact to 2^-35 of the largest entry of its chunk of 1024 (cmax),
-  and the dropped slice pairs are below 2^-35 cmax_A cmax_B per term, so the
-  error of D_ij is bounded by 2^-34 sum_k (cmax_A |B_jk| + |A_ik| cmax_B +
+  value are exact to 2^-42 of the largest entry of its chunk of 1024 (cmax),
+  and the dropped slice pairs are below 2^-42 cmax_A cmax_B per term, so the
+  error of D_ij is bounded by 2^-40 sum_k (cmax_A |B_jk| + |A_ik| cmax_B +
   cmax_A cmax_B); for data without a wide range inside a chunk that is
-  within 2^-32 (|A| |B|^T).  Both are checked, with entries spanning eight
+  within 2^-38 (|A| |B|^T).  Both are checked, with entries spanning eight
   decades across chunks and within chunks, and K not a multiple of 1024.
   The drained split-bf16 product of the same inputs is ~1e-7 off.
 * The mixed form with exact residuals refines to 1e-11 against its stored
@@ -47,7 +47,7 @@ def test_gemm_exact_componentwise(M, Nc, K, within):
     ref = A @ B.T
     D = to_np(gemm_exact(A, B))
     cA, cB = _chunk_max(A), _chunk_max(B)
-    chunked = 2.0 ** -34 * (cA @ np.abs(B).T + np.abs(A) @ cB.T + cA @ cB.T)
+    chunked = 2.0 ** -40 * (cA @ np.abs(B).T + np.abs(A) @ cB.T + cA @ cB.T)
     assert np.all(np.abs(D - ref) <= chunked), np.max(np.abs(D - ref) / chunked)
     plain = np.abs(A) @ np.abs(B).T
     err = np.max(np.abs(D - ref) / plain)
@@ -55,7 +55,7 @@ def test_gemm_exact_componentwise(M, Nc, K, within):
     err_acc = np.max(np.abs(acc - ref) / plain)
     print(f"within={within}: exact {err:.1e}, drained split-bf16 {err_acc:.1e}")
     if not within:
-        assert err <= 2.0 ** -32, err
+        assert err <= 2.0 ** -38, err
         assert err_acc > 100 * err
 
 

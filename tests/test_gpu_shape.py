@@ -114,3 +114,45 @@ def test_shape_gradient_beta_rotation_identity():
         s.close()
         assert abs(ga[m]) > 1e-2
         assert abs(gb[Mr + m - 1] - ga[m]) <= 1e-6 * abs(ga[m]), (m, gb[Mr + m - 1], ga[m])
+
+
+@pytest.fixture(scope="module")
+def oracle_operator_derivatives():
+    # central differences (delta 1e-6) of the oracle's dense operators at an
+    # asymmetric point of the ellipse, for 3 cosine and 3 sine parameters
+    w = workloads.WORKLOADS["ellipse_n8192"]
+    fam, base = w["family"], w["params"]
+    k = 2.0 * np.pi * (N / 10.0) / geometry.Contour(fam, base).L
+    Mp = 3
+    p = np.zeros(2 * Mp)
+    p[2] = 0.01                   # alpha_2
+    p[Mp + 1] = 0.01              # beta_2
+    d = 1e-6
+    dX = []
+    for i in range(2 * Mp):
+        e = np.zeros(2 * Mp)
+        e[i] = d
+        op_p, _, _, _ = shape.operators_at(fam, base, p + e, Mp, N, k, INC[:1], OBS[:1])
+        op_m, _, _, _ = shape.operators_at(fam, base, p - e, Mp, N, k, INC[:1], OBS[:1])
+        dX.append({key: (op_p[key] - op_m[key]) / (2 * d) for key in ("S", "D", "Dt", "N")})
+    return fam, base, k, Mp, p, dX
+
+
+@pytest.mark.parametrize("op", ["S", "D", "Dt", "N"])
+def test_operator_shape_derivative_forms_vs_oracle(oracle_operator_derivatives, op):
+    # the one-pass derivative kernel (far pairs) plus the differenced near band,
+    # per operator: sum_b u_b^H dX/dp_i v_b against the oracle's differenced
+    # dense operators, for every parameter
+    built()
+    from paper_2203_13283_gb300 import Solver
+    fam, base, k, Mp, p, dX = oracle_operator_derivatives
+    g = np.random.default_rng(7)
+    u = g.standard_normal((N, 3)) + 1j * g.standard_normal((N, 3))
+    v = g.standard_normal((N, 3)) + 1j * g.standard_normal((N, 3))
+    s = Solver(precision=0)
+    s.contour(fam, **base).perturb(p[:Mp], p[Mp:]).mesh(N, k).assemble()
+    T = s.shape_operator_forms(op, u, v, Mp)
+    s.close()
+    ref = np.array([np.sum(u.conj() * (d[op] @ v)) for d in dX])
+    print(op, np.max(np.abs(T - ref)) / np.max(np.abs(ref)))
+    assert np.max(np.abs(T - ref)) <= 1e-8 * np.max(np.abs(ref)), (T, ref)
