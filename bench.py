@@ -120,7 +120,9 @@ def blas_threads():
         n = [d.get("num_threads") for d in threadpool_info() if d.get("user_api") == "blas"]
         return max(n) if n else None
     except Exception:
-        return None
+        env = [os.environ.get(v) for v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")]
+        env = [v for v in env if v]
+        return f"{env[0]} (environment)" if env else f"library default ({cpu_threads()} cores visible)"
 
 
 def oracle_sample(w, n_sample, B_sample):
@@ -161,7 +163,7 @@ def run_reference(args, w):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "RHS solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "N": w["N"], "B": int(w["angles"].size)},
+            "data": "synthetic", "config": {"workload": args.wname, "N": w["N"], "B": int(w["angles"].size)},
             "cpu_baseline": {"value": value, "unit": "RHS solves/s", "cores": cpu_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "RHS solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -236,6 +238,65 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
     return None
 
 
+def shape_leg(local):
+    """Shape gradient of the differentiation workload, FP64 and mixed forms."""
+    import torch
+    from paper_2203_13283_gb300 import Solver
+    ws = workloads.WORKLOADS["ellipse_n8192"]
+    N, M = ws["N"], ws["shape_modes"]
+    inc, obs = ws["angles"], ws["observation_angles"]
+    out = {"workload": "ellipse 1 x 0.7, N = 8192, 16 incidences, 90 observation angles, "
+                       "32 shape coefficients (alpha_0..15, beta_1..16)"}
+    grads = {}
+
+    k0 = []   # the wavenumber of the unperturbed contour, held fixed for every evaluation of J
+
+    def setup(prec, alpha=None, beta=None):
+        S = Solver(device=f"cuda:{local}", precision=prec, refine_tol=1e-8 if prec else 1e-11, max_refine=30,
+                   rhs_chunk=64, block=64)
+        S.contour(ws["family"], **ws["params"])
+        if alpha is not None:
+            S.perturb(alpha, beta)
+        S.mesh(N, k0[0] if k0 else ws["k"])
+        if not k0:
+            k0.append(S.info()["k"])
+        S.assemble()
+        S.skeleton(1e-6, max_rank=N // 8, seed=1, allow_cap=True)
+        S.factor()
+        return S
+
+    for form, prec in (("mixed", 1), ("fp64", 0)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        S = setup(prec)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        J, g = S.shape_gradient(inc, obs, M, allow_unconverged=True)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        S.close()
+        grads[form] = (J, np.asarray(g))
+        out[form] = {"setup_s": t1 - t0, "gradient_s": t2 - t1, "J": float(J),
+                     "note": "wall clock; gradient_s = forward + adjoint solve, one far-pair derivative pass, "
+                             "near band and geometry differenced per coefficient"}
+    g64, gm = grads["fp64"][1], grads["mixed"][1]
+    out["mixed_vs_fp64_rel_err"] = float(np.max(np.abs(gm - g64)) / np.max(np.abs(g64)))
+    i = int(np.argmax(np.abs(g64[:M])))
+    h = 1e-6
+    Js = []
+    for sgn in (1.0, -1.0):
+        a = np.zeros(M)
+        a[i] = sgn * h
+        S = setup(0, a, np.zeros(M))
+        Js.append(S.shape_gradient(inc, obs, M, allow_unconverged=True, params=(0, 0))[0])
+        S.close()
+    fd = (Js[0] - Js[1]) / (2 * h)
+    out["fd_check"] = {"param": f"alpha_{i}", "adjoint": float(g64[i]), "central_difference": float(fd),
+                       "h": h, "rel_diff": float(abs(fd - g64[i]) / abs(g64[i]))}
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -249,6 +310,14 @@ def main():
                     help="skeleton rank cap (default N/8 in the mixed form, 512 in FP64)")
     ap.add_argument("--refine-tol", type=float, default=None)
     ap.add_argument("--rhs", type=int, default=None)
+    ap.add_argument("--n", type=int, default=None,
+                    help="override the workload's N (k then follows 10 elements per wavelength); small "
+                         "cases of the same contour for profiler captures")
+    ap.add_argument("--rhs-chunk", type=int, default=None,
+                    help="right-hand sides per solve block (default 1024 mixed, 64 FP64)")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="bracket the last timed step's solve with cudaProfilerStart/Stop "
+                         "(for ncu --profile-from-start off)")
     ap.add_argument("--zfast", type=float, default=None,
                     help="mixed form: FP32 far pairs above k R = zfast (default: library default)")
     ap.add_argument("--sample-planes", type=int, default=0,
@@ -260,6 +329,8 @@ def main():
     ap.add_argument("--no-batch-leg", action="store_true",
                     help="skip the batched leg (64 star contours, N in [512, 16384], 64 plane waves each)")
     ap.add_argument("--batch-workers", type=int, default=2)
+    ap.add_argument("--no-shape-leg", action="store_true",
+                    help="skip the shape-gradient leg (ellipse 1 x 0.7, N = 8192, 32 shape coefficients)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -273,6 +344,9 @@ def main():
     w = dict(workloads.WORKLOADS[args.workload])
     if args.rhs:
         w["angles"] = workloads.uniform_angles(args.rhs)
+    if args.n:
+        w["N"], w["k"] = args.n, None
+    args.wname = args.workload if not args.n else f"{w['family']}_n{args.n}"
 
     if args.impl == "reference":
         if rank == 0:
@@ -297,7 +371,8 @@ def main():
     rtol = args.refine_tol if args.refine_tol is not None else (5e-7 if mixed else 1e-11)
     extra = {} if args.zfast is None else {"zfast": args.zfast}
     S = Solver(device=f"cuda:{local}", precision=1 if mixed else 0, refine_tol=rtol, max_refine=12 if mixed else 30,
-               rhs_chunk=1024 if mixed else 64, block=64, sample_planes=args.sample_planes, **extra)
+               rhs_chunk=args.rhs_chunk or (1024 if mixed else 64), block=64, sample_planes=args.sample_planes,
+               **extra)
     stream = S.stream
     angles = w["angles"]
     B = len(angles)
@@ -308,7 +383,7 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    def step():
+    def step(profile_solve=False):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
         S.contour(w["family"], **w["params"])
@@ -317,7 +392,13 @@ def main():
         rank_ = S.skeleton(tol, max_rank=max_rank, seed=1, allow_cap=True)
         S.factor()
         e1.record(stream)
+        if profile_solve:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.start()
         S.solve_planewaves(angles, out=j, allow_unconverged=True)
+        if profile_solve:
+            torch.cuda.synchronize()
+            torch.cuda.profiler.stop()
         e2.record(stream)
         e2.synchronize()
         return e0.elapsed_time(e1) / 1e3, e1.elapsed_time(e2) / 1e3, rank_
@@ -335,8 +416,8 @@ def main():
     T1 = torch.cuda.Event(enable_timing=True)
     T0.record(stream)
     setups, solves, ranks = [], [], []
-    for _ in range(args.steps):
-        su, so, rk = step()
+    for i in range(args.steps):
+        su, so, rk = step(args.profile_solve and i == args.steps - 1)
         setups.append(su)
         solves.append(so)
         ranks.append(rk)
@@ -389,14 +470,14 @@ def main():
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3/fp32/f64" if mixed else "f64",
         "data": "synthetic",
-        "config": {"workload": args.workload, "N": w["N"], "B": B, "k": info["k"], "form": args.form,
+        "config": {"workload": args.wname, "N": w["N"], "B": B, "k": info["k"], "form": args.form,
                    "skeleton_tol": tol, "rank": ranks[-1], "rank_cap": max_rank, "refine_tol": rtol,
                    "refine_steps": last["refine_steps"], "rel_residual": last["rel_residual"],
                    "converged": bool(last["rel_residual"] <= rtol),
                    "residual_history": last["history"],
                    "refine_steps_to_1e-6": steps_to(last["history"], 1e-6),
                    "refine_steps_to_1e-10": steps_to(last["history"], 1e-10),
-                   "zfast": info["zfast"], "setup_s": statistics.median(setups), "solve_s": statistics.median(solves),
+                   "zfast": info["zfast"], "capacitance_residual": info["capacitance_residual"], "setup_s": statistics.median(setups), "solve_s": statistics.median(solves),
                    "l2": "operators (tens of GB) exceed L2: no flush needed", "parallelism": f"replicas{world}"},
         "setup_s": statistics.median(setups),
         "e2e": e2e, "clocks": clk, "roofline": roof, "rooflines": rooflines, "roofline_kernel": dominant,
@@ -497,6 +578,13 @@ def main():
                                                              "per_column": [float(x) for x in ex]}
         line["speedup_vs_fp64_form"] = {"rhs_per_s": value / line["fp64_form"]["rhs_per_s"],
                                         "setup": line["fp64_form"]["setup_s"] / line["setup_s"]}
+
+    # the differentiation workload: J = sum |F|^2 over 16 incidences and 90
+    # observation angles on the ellipse 1 x 0.7 at N = 8192, and its gradient in
+    # 32 Fourier shape coefficients by the adjoint route, in both forms; one
+    # coefficient is also checked against central differences of J (h = 1e-6)
+    if mixed and world == 1 and not args.no_shape_leg:
+        line["shape_gradient_leg"] = shape_leg(local)
 
     if rank == 0 and not args.no_cpu_baseline:
         t, tf = oracle_sample(w, ORACLE_N, ORACLE_B)

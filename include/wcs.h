@@ -101,6 +101,9 @@ typedef struct wcs_info {
   double norm_cc;     /* ||C_c||_2 = max |mu_C| (after wcs_assemble) */
   double min_curvature; /* minimum curvature found by the convexity check */
   double zfast;       /* far-pair FP32 threshold in effect (mixed form; 0 in the FP64 form) */
+  double capacitance_residual; /* ||I - K K^-1||_F / sqrt(rank) of the last wcs_factor, measured
+                         with exact products when K^-1 came from the tensor-core iteration
+                         (mixed form, rank >= 256); -1 when not measured */
 } wcs_info;
 
 /* Entries of wcs_solve_info::history. */
@@ -130,7 +133,8 @@ typedef enum wcs_op {
   WCS_OP_N = 8,       /* N^k */
   WCS_OP_G = 9,       /* Gram matrix of the hats */
   WCS_OP_SKEL = 10,   /* U V^T, the skeleton of C - C_c (Eq. 7) */
-  WCS_OP_GINV = 11    /* G^-1 (cyclic tridiagonal solve) */
+  WCS_OP_GINV = 11,   /* G^-1 (cyclic tridiagonal solve) */
+  WCS_OP_CCH_INV = 12 /* C_c^{-H} */
 } wcs_op;
 
 /* Library version string. */
@@ -193,7 +197,12 @@ int wcs_operator_entries(wcs_ctx* ctx, int64_t count, const int64_t* rows_host,
  * eigenvalue for the eigenvector exp(2 pi i m j / N).  out_dev: N complex. */
 int wcs_circulant_eigs(wcs_ctx* ctx, int op, double* out_dev);
 
-/* Y = op X for B columns (X, Y device, column-major, may not alias). */
+/* Y = op X for B columns (X, Y device, column-major, may not alias).
+ * The circulant operators (CC, CCH, CC_INV, CCH_INV) are applied by FFT with
+ * the FP64 eigenvalues mu_C.  In the mixed form, for power-of-two N in
+ * [1024, 65536], the transform itself runs in FP32 (relative error ~1e-6:
+ * these applies serve the Woodbury approximate inverse of Eq. 9 and the
+ * sampling of C - C_c, both corrected by refinement); otherwise in FP64. */
 int wcs_apply(wcs_ctx* ctx, int op, int64_t B, const double* X_dev, int64_t ldx, double* Y_dev,
               int64_t ldy);
 

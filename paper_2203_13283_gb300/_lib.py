@@ -13,7 +13,7 @@ STATUS_NAMES = {0: "WCS_OK", 1: "WCS_ERR_ARG", 2: "WCS_ERR_NOT_CONVEX", 3: "WCS_
                 10: "WCS_ERR_UNSUPPORTED"}
 
 OPS = {"C": 0, "CH": 1, "CC": 2, "CCH": 3, "CC_INV": 4, "S": 5, "D": 6, "DT": 7, "N": 8, "G": 9,
-       "SKEL": 10, "GINV": 11}
+       "SKEL": 10, "GINV": 11, "CCH_INV": 12}
 
 
 class Options(C.Structure):
@@ -28,7 +28,7 @@ class Info(C.Structure):
     _fields_ = [("N", C.c_int64), ("L", C.c_double), ("h", C.c_double), ("a", C.c_double),
                 ("k", C.c_double), ("kt_re", C.c_double), ("kt_im", C.c_double),
                 ("rank", C.c_int), ("norm_cc", C.c_double), ("min_curvature", C.c_double),
-                ("zfast", C.c_double)]
+                ("zfast", C.c_double), ("capacitance_residual", C.c_double)]
 
 
 WCS_HISTORY = 32

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libwcs.so")
 SOURCES = ["geometry.cu", "quad.cu", "assemble.cu", "fft.cu", "linalg.cu", "rhs.cu", "gemm_tc.cu",
-           "mixed.cu", "exact.cu", "noalloc.cu", "probe.cu", "batch.cu", "solver.cu"]
+           "mixed.cu", "exact.cu", "noalloc.cu", "probe.cu", "batch.cu", "circ32.cu", "solver.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

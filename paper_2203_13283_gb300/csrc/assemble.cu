@@ -17,6 +17,8 @@
 // weights (split K = A log|s - s'| + B, A = -(1/2pi) J0 or -(kappa/2pi) J1 g).
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <complex>
 #include <cstring>
 #include <vector>
@@ -545,8 +547,11 @@ __global__ void k_entries(AsmArgs A, int64_t count, const int64_t* rows, const i
   for (int op = 0; op < 4; ++op) out4[op * count + t] = sum[op];
 }
 
-// Coefficient tables of hankel01_asymptotic_fixed for k~ = k (1 + i t)
-void fill_asymptotic(KtPair& kp) {
+// Coefficient tables of hankel01_asymptotic_fixed for k~ = k (1 + i t), and
+// the x above which 2M terms (M = 2, 3, 4, 5, 7) meet the relative tolerance
+// tol: the first omitted term max_nu |a_2M(nu)| / x^2M (|1 + i t|^-2M <= 1),
+// with 10% margin on x and never below 20, where the expansion starts
+void fill_asymptotic(KtPair& kp, double tol) {
   AsymCoef& h = kp.asym;
   std::memset(&h, 0, sizeof(h));
   const std::complex<double> c1 = std::complex<double>(1.0, 0.0) / std::complex<double>(1.0, kp.t);
@@ -564,6 +569,17 @@ void fill_asymptotic(KtPair& kp) {
       if ((k & 1) == 0) { h.re[nu][m] = sg * a; h.ce[nu][m] = mkz(b.real(), b.imag()); }
       else { h.ro[nu][m] = sg * a; h.co[nu][m] = mkz(b.real(), b.imag()); }
     }
+  }
+  const int Ms[5] = {2, 3, 4, 5, 7};
+  for (int i = 0; i < 5; ++i) {
+    const int k2 = 2 * Ms[i];
+    double need = 20.0;
+    for (int nu = 0; nu < 2; ++nu) {
+      double a = 1.0;
+      for (int k = 1; k <= k2; ++k) a *= (4.0 * nu * nu - (2.0 * k - 1.0) * (2.0 * k - 1.0)) / (8.0 * k);
+      need = std::max(need, 1.1 * std::pow(std::fabs(a) / tol, 1.0 / k2));
+    }
+    kp.xth[i] = need;
   }
 }
 
@@ -670,6 +686,38 @@ __global__ void k_tile_flags(AsmArgs A, int64_t nt, uint8_t* flag) {
 // pair_fast_f accumulated per node pair in shared memory (FP32, four
 // conflict-free phases), then scaled by their FP64 factors, combined (N) and
 // written as split-bf16 planes.
+// float-float helpers for the epilogue of k_assemble_fast
+struct ff2 {
+  ff r, i;
+};
+__device__ __forceinline__ ff ff_of(double x) {
+  const float h = (float)x;
+  return ff{h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ ff2 ff2_of(zd z) { return ff2{ff_of(z.x), ff_of(z.y)}; }
+__device__ __forceinline__ ff ff_mul_f(ff a, float b) {
+  const ff p = ff_two_prod(a.hi, b);
+  return ff_quick(p.hi, fmaf(a.lo, b, p.lo));
+}
+// bf16 planes of a float-float value: hi - bf16(hi) is exact in FP32, so the
+// second residual carries the value to ~2^-24 of the first plane's scale
+__device__ __forceinline__ void ff_planes(ff x, uint16_t (&p)[3]) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x.hi);
+  const float r1 = (x.hi - __bfloat162float(h0)) + x.lo;
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h1);
+  p[0] = __bfloat16_as_ushort(h0);
+  p[1] = __bfloat16_as_ushort(h1);
+  p[2] = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+// (re, im) as adjacent bf16 pairs, one 32-bit store per plane (off even)
+__device__ __forceinline__ void split_store_ff2(ff re, ff im, int planes, uint16_t* const* P, int64_t off) {
+  uint16_t a[3], b[3];
+  ff_planes(re, a);
+  ff_planes(im, b);
+  for (int q = 0; q < planes; ++q) *(uint32_t*)(P[q] + off) = (uint32_t)a[q] | ((uint32_t)b[q] << 16);
+}
+
 __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_t nt, const uint8_t* flag) {
   const int64_t ti = blockIdx.y, tj = blockIdx.x;
   if (flag[ti * nt + tj]) return;
@@ -705,30 +753,40 @@ __global__ void __launch_bounds__(ASM_THREADS) k_assemble_fast(AsmArgs A, int64_
       __syncthreads();
     }
   }
-  // entry (li, lj) of operator op in FP64
-  auto entry = [&](int op, int li, int lj) -> zd {
-    const int t = li * TILE + lj;
-    if (op == 0) return A.fS * zf2d(acc[t]);
-    if (op == 1) return A.fD * zf2d(acc[TILE * TILE + t]);
-    if (op == 2) return A.fDt * zf2d(acc[2 * TILE * TILE + t]);
-    return A.fN * (zf2d(acc[4 * TILE * TILE + t]) - A.kk2h2 * zf2d(acc[3 * TILE * TILE + t]));
-  };
-  for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
-    const int comp = t & 1, u = t >> 1;
-    const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
-    const int li = rem / TILE, lj = rem - (rem / TILE) * TILE;
-    if (i0 + li < N && j0 + lj < N) {
-      const zd v = entry(op, li, lj);
-      split_store(comp ? v.y : v.x, A.planes, A.P[op][0], (i0 + li) * A.ldp + 2 * (j0 + lj) + comp);
+  // Entries: the FP64 run factors times the FP32 tile sums, in float-float
+  // on the FP32 pipe (the factors as hi + lo; products by TwoProd), split
+  // into bf16 planes from the float-float value.  The result carries ~44
+  // bits, far beyond the 24 of the FP32 sums, without touching the FP64
+  // pipe (64 times slower), which the FP64 form of this epilogue saturated.
+  const ff2 fS = ff2_of(A.fS), fD = ff2_of(A.fD), fDt = ff2_of(A.fDt), fN = ff2_of(A.fN);
+  const ff kk = ff_of(A.kk2h2);
+  auto entry = [&](int op, int t, ff& re, ff& im) {
+    if (op == 3) {
+      // N = fN (Nd - k^2 h^2 Nb)
+      const cf nb = acc[3 * TILE * TILE + t], nd = acc[4 * TILE * TILE + t];
+      const ff dr = ff_add(ff{nd.x, 0.f}, ff_neg(ff_mul_f(kk, nb.x)));
+      const ff di = ff_add(ff{nd.y, 0.f}, ff_neg(ff_mul_f(kk, nb.y)));
+      re = ff_add(ff_mul(fN.r, dr), ff_neg(ff_mul(fN.i, di)));
+      im = ff_add(ff_mul(fN.r, di), ff_mul(fN.i, dr));
+      return;
     }
-  }
-  for (int t = threadIdx.x; t < 4 * TILE * TILE * 2; t += blockDim.x) {
-    const int comp = t & 1, u = t >> 1;
-    const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
-    const int lj = rem / TILE, li = rem - (rem / TILE) * TILE;
-    if (i0 + li < N && j0 + lj < N) {
-      const zd v = entry(op, li, lj);
-      split_store(comp ? v.y : v.x, A.planes, A.P[op][1], (j0 + lj) * A.ldp + 2 * (i0 + li) + comp);
+    const ff2& f = (op == 0) ? fS : (op == 1) ? fD : fDt;
+    const cf a = acc[op * TILE * TILE + t];
+    re = ff_add(ff_mul_f(f.r, a.x), ff_neg(ff_mul_f(f.i, a.y)));
+    im = ff_add(ff_mul_f(f.r, a.y), ff_mul_f(f.i, a.x));
+  };
+  // layout 0: rows i (consecutive threads along j); layout 1: rows j
+  for (int lay = 0; lay < 2; ++lay) {
+    for (int u = threadIdx.x; u < 4 * TILE * TILE; u += blockDim.x) {
+      const int op = u / (TILE * TILE), rem = u - op * TILE * TILE;
+      const int a = rem / TILE, b = rem - (rem / TILE) * TILE;
+      const int li = lay ? b : a, lj = lay ? a : b;
+      if (i0 + li < N && j0 + lj < N) {
+        ff re, im;
+        entry(op, li * TILE + lj, re, im);
+        const int64_t off = lay ? (j0 + lj) * A.ldp + 2 * (i0 + li) : (i0 + li) * A.ldp + 2 * (j0 + lj);
+        split_store_ff2(re, im, A.planes, A.P[op][lay], off);
+      }
     }
   }
 }

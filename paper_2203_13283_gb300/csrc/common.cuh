@@ -36,6 +36,9 @@ struct KtPair {
   zd c1;   // 1 / (1 + i t)
   zd c2;   // (1 + i t)^(-1/2), principal branch
   AsymCoef asym;
+  // x above which 4, 6, 8, 10, 14 terms of the expansion meet the run's
+  // tolerance (below xth[4]: all 2 ASYM_M terms); see set_asym_terms
+  double xth[5] = {1e300, 1e300, 1e300, 1e300, 1e300};
 };
 
 

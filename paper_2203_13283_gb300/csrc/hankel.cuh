@@ -316,17 +316,20 @@ __device__ inline void hankel01_asymptotic_pair(double x, const KtPair& kp, Hank
 // terms (k = 0..19) leave a relative truncation error below 4e-16 for both
 // orders and both arguments.  Even and odd powers of u = 1/x are summed by
 // Horner's rule in u^2 with per-run coefficient tables: (-1)^m a_k(nu) for the
-// real argument and (-1)^m a_k(nu) (1 + i t)^-k for x (1 + i t).
+// real argument and (-1)^m a_k(nu) (1 + i t)^-k for x (1 + i t).  The first
+// omitted term of a sum of 2M terms is a_2M(nu) / x^2M, so larger x needs
+// fewer terms: KtPair::xth[] holds, for M = 2, 3, 4, 5, 7, the smallest x at
+// which that term is below the run's tolerance (1e-16 for the FP64 form, 1e-13
+// for the mixed form, whose entries are stored to 24 bits).
 
-__device__ inline void hankel01_asymptotic_fixed(double x, const KtPair& kp, Hankel01& hk, Hankel01& ht) {
-  const double u = 1.0 / x, u2 = u * u;
-  zd S[2], St[2];
+template <int M>
+__device__ __forceinline__ void asym_sums(double u, double u2, const KtPair& kp, zd (&S)[2], zd (&St)[2]) {
 #pragma unroll
   for (int nu = 0; nu < 2; ++nu) {
-    double e = kp.asym.re[nu][ASYM_M - 1], o = kp.asym.ro[nu][ASYM_M - 1];
-    zd ce = kp.asym.ce[nu][ASYM_M - 1], co = kp.asym.co[nu][ASYM_M - 1];
+    double e = kp.asym.re[nu][M - 1], o = kp.asym.ro[nu][M - 1];
+    zd ce = kp.asym.ce[nu][M - 1], co = kp.asym.co[nu][M - 1];
 #pragma unroll
-    for (int m = ASYM_M - 2; m >= 0; --m) {
+    for (int m = M - 2; m >= 0; --m) {
       e = fma(e, u2, kp.asym.re[nu][m]);
       o = fma(o, u2, kp.asym.ro[nu][m]);
       ce = mkz(fma(ce.x, u2, kp.asym.ce[nu][m].x), fma(ce.y, u2, kp.asym.ce[nu][m].y));
@@ -335,6 +338,17 @@ __device__ inline void hankel01_asymptotic_fixed(double x, const KtPair& kp, Han
     S[nu] = mkz(e, u * o);                             // sum a_k (i u)^k
     St[nu] = mkz(ce.x - u * co.y, ce.y + u * co.x);    // sum a_k (i u / (1 + i t))^k
   }
+}
+
+__device__ inline void hankel01_asymptotic_fixed(double x, const KtPair& kp, Hankel01& hk, Hankel01& ht) {
+  const double u = 1.0 / x, u2 = u * u;
+  zd S[2], St[2];
+  if (x >= kp.xth[0]) asym_sums<2>(u, u2, kp, S, St);
+  else if (x >= kp.xth[1]) asym_sums<3>(u, u2, kp, S, St);
+  else if (x >= kp.xth[2]) asym_sums<4>(u, u2, kp, S, St);
+  else if (x >= kp.xth[3]) asym_sums<5>(u, u2, kp, S, St);
+  else if (x >= kp.xth[4]) asym_sums<7>(u, u2, kp, S, St);
+  else asym_sums<ASYM_M>(u, u2, kp, S, St);
   double sn, cs;
   sincos(x - 0.25 * WCS_PI, &sn, &cs);
   const double amp = sqrt((2.0 / WCS_PI) * u);

@@ -128,8 +128,9 @@ struct AsmArgs {
   FastConsts fk;
   const uint8_t* tile_flags = nullptr;           // mixed tile kernel: only flagged tiles
 };
-// Fill kp.asym for kp.t (host).
-void fill_asymptotic(KtPair& kp);
+// Fill kp.asym for kp.t and the term-count thresholds kp.xth for relative
+// tolerance tol (host).
+void fill_asymptotic(KtPair& kp, double tol);
 int assemble_dense(const AsmArgs& a, cudaStream_t s);
 // Mixed form: the same operators written as split-bf16 planes (see AsmArgs):
 // the FP32 far-pair kernel over the tiles it can take, then the FP64 kernel
@@ -176,6 +177,22 @@ struct FFTPlan {
   zd* work = nullptr;              // Bluestein work (m * batch_cap)
   int64_t work_cols = 0;
 };
+// FP32 circulant applies of the mixed form (circ32.cu): y = F^-1 diag(s) F x
+// with s = mu, conj(mu), 1/mu, 1/conj(mu) (mode 0..3) for power-of-two
+// 1024 <= n <= 65536; x, y FP64 columns (y may alias x).
+struct Circ32 {
+  int64_t n = 0;
+  int n1 = 0, n2 = 0;
+  float2* scale = nullptr;   // 4 x n, permuted to the middle pass's register layout, times 1/n
+  int64_t scale_n = 0;
+  float2* work = nullptr;    // FP32 scratch columns
+  int64_t work_elems = 0;
+  bool ready = false;
+};
+bool circ32_supported(int64_t n);
+int circ32_prepare(Circ32& p, const zd* mu, int64_t n, cudaStream_t s);
+int circ32_apply(Circ32& p, const zd* x, int64_t ldx, zd* y, int64_t ldy, int64_t cols, int mode, cudaStream_t s);
+void circ32_release(Circ32& p);
 int fft_plan_create(FFTPlan& p, int64_t n, cudaStream_t s);
 void fft_plan_destroy(FFTPlan& p);
 // In-place batched transform of `cols` columns of length n (column-major, ld).

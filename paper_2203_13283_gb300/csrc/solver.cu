@@ -74,6 +74,8 @@ struct wcs_ctx {
   double norm_cc = 0;
   FFTPlan fft{};
   bool fft_ready = false;
+  Circ32 circ{};                          // mixed form: FP32 circulant applies (built from mu_C on first use)
+  double kinv_res = -1.0;                 // ||I - K K^-1||_F / sqrt(r) of the last factor (-1: not measured)
   int rank = -1;
   DevBuf U, Vw, Wt;                       // N x rank each
   DevBuf w1, w2, w3, w4, w5;              // N x chunk scratch
@@ -88,7 +90,6 @@ struct wcs_ctx {
   DevBuf stage0, stage1, stage2;          // staged right-hand blocks (bf16 planes)
   int64_t stage_cols = 0;
   DevBuf tcerr;
-  bool first_accurate = false;   // mixed form: the first residual has been small enough to skip the fast pass
   DevBuf gW;                 // split-K workspace of the small contractions (FP32)
   DevBuf qh, qt;             // skeleton basis as resident bf16 planes: rows conj(q_i); rows of Q
   DevBuf gA, gB;                          // staging for general complex tensor products
@@ -263,7 +264,11 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
 
 static int check_tc(wcs_ctx* c) {
   int e = 0;
-  cudaMemcpyAsync(&e, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+  // the flag exists once a tensor-core product has run on this context
+  if (c->tcerr.p) {
+    const cudaError_t m = cudaMemcpyAsync(&e, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, c->s);
+    if (m != cudaSuccess) { set_error(std::string("device: ") + cudaGetErrorString(m)); return WCS_ERR_CUDA; }
+  }
   cudaError_t r = cudaStreamSynchronize(c->s);
   if (r != cudaSuccess) { set_error(std::string("device: ") + cudaGetErrorString(r)); return WCS_ERR_CUDA; }
   if (e) { set_error("tensor-core contraction: a bounded wait expired"); return WCS_ERR_TIMEOUT; }
@@ -487,6 +492,13 @@ static int apply_C(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int
 // Y = C_c X, C_c^H X or C_c^{-1} X by FFT (mode 0, 1, 2).  Y may alias X.
 static int apply_Cc(wcs_ctx* c, const zd* X, int64_t ldx, zd* Y, int64_t ldy, int64_t cols, int mode) {
   const int64_t N = c->N;
+  if (c->mixed && circ32_supported(N)) {
+    // mixed form: the three-pass FP32 transform (x and y read and written
+    // once in FP64, one FP32 scratch round trip in between)
+    if (!c->circ.ready) TRY(circ32_prepare(c->circ, mu_ptr(c, MU_C), N, c->s));
+    ProfScope ps(c, CAT_FFT, 0.0, 64.0 * (double)N * cols);
+    return circ32_apply(c->circ, X, ldx, Y, ldy, cols, mode, c->s);
+  }
   if (X != Y) {
     cudaError_t e = cudaMemcpy2DAsync(Y, sizeof(zd) * ldy, X, sizeof(zd) * ldx, sizeof(zd) * N, cols,
                                       cudaMemcpyDeviceToDevice, c->s);
@@ -654,6 +666,14 @@ __global__ void k_two_minus(zd* T, int64_t r) {
   T[t] = v;
 }
 
+// At = A^T for an r x r complex column-major A (At row-major A)
+__global__ void k_transpose_z(const zd* __restrict__ A, int64_t r, zd* __restrict__ At) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= r * r) return;
+  const int64_t i = t / r, j = t % r;   // At row i, column j (coalesced writes)
+  At[t] = A[i + j * r];
+}
+
 // ||I - T||_F^2 partial sums (one block)
 // ||T - I||_F in two deterministic stages: per-block partial sums, then one block
 constexpr int EYE_BLOCKS = 304;
@@ -781,8 +801,9 @@ static void free_mesh(wcs_ctx* c) {
   c->U.release(); c->Vw.release(); c->Wt.release(); c->Kinv.release(); c->Wa.release();
   c->sol_e.release(); c->sol_h.release(); c->sol_b.release(); c->sol_ang.release(); c->sol_j.release();
   c->exops.release(); c->exrhs.release(); c->exws.release(); c->exact_ready = false;
-  c->first_accurate = false;   // per-contour refinement state
   if (c->fft_ready) { fft_plan_destroy(c->fft); c->fft_ready = false; }
+  circ32_release(c->circ);
+  c->kinv_res = -1.0;
   c->rank = -1;
 }
 
@@ -919,6 +940,7 @@ int wcs_query(const wcs_ctx* c, wcs_info* info) {
   info->norm_cc = c->stage >= ST_ASSEMBLED ? c->norm_cc : 0.0;
   info->min_curvature = c->kmin;
   info->zfast = c->mixed ? c->opt.zfast : 0.0;
+  info->capacitance_residual = c->kinv_res;
   return WCS_OK;
 }
 
@@ -939,7 +961,9 @@ static AsmArgs asm_args(wcs_ctx* c, bool circle) {
     A.ktp.t = t;
     A.ktp.c1 = mkz(c1.real(), c1.imag());
     A.ktp.c2 = mkz(c2.real(), c2.imag());
-    fill_asymptotic(A.ktp);
+    // the mixed form stores entries to 24 bits: its expansion stops at 1e-13;
+    // the FP64 form and the circle rows (the eigenvalues) keep 1e-16
+    fill_asymptotic(A.ktp, (c->mixed && !circle) ? 1e-13 : 1e-16);
   }
   return A;
 }
@@ -1080,6 +1104,7 @@ int wcs_assemble(wcs_ctx* c) {
   TRY(fft_columns(c->fft, mu_ptr(c, MU_S), N, 4, +1, c->s));
   k_mu_finish<<<(unsigned)((N + 255) / 256), 256, 0, c->s>>>(c->mu.z(), N, c->h);
   note_launch();
+  c->circ.ready = false;   // the FP32 circulant tables follow mu_C
   TRY(c->small.ensure(sizeof(double) * 8));
   k_absmax<<<1, 256, 0, c->s>>>(mu_ptr(c, MU_C), N, c->small.d());
   note_launch();
@@ -1168,6 +1193,7 @@ int wcs_apply(wcs_ctx* c, int op, int64_t B, const double* X, int64_t ldx, doubl
       case WCS_OP_CC: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 0)); break;
       case WCS_OP_CCH: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 1)); break;
       case WCS_OP_CC_INV: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 2)); break;
+      case WCS_OP_CCH_INV: TRY(apply_Cc(c, xc, ldx, yc, ldy, cc, 3)); break;
       case WCS_OP_S:
       case WCS_OP_D:
       case WCS_OP_DT:
@@ -1340,10 +1366,52 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   return status;
 }
 
+// Y = A X for r x r complex A and r x cols complex X (column-major, ld r),
+// exact up to the FP64 sums of the scaled integer partials (exact.cu): the
+// rows of A as fixed-point slices, X as slices of a right-hand block.
+static int exact_square(wcs_ctx* c, const zd* A, int64_t r, const zd* X, int64_t cols, zd* Y) {
+  TRY(ensure_tcerr(c));
+  DevBuf At, pa, pb, ws;
+  TRY(At.ensure(sizeof(zd) * r * r));
+  k_transpose_z<<<(unsigned)((r * r + 255) / 256), 256, 0, c->s>>>(A, r, At.z());
+  note_launch();
+  int64_t lda = 0, ncha = 0, ldb = 0, nchb = 0;
+  size_t sa = 0, ea = 0, sb = 0, eb = 0;
+  const int64_t G = 256;
+  exact_operand_alloc_bytes(r, 2 * r, &lda, &ncha, &sa, &ea);
+  exact_operand_alloc_bytes(2 * G, 2 * r, &ldb, &nchb, &sb, &eb);
+  const size_t sa2 = ((sa + 255) / 256) * 256, sb2 = ((sb + 255) / 256) * 256;
+  TRY(pa.ensure(EX_SLICES * sa2 + ea + 256));
+  TRY(pb.ensure(EX_SLICES * sb2 + eb + 256));
+  const int64_t ws_elems = nchb * 2 * G * r;
+  TRY(ws.ensure(sizeof(float) * (size_t)ws_elems));
+  ExactOperand oa, ob;
+  oa.ld = lda;
+  oa.nchunks = ncha;
+  ob.ld = ldb;
+  ob.nchunks = nchb;
+  for (int q = 0; q < EX_SLICES; ++q) {
+    oa.slice[q] = (uint16_t*)((char*)pa.p + q * sa2);
+    ob.slice[q] = (uint16_t*)((char*)pb.p + q * sb2);
+  }
+  oa.expo = (int16_t*)((char*)pa.p + EX_SLICES * sa2);
+  ob.expo = (int16_t*)((char*)pb.p + EX_SLICES * sb2);
+  TRY(exact_slice_real((const double*)At.p, r, 2 * r, 2 * r, oa, c->s));
+  ProfScope ps(c, CAT_GEMM_EXACT, 2.0 * r * (2.0 * cols) * (2.0 * r), 0.0);
+  for (int64_t c0 = 0; c0 < cols; c0 += G) {
+    const int64_t cc = std::min(G, cols - c0);
+    TRY(exact_slice_rhs(X + c0 * r, r, cc, r, 0, ob, c->s));
+    TRY(exact_product(oa, (int)r, ob, (int)cc, (int)(2 * r), mkz(1.0), mkz(0.0), 0, Y + c0 * r, r,
+                      (float*)ws.p, ws_elems, (int*)c->tcerr.p, c->s));
+  }
+  return check_tc(c);
+}
+
 int wcs_factor(wcs_ctx* c) {
   if (!c) { set_error("null context"); return WCS_ERR_ARG; }
   if (c->stage < ST_SKELETON) { set_error("skeleton first"); return WCS_ERR_STATE; }
   const int64_t N = c->N, r = c->rank;
+  c->kinv_res = -1.0;
   ProfScope whole(c, CAT_FACTOR, 8.0 / 3.0 * r * (double)r * r, 0.0);
   if (r > 0) {
     TRY(c->Wt.ensure(sizeof(zd) * N * r));
@@ -1417,6 +1485,27 @@ int wcs_factor(wcs_ctx* c) {
         std::swap(X, Xn);
       }
       if (!(res < 0.1 * std::sqrt((double)r))) { set_error("capacitance iteration did not converge"); return WCS_ERR_SINGULAR; }
+      // The split-bf16 iteration stalls near 1e-4 per direction.  Two closing
+      // steps with exact products (each squares the residual) carry K^-1 to
+      // FP64 accuracy, and a third exact product measures ||I - K X||_F.
+      {
+        for (int it = 0; it < 2; ++it) {
+          TRY(exact_square(c, Kb.z(), r, X, r, T.z()));          // T = K X
+          k_two_minus<<<(unsigned)((r * r + 255) / 256), 256, 0, c->s>>>(T.z(), r);
+          note_launch();
+          TRY(exact_square(c, X, r, T.z(), r, Xn));             // X <- X (2I - K X)
+          std::swap(X, Xn);
+        }
+        TRY(exact_square(c, Kb.z(), r, X, r, T.z()));
+        k_eye_partial<<<EYE_BLOCKS, 256, 0, c->s>>>(T.z(), r, cs + 3 * r);
+        note_launch();
+        k_eye_finish<<<1, 256, 0, c->s>>>(cs + 3 * r, EYE_BLOCKS, cs + 2 * r);
+        note_launch();
+        cudaMemcpyAsync(&res, cs + 2 * r, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+        TRY(sync(c));
+        c->kinv_res = res / std::sqrt((double)r);
+        if (!(c->kinv_res < 1e-6)) { set_error("capacitance iteration did not reach FP64 accuracy"); return WCS_ERR_SINGULAR; }
+      }
       if (X != Kinv.z())
         cudaMemcpyAsync(Kinv.p, X, sizeof(zd) * r * r, cudaMemcpyDeviceToDevice, c->s);
     }
@@ -1835,6 +1924,20 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
     }
     return worst_of(worst);
   };
+  // After an update, the contraction of the previous one (carried residual
+  // upd after prev_upd) predicts the next carried residual.  When that is far
+  // below the target the round ends without carrying the residual: the
+  // recomputed residual that closes every round replaces it anyway, so the
+  // product R <- R - C dx would be spent only to be overwritten.  The round's
+  // first update has no contraction yet and always carries.  A wrong
+  // prediction costs nothing but another round.
+  auto ends_round = [&](double& upd, double prev_upd) -> bool {
+    if (!(prev_upd < 1e299) || !(upd > 0.0)) return false;
+    const double pred = upd * (upd / prev_upd);
+    if (!(pred < 0.01 * c->opt.refine_tol)) return false;
+    upd = pred;
+    return true;
+  };
   double worst = 0;
   if (!c->mixed) {
     // FP64 form: plain refinement on the exact residual
@@ -1862,6 +1965,7 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
         TRY(approx_inverse(R, N, dx, N));
         TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
         ++it;
+        if (ends_round(upd, prev_upd)) break;
         const int m = (upd > 5e-5) ? PREC_EXACT : (upd > 5e-7 ? PREC_ACCURATE : PREC_PERIODIC);
         TRY(apply_C(c, dx, N, T, N, cc, adj, m));
         TRY(axpby(N, cc, mkz(-1.0), T, N, mkz(1.0), R, N, c->s));
@@ -1872,24 +1976,14 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
       floor = worst > 10.0 * upd;
     }
   } else {
-    // Mixed form.  While the first residual is large, fast residuals do (their
-    // own error, ~1e-4, is below it); once it is small, the residual is formed
-    // with the drained accumulation (~1e-7) and then carried forward by updates
-    // R <- R - C dx in the periodic-drain precision: their error is ~1e-5 of
-    // |C dx|, i.e. far below the residual once |dx| is small.  Each round ends
-    // with a recomputed residual, so the reported residual is the true one;
-    // rounds stop when it reaches refine_tol or stops decreasing (its floor is
-    // the accuracy of the drained product).
-    if (!c->first_accurate) {
-      TRY(residual(PREC_FAST, worst));
-      while (worst >= 3e-3 && it < c->opt.max_refine / 2) {
-        TRY(approx_inverse(R, N, dx, N));
-        TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
-        ++it;
-        TRY(residual(PREC_FAST, worst));
-      }
-      if (it == 0) c->first_accurate = true;   // later blocks skip the fast pass
-    }
+    // Mixed form.  The first residual is formed with the drained accumulation
+    // (~1e-7) and then carried forward by updates R <- R - C dx in the
+    // periodic-drain precision: their error is ~1e-5 of |C dx|, i.e. far
+    // below the residual once |dx| is small, and no more expensive than a
+    // fast product while it is large.  Each round ends with a recomputed
+    // residual, so the reported residual is the true one; rounds stop when it
+    // reaches refine_tol or stops decreasing (its floor is the accuracy of
+    // the drained product).
     TRY(residual(PREC_ACCURATE, worst));
     double prev_true = 1e300;
     bool floor = false;   // a round ended with the true residual far above the carried one
@@ -1901,6 +1995,7 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
         TRY(approx_inverse(R, N, dx, N));
         TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
         ++it;
+        if (ends_round(upd, prev_upd)) break;
         TRY(apply_C(c, dx, N, T, N, cc, adj, PREC_PERIODIC));
         TRY(axpby(N, cc, mkz(-1.0), T, N, mkz(1.0), R, N, c->s));
         prev_upd = upd;

@@ -53,7 +53,10 @@ def test_mixed_operator_products(pair4096):
 
 def test_mixed_solve_vs_fp64_capacitance_iteration(pair4096):
     # rank 512 >= 256: the mixed form inverts the capacitance matrix by
-    # Newton-Schulz on the tensor cores
+    # Newton-Schulz on the tensor cores, closed by two steps with exact
+    # products; their residual ||I - K K^-1||_F / sqrt(r), measured with an
+    # exact product, is at the level of FP64 rounding (the float-float sums
+    # of the exact products keep ~2^-48 of each chunk)
     w, s64, sm = pair4096
     ang = workloads.uniform_angles(48)
     s64.skeleton(1e-2, seed=2)
@@ -62,6 +65,9 @@ def test_mixed_solve_vs_fp64_capacitance_iteration(pair4096):
     rank = sm.skeleton(1e-6, max_rank=512, seed=2, allow_cap=True)
     assert rank == 512
     sm.factor()
+    kres = sm.info()["capacitance_residual"]
+    print("capacitance residual", kres)
+    assert 0.0 <= kres <= 1e-12
     jm = to_np(sm.solve_planewaves(ang, allow_unconverged=True))
     assert colrel(jm, j64) < 1e-6
     assert sm.last_solve["rel_residual"] < 1e-6
