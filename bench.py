@@ -195,23 +195,30 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
         return None
     sec = v["ms"] / 1e3
     per = v["launches"]
-    if cat in ("gemm_tc", "gemm_tc_acc"):
+    if cat in ("gemm_tc", "gemm_tc_acc", "gemm_tc_per"):
         achieved = v["work"] / sec / 1e12
-        name = "k_gemm_tc" if cat == "gemm_tc" else "k_gemm_tc_acc"
+        name, nprod, mode = {"gemm_tc": ("k_gemm_tc", 3, "one accumulator, 2 planes"),
+                             "gemm_tc_acc": ("k_gemm_tc_acc", 6, "drained every K = 16 step, 3 planes"),
+                             "gemm_tc_per": ("k_gemm_tc_per", 3, "drained every 64 steps, 2 planes")}[cat]
         ratio, src = profile_figure(f"{name}_ellipse_n4096_mixed.md", "dram_bytes_per_algorithmic_byte")
         return {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
+                "issued_frac": nprod * achieved / bf16s,
                 "traffic": (ratio * v["bytes"] / per) if ratio else None,
                 "algorithmic_bytes_per_launch": v["bytes"] / per, "traffic_source": src,
-                "kernel": f"{name} (tcgen05 split-bf16 complex operator product)",
-                "work": "useful complex-product flops 2*M*Nc*K (split-bf16 issues nprod x these)",
+                "kernel": f"{name} (tcgen05 split-bf16 complex operator product, {mode})",
+                "work": f"useful complex-product flops 2*M*Nc*K; split-bf16 issues {nprod} products of these "
+                        f"(issued_frac)",
                 "peak_source": "measured bf16 sustained (cuBLAS, MEASURED_PEAKS.json)", "launches": per,
                 "ms_total": v["ms"]}
     if cat == "fft":
         achieved = v["bytes"] / sec / 1e9
+        bpu, src = profile_figure("k_circ_pass_superellipse_n32768_mixed.md", "dram_bytes_per_algorithmic_byte")
         return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": "k_fft_tile (C_c, C_c^-1 applies: two transforms + scaling)",
-                "work": "4 x 16 N bytes per column and apply", "peak_source": "measured copy (MEASURED_PEAKS.json)",
-                "launches": per, "ms_total": v["ms"]}
+                "traffic": (bpu * v["bytes"] / per) if bpu else None, "traffic_source": src,
+                "algorithmic_bytes_per_launch": v["bytes"] / per,
+                "kernel": "k_circ_pass1/2/3 (FP32 circulant applies C_c, C_c^-1: three passes)",
+                "work": "64 N bytes per column and apply (FP64 in and out, one FP32 scratch round trip)",
+                "peak_source": "measured copy (MEASURED_PEAKS.json)", "launches": per, "ms_total": v["ms"]}
     if cat in ("assembly", "assembly_fast"):
         units = v["work"] / per                      # far point pairs of the kernel's tiles, per launch
         fp64 = cat == "assembly"
@@ -458,7 +465,7 @@ def main():
         if _lib.load().wcs_fma_rate(prec, iters, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(r)) == 0:
             fma[prec] = r.value
     rooflines = {cat: roofline_entry(cat, prof, hbm, bf16s, fma)
-                 for cat in ("assembly", "assembly_fast", "gemm_tc", "gemm_tc_acc", "fft")}
+                 for cat in ("assembly", "assembly_fast", "gemm_tc", "gemm_tc_acc", "gemm_tc_per", "fft")}
     rooflines = {k: v for k, v in rooflines.items() if v}
     # the headline roofline is that of the kernel category with the largest share of the step
     share = {k: prof[k]["ms"] for k in rooflines}

@@ -453,7 +453,7 @@ uint64_t wcs_launch_count(void);
  * each instrumented launch (enable != 0 turns it on; off by default). */
 int wcs_profile(wcs_ctx* ctx, int enable);
 
-/* Sum the recorded launches by category (synchronises): out_host gets 15 x 4
+/* Sum the recorded launches by category (synchronises): out_host gets 16 x 4
  * doubles {launches, total ms, algorithmic work, bytes} for the categories, in
  * order: tensor-core contraction (work = useful real flops 2 M Nc K of the
  * complex product), assembly (work = far point pairs), FFT circulant applies
@@ -461,7 +461,9 @@ int wcs_profile(wcs_ctx* ctx, int enable);
  * contraction, skeleton sampling, projection, orthonormalisation, V_w,
  * capacitance inverse, exact contraction (work = useful flops, as the first),
  * FP32 far-pair assembly kernel (work = far point pairs of its tiles; the
- * assembly category then counts the FP64 kernel over the other tiles).
+ * assembly category then counts the FP64 kernel over the other tiles),
+ * periodically drained tensor-core contraction (work as the first; the
+ * drained category then counts the every-step drain only).
  * reset != 0 clears the records. */
 int wcs_profile_read(wcs_ctx* ctx, int reset, double* out_host);
 

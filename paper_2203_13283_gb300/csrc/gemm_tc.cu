@@ -635,6 +635,207 @@ static int launch_tc_acc(const TcOperand& A, const TcOperand& B, TcArgs& args, c
   return 0;
 }
 
+// ----------------------------------------------------------------------------- periodic drain, wide tile
+// The periodic mode (two planes, three products, accumulator drained every
+// `drain` K = 16 steps) on 128 x 256 tiles.  With 128 x 128 tiles its three
+// products per 64 KB stage (96 flop per staged byte) starved the tensor pipe
+// on the L2-to-shared-memory feed; 128 x 256 tiles carry 131 flop per byte,
+// like the one-accumulator kernel.  Two TMEM accumulators of 256 columns fill
+// the 512 TMEM columns, so the drained sums stay in registers: warp w of the
+// eight drain warps owns TMEM lanes 32 (w % 4) and columns 128 (w / 4), 128
+// FP32 sums per thread.  A single level of sums suffices: K / (16 drain)
+// additions (64 at K = 65536) round far below this mode's ~1e-5.
+constexpr int PER_NT = 256, PER_THREADS = 320;
+
+template <int STAGES>
+struct PerSmem {
+  static constexpr int A_BYTES = TC_BM * TC_BK * 2;        // 16 KB
+  static constexpr int B_BYTES = PER_NT * TC_BK * 2;       // 32 KB
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(PER_THREADS, 1)
+    k_gemm_tc_per(const __grid_constant__ CUtensorMap mA0, const __grid_constant__ CUtensorMap mA1,
+                  const __grid_constant__ CUtensorMap mB0, const __grid_constant__ CUtensorMap mB1, TcArgs args) {
+  using L = PerSmem<STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  if (*(volatile int*)args.err != 0) return;
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + STAGES * L::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;      // [2] MMA -> drain
+  uint64_t* tempty = tfull + 2;          // [2] drain -> MMA
+  uint32_t* tslot = (uint32_t*)(tempty + 2);
+  volatile int* abort_flag = (volatile int*)(tslot + 1);
+  volatile int* issued = (volatile int*)(tslot + 2);
+  volatile int* consumed = (volatile int*)(tslot + 3);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * TC_BM;
+  const int n0 = blockIdx.x * PER_NT;
+  const int nk = (args.K + TC_BK - 1) / TC_BK;
+  const int nsteps = nk * (TC_BK / 16);
+  const int drain = args.drain > 1 ? args.drain : 1;
+  const int ngroups = (nsteps + drain - 1) / drain;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < STAGES; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
+    for (int q = 0; q < 2; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], 8); }
+    *abort_flag = 0;
+    *issued = 0;
+    *consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(512u));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(PER_NT >> 3) << 17) |
+                         ((uint32_t)(TC_BM >> 4) << 24);
+
+  float sum[128];
+#pragma unroll
+  for (int i = 0; i < 128; ++i) sum[i] = 0.f;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      for (int kb = 0; kb < nk; ++kb) {
+        const int st = kb % STAGES;
+        if (kb >= STAGES) {
+          if (!mbar_wait(&empty[st], ((kb / STAGES) + 1) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 31; break; }
+        }
+        if (*abort_flag) break;
+        uint8_t* sp = smem + st * L::STAGE_BYTES;
+        mbar_expect_tx(&full[st], L::STAGE_BYTES);
+        const int k0 = kb * TC_BK;
+        tma_load_2d(sp, &mA0, &full[st], k0, m0);
+        tma_load_2d(sp + L::A_BYTES, &mA1, &full[st], k0, m0);
+        tma_load_2d(sp + 2 * L::A_BYTES, &mB0, &full[st], k0, n0);
+        tma_load_2d(sp + 2 * L::A_BYTES + L::B_BYTES, &mB1, &full[st], k0, n0);
+        *issued = kb + 1;
+      }
+    }
+  } else if (warp == 9) {
+    if (lane == 0) {
+      // products of order < 2, smallest first: A1 B0, A0 B1, A0 B0
+      constexpr int IA[3] = {1, 0, 0};
+      constexpr int IB[3] = {0, 1, 0};
+      int b = 0, ingroup = 0, q = 0;
+      bool ok = true;
+      for (int kb = 0; kb < nk && ok; ++kb) {
+        const int st = kb % STAGES;
+        if (!mbar_wait(&full[st], (kb / STAGES) & 1, WAIT_LIMIT, args.err)) { *abort_flag = 32; break; }
+        *consumed = kb + 1;
+        if (*abort_flag) break;
+        tc_fence_after();
+        const uint8_t* sp = smem + st * L::STAGE_BYTES;
+        uint64_t da[3], db[3];
+#pragma unroll
+        for (int p = 0; p < 3; ++p) {
+          da[p] = sw128_desc(sp + IA[p] * L::A_BYTES);
+          db[p] = sw128_desc(sp + 2 * L::A_BYTES + IB[p] * L::B_BYTES);
+        }
+#pragma unroll
+        for (int kk = 0; kk < TC_BK / 16; ++kk) {
+          if (ingroup == 0 && q >= 2) {
+            if (!mbar_wait(&tempty[b], ((q / 2) - 1) & 1, WAIT_LIMIT, args.err)) {
+              *abort_flag = 35; ok = false; break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t dt = tmem + (uint32_t)(b * PER_NT);
+#pragma unroll
+          for (int p = 0; p < 3; ++p)
+            mma_bf16(dt, da[p] + (uint64_t)(2 * kk), db[p] + (uint64_t)(2 * kk), idesc,
+                     (ingroup == 0 && p == 0) ? 0u : 1u);
+          ++ingroup;
+          if (ingroup == drain || (kb == nk - 1 && kk == TC_BK / 16 - 1)) {
+            mma_commit(&tfull[b]);
+            ingroup = 0;
+            ++q;
+            b ^= 1;
+          }
+        }
+        mma_commit(&empty[st]);
+      }
+    }
+  } else {
+    // drain warps: sums of their 32 lanes x 128 columns in registers
+    const int lanebase = 32 * (warp & 3), colbase = 128 * (warp >> 2);
+    for (int g = 0; g < ngroups; ++g) {
+      const int b = g & 1;
+      bool got = mbar_wait_sleep(&tfull[b], (g >> 1) & 1, WAIT_LIMIT, args.err, 256u);
+      got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
+      if (!got) { if (lane == 0) atomicCAS((int*)abort_flag, 0, 34); break; }
+      tc_fence_after();
+#pragma unroll
+      for (int c4 = 0; c4 < 4; ++c4) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * PER_NT + colbase + 32 * c4), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) sum[32 * c4 + i] += v[i];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
+    }
+  }
+  __syncthreads();
+  const bool ok = (*abort_flag == 0);
+  if (!ok) {
+    if (threadIdx.x == 0) {
+      const int zero_flag = 0;
+      atomicExch(args.err, 1000 * (*abort_flag) + (int)(blockIdx.x % 1000));
+      for (int kb = *consumed; kb < *issued; ++kb)
+        (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
+    }
+  } else if (warp < 8) {
+    const int lanebase = 32 * (warp & 3), colbase = 128 * (warp >> 2);
+#pragma unroll
+    for (int c4 = 0; c4 < 4; ++c4) {
+      float out[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) out[i] = sum[32 * c4 + i];
+      epilogue_store(args, m0 + lanebase + lane, n0 + colbase + 32 * c4, out);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u));
+  }
+}
+
+template <int STAGES>
+static int launch_tc_per(const TcOperand& A, const TcOperand& B, TcArgs& args, cudaStream_t s) {
+  using L = PerSmem<STAGES>;
+  CUtensorMap ma[2], mb[2];
+  std::memset(ma, 0, sizeof(ma));
+  std::memset(mb, 0, sizeof(mb));
+  for (int p = 0; p < 2; ++p) TRY_TC(make_map(&ma[p], A.plane[p], args.M, args.K, A.ld, TC_BM));
+  for (int p = 0; p < 2; ++p) TRY_TC(make_map(&mb[p], B.plane[p], args.Nc, args.K, B.ld, PER_NT));
+  auto kern = k_gemm_tc_per<STAGES>;
+  static DeviceOnce attr;
+  if (attr.need()) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+    if (e != cudaSuccess) { set_error(std::string("gemm_tc: shared-memory opt-in: ") + cudaGetErrorString(e)); return 3; }
+    attr.done();
+  }
+  dim3 grid((unsigned)((args.Nc + PER_NT - 1) / PER_NT), (unsigned)((args.M + TC_BM - 1) / TC_BM));
+  kern<<<grid, PER_THREADS, L::TOTAL, s>>>(ma[0], ma[1], mb[0], mb[1], args);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) { set_error(std::string("gemm_tc_per launch: ") + cudaGetErrorString(e)); return 3; }
+  return 0;
+}
+
 int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s) {
   if (args.M <= 0 || args.Nc <= 0 || args.K <= 0) return 0;
   if (args.nprod < 1 || args.nprod > 6) { set_error("gemm_tc: 1..6 products"); return 1; }
@@ -650,6 +851,9 @@ int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaSt
     if (!same) { set_error("gemm_tc_accurate: needs the full product list of tc_products"); return 1; }
   }
   if (A.planes == 3 && B.planes == 3) return launch_tc_acc<3, 3, 2>(A, B, args, s);
+  // two planes drained every 16 or more steps on a grid of more than one
+  // column tile: the wide-tile kernel
+  if (A.planes == 2 && B.planes == 2 && args.drain >= 16 && args.Nc > 128) return launch_tc_per<2>(A, B, args, s);
   if (A.planes == 2 && B.planes == 2) return launch_tc_acc<2, 2, 3>(A, B, args, s);
   set_error("gemm_tc_accurate: plane combination not built");
   return 1;

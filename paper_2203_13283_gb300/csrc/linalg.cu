@@ -130,10 +130,11 @@ __global__ void k_gram_fwd(const zd* __restrict__ X, int64_t ldx, zd* __restrict
   zd* u = U + c * n;
   zd acc = mkz(0.0);
   const int64_t warm = GI_WARM;  // the input is periodic: wrapping more than once is fine
+  int64_t ii = ((i0 - warm) % n + n) % n;   // index mod n, advanced with a compare (no division per step)
   for (int64_t i = i0 - warm; i < i1; ++i) {
-    const int64_t ii = (i % n + n) % n;
     acc = x[ii] + rho * acc;
     if (i >= i0) u[ii] = acc;
+    if (++ii == n) ii = 0;
   }
 }
 
@@ -148,10 +149,11 @@ __global__ void k_gram_bwd(const zd* __restrict__ U, zd* __restrict__ Y, int64_t
   zd* y = Y + c * ldy;
   zd acc = mkz(0.0);
   const int64_t warm = GI_WARM;
+  int64_t ii = (i1 - 1 + warm) % n;
   for (int64_t i = i1 - 1 + warm; i >= i0; --i) {
-    const int64_t ii = (i % n + n) % n;
     acc = u[ii] + rho * acc;
     if (i < i1) y[ii] = scale * acc;
+    if (--ii < 0) ii = n - 1;
   }
 }
 
@@ -177,7 +179,7 @@ __global__ void k_gram_apply(const zd* __restrict__ X, int64_t ldx, zd* __restri
   const int64_t c = blockIdx.y;
   if (i >= n) return;
   const zd* x = X + c * ldx;
-  const zd xm = x[(i - 1 + n) % n], x0 = x[i], xp = x[(i + 1) % n];
+  const zd xm = x[i == 0 ? n - 1 : i - 1], x0 = x[i], xp = x[i == n - 1 ? 0 : i + 1];
   zd r = a6 * (xm + xp) + a4 * x0;
   zd* y = Y + c * ldy;
   if (beta != 0.0) r += beta * y[i];

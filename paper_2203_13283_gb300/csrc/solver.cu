@@ -110,7 +110,7 @@ struct wcs_ctx {
 enum StatCat { CAT_GEMM_TC = 0, CAT_ASSEMBLY = 1, CAT_FFT = 2, CAT_ZGEMM = 3, CAT_SKELETON = 4,
                CAT_FACTOR = 5, CAT_SOLVE = 6, CAT_GEMM_ACC = 7, CAT_SAMPLE = 8, CAT_PROJECT = 9,
                CAT_ORTH = 10, CAT_VW = 11, CAT_INVERSE = 12, CAT_GEMM_EXACT = 13, CAT_ASSEMBLY_FAST = 14,
-               CAT_COUNT = 15 };
+               CAT_GEMM_PER = 15, CAT_COUNT = 16 };
 
 struct ProfScope {
   wcs_ctx* c;
@@ -250,7 +250,8 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.err = (int*)c->tcerr.p;
   t.drain = (mode == PREC_PERIODIC) ? 64 : 1;
   const bool drained = (mode == PREC_ACCURATE || mode == PREC_PERIODIC);
-  ProfScope ps(c, drained ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K,
+  ProfScope ps(c, mode == PREC_PERIODIC ? CAT_GEMM_PER : (drained ? CAT_GEMM_ACC : CAT_GEMM_TC),
+               2.0 * t.M * (double)t.Nc * t.K,
                tc_bytes(t, P, P));
   TRY(drained ? gemm_tc_accurate(A, B, t, c->s) : gemm_tc(A, B, t, c->s));
   if (debug_finite()) {
@@ -1377,7 +1378,9 @@ static int exact_square(wcs_ctx* c, const zd* A, int64_t r, const zd* X, int64_t
   note_launch();
   int64_t lda = 0, ncha = 0, ldb = 0, nchb = 0;
   size_t sa = 0, ea = 0, sb = 0, eb = 0;
-  const int64_t G = 256;
+  // columns per pass: wide passes keep the 21 slice-pair launches large
+  // (the FP32 partials take nchunks x 2G x r floats, 268 MB at r = 4096)
+  const int64_t G = std::min<int64_t>(1024, std::max<int64_t>(cols, 1));
   exact_operand_alloc_bytes(r, 2 * r, &lda, &ncha, &sa, &ea);
   exact_operand_alloc_bytes(2 * G, 2 * r, &ldb, &nchb, &sb, &eb);
   const size_t sa2 = ((sa + 255) / 256) * 256, sb2 = ((sb + 255) / 256) * 256;
@@ -1487,7 +1490,8 @@ int wcs_factor(wcs_ctx* c) {
       if (!(res < 0.1 * std::sqrt((double)r))) { set_error("capacitance iteration did not converge"); return WCS_ERR_SINGULAR; }
       // The split-bf16 iteration stalls near 1e-4 per direction.  Two closing
       // steps with exact products (each squares the residual) carry K^-1 to
-      // FP64 accuracy, and a third exact product measures ||I - K X||_F.
+      // the products' own precision (42 bits below each chunk's scale,
+      // ~1e-11 per direction), and a third exact product measures ||I - K X||_F.
       {
         for (int it = 0; it < 2; ++it) {
           TRY(exact_square(c, Kb.z(), r, X, r, T.z()));          // T = K X
@@ -1978,9 +1982,8 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
   } else {
     // Mixed form.  The first residual is formed with the drained accumulation
     // (~1e-7) and then carried forward by updates R <- R - C dx in the
-    // periodic-drain precision: their error is ~1e-5 of |C dx|, i.e. far
-    // below the residual once |dx| is small, and no more expensive than a
-    // fast product while it is large.  Each round ends with a recomputed
+    // periodic-drain precision (~2e-5 of |C dx|, far below the residual once
+    // |dx| is small) or, while |C dx| is large, the drained one.  Each round ends with a recomputed
     // residual, so the reported residual is the true one; rounds stop when it
     // reaches refine_tol or stops decreasing (its floor is the accuracy of
     // the drained product).
@@ -1996,7 +1999,13 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
         TRY(axpby(N, cc, mkz(1.0), dx, N, mkz(1.0), x, ldx, c->s));
         ++it;
         if (ends_round(upd, prev_upd)) break;
-        TRY(apply_C(c, dx, N, T, N, cc, adj, PREC_PERIODIC));
+        // the update's error is ~2e-5 of |C dx| ~ the carried residual in the
+        // periodic drain: while that would exceed a tenth of the target (a
+        // poor approximate inverse, a large residual), the drained product
+        // (~3e-7) carries it instead, so the carried residual does not drift
+        // from the true one
+        const int m = (2e-5 * upd <= 0.1 * c->opt.refine_tol) ? PREC_PERIODIC : PREC_ACCURATE;
+        TRY(apply_C(c, dx, N, T, N, cc, adj, m));
         TRY(axpby(N, cc, mkz(-1.0), T, N, mkz(1.0), R, N, c->s));
         prev_upd = upd;
         TRY(worst_of(upd));

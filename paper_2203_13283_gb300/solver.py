@@ -255,7 +255,7 @@ class Solver:
         return (out[0::2] + 1j * out[1::2])[:i1 - i0]
 
     PROFILE_CATS = ("gemm_tc", "assembly", "fft", "zgemm", "skeleton", "factor", "solve", "gemm_tc_acc",
-                    "sample", "project", "orth", "vw", "inverse", "gemm_exact", "assembly_fast")
+                    "sample", "project", "orth", "vw", "inverse", "gemm_exact", "assembly_fast", "gemm_tc_per")
 
     def profile(self, enable=True):
         check(self.lib.wcs_profile(self.h, 1 if enable else 0))

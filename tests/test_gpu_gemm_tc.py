@@ -61,12 +61,14 @@ def test_split_bf16_gemm_accurate(M, Nc, K, planes):
     assert err < bound, err
 
 
-@pytest.mark.parametrize("M,Nc,K", [(256, 128, 65536), (300, 200, 5000)])
+@pytest.mark.parametrize("M,Nc,K", [(256, 128, 65536), (300, 200, 5000), (384, 640, 20000)])
 @pytest.mark.parametrize("planes", [2, 3])
 def test_split_bf16_gemm_periodic_drain(M, Nc, K, planes):
     """Accumulator drained every 64 steps (K = 1024): its truncation error
     spans at most 64 steps, so it stays near 1e-5 at any K, between the
-    one-accumulator contraction and the every-step drain."""
+    one-accumulator contraction and the every-step drain.  Two planes with
+    Nc > 128 run on the 128 x 256 tile with register sums (ragged and
+    multi-tile column counts here)."""
     built()
     from paper_2203_13283_gb300.solver import gemm_split_bf16
     g = torch.Generator(device="cpu").manual_seed(M + 5 * Nc + K)
