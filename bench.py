@@ -200,7 +200,9 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
         name, nprod, mode = {"gemm_tc": ("k_gemm_tc", 3, "one accumulator, 2 planes"),
                              "gemm_tc_acc": ("k_gemm_tc_acc", 6, "drained every K = 16 step, 3 planes"),
                              "gemm_tc_per": ("k_gemm_tc_per", 3, "drained every 64 steps, 2 planes")}[cat]
-        ratio, src = profile_figure(f"{name}_ellipse_n4096_mixed.md", "dram_bytes_per_algorithmic_byte")
+        prof_file = {"gemm_tc": "k_gemm_tc_ellipse_n4096_mixed.md", "gemm_tc_acc": "k_gemm_tc_acc_ellipse_n4096_mixed.md",
+                     "gemm_tc_per": "k_gemm_tc_per_superellipse_n4096_mixed.md"}[cat]
+        ratio, src = profile_figure(prof_file, "dram_bytes_per_algorithmic_byte")
         return {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
                 "issued_frac": nprod * achieved / bf16s,
                 "traffic": (ratio * v["bytes"] / per) if ratio else None,
@@ -457,6 +459,20 @@ def main():
            "d2h_bytes_per_step": int(jh.numel() * 16)}
     del jh
 
+    # the Woodbury apply alone (Eq. 9: Y = C_c^-1 B, X = Y - W~ (V^T Y)) on the
+    # batch's 1024 columns: algorithmic bytes = read b and write x (32 N per
+    # column) plus V_w and W~ once (2 x 16 N r)
+    jb = j.t()
+    S.woodbury_apply(jb)
+    w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    for _ in range(3):
+        S.woodbury_apply(jb)
+    w1.record(stream)
+    w1.synchronize()
+    wood_s = w0.elapsed_time(w1) / 3e3
+    wood_bytes = 32.0 * w["N"] * B + 32.0 * w["N"] * max(info["rank"], 0)
+
     hbm, bf16, bf16s, src = peaks()
     import ctypes
     fma = {}
@@ -464,6 +480,9 @@ def main():
         r = ctypes.c_double(0.0)
         if _lib.load().wcs_fma_rate(prec, iters, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(r)) == 0:
             fma[prec] = r.value
+    woodbury_only = {"rhs_per_s": B / wood_s, "ms": wood_s * 1e3, "achieved_gbs": wood_bytes / wood_s / 1e9,
+                     "peak_gbs": hbm, "frac": wood_bytes / wood_s / 1e9 / hbm,
+                     "work": "32 N bytes per column (b in, x out) + 2 x 16 N r (V_w, W~), algorithmic"}
     rooflines = {cat: roofline_entry(cat, prof, hbm, bf16s, fma)
                  for cat in ("assembly", "assembly_fast", "gemm_tc", "gemm_tc_acc", "gemm_tc_per", "fft")}
     rooflines = {k: v for k, v in rooflines.items() if v}
@@ -484,7 +503,8 @@ def main():
                    "residual_history": last["history"],
                    "refine_steps_to_1e-6": steps_to(last["history"], 1e-6),
                    "refine_steps_to_1e-10": steps_to(last["history"], 1e-10),
-                   "zfast": info["zfast"], "capacitance_residual": info["capacitance_residual"], "setup_s": statistics.median(setups), "solve_s": statistics.median(solves),
+                   "zfast": info["zfast"], "capacitance_residual": info["capacitance_residual"],
+                   "setup_s": statistics.median(setups), "solve_s": statistics.median(solves),
                    "l2": "operators (tens of GB) exceed L2: no flush needed", "parallelism": f"replicas{world}"},
         "setup_s": statistics.median(setups),
         "e2e": e2e, "clocks": clk, "roofline": roof, "rooflines": rooflines, "roofline_kernel": dominant,
@@ -493,6 +513,7 @@ def main():
         "assembly_pairs_per_s": (prof["assembly"]["work"] / (prof["assembly"]["ms"] / 1e3))
         if prof["assembly"]["launches"] else None,
         "gpu_launches": launches,
+        "woodbury_only": woodbury_only,
     }
 
     stride = max(1, B // max(args.fp64_rhs, 1))

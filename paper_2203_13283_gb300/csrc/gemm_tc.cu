@@ -175,6 +175,24 @@ __device__ __forceinline__ void tmem_st64(uint32_t taddr, const float (&v)[64]) 
       : "memory");
 }
 
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+  uint32_t r[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) r[i] = __float_as_uint(v[i]);
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%32], {"
+      "%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31"
+      "};\n"
+      "tcgen05.wait::st.sync.aligned;"
+      :
+      : "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31]), "r"(taddr)
+      : "memory");
+}
+
 // ----------------------------------------------------------------------------- kernel
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 128;
 constexpr long long WAIT_LIMIT = 4000000000ll;  // SM cycles (~2 s) before a wait is declared stuck
@@ -418,12 +436,15 @@ __global__ void k_splitk_reduce(TcArgs a, int splits) {
 // TMEM sum spans more than one step.  Register sums are two-level (an inner
 // sum over 64 steps folded into an outer sum), which keeps the FP32 rounding
 // of ~K/16 additions near 1e-7 at a quarter of the cost of compensated
-// summation.  Tile 128 x 128; warps 0-7 drain (warp w: TMEM lanes 32 (w % 4),
-// columns 64 (w / 4)), warp 8 loads (TMA), warp 9 issues the MMAs.  The drain
-// is bound by the latency of the TMEM load, so each warp moves its 64 columns
-// in one load and keeps only the inner sums in registers; the outer sums live
-// in the last 128 TMEM columns, after three step buffers (384 columns).
-constexpr int ACC_NT = 128, ACC_THREADS = 320, ACC_FOLD = 64, ACC_NBUF = 3;
+// summation.  Tile 128 x 128; warps 0-15 drain (warp w: TMEM lanes 32 (w % 4),
+// columns 32 (w / 4)), warp 16 loads (TMA), warp 17 issues the MMAs.  The
+// drain is bound by the latency of the TMEM load, so sixteen warps each move
+// 32 columns per step (eight warps of 64 columns kept the tensor pipe at ~70%
+// of its issue rate with six products per step) and keep only the inner sums
+// in registers; the outer sums live in the last 128 TMEM columns, after three
+// step buffers (384 columns).
+constexpr int ACC_DW = 16;                       // drain warps
+constexpr int ACC_NT = 128, ACC_THREADS = 32 * (ACC_DW + 2), ACC_FOLD = 64, ACC_NBUF = 3;
 constexpr int ACC_OUTER = ACC_NBUF * ACC_NT;   // first TMEM column of the outer sums
 
 template <int PA, int PB, int STAGES>
@@ -464,7 +485,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < STAGES; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
-    for (int q = 0; q < ACC_NBUF; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], 8); }
+    for (int q = 0; q < ACC_NBUF; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], ACC_DW); }
     *abort_flag = 0;
     *issued = 0;
     *consumed = 0;
@@ -484,11 +505,11 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ACC_NT >> 3) << 17) |
                          ((uint32_t)(TC_BM >> 4) << 24);
 
-  float inner[64];
+  float inner[32];
 #pragma unroll
-  for (int i = 0; i < 64; ++i) inner[i] = 0.f;
+  for (int i = 0; i < 32; ++i) inner[i] = 0.f;
 
-  if (warp == 8) {
+  if (warp == ACC_DW) {
     if (lane == 0) {
       for (int kb = 0; kb < nk; ++kb) {
         const int st = kb % STAGES;
@@ -506,7 +527,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
         *issued = kb + 1;
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == ACC_DW + 1) {
     if (lane == 0) {
       // products of order < planes, smallest first (the order of tc_products,
       // checked on the host); descriptors are formed once per stage and the
@@ -556,12 +577,12 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
     }
   } else {
     // drain warps
-    const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
-    const uint32_t touter = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colhalf);
-    float v[64];
+    const int lanebase = 32 * (warp & 3), colq = 32 * (warp >> 2);
+    const uint32_t touter = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colq);
+    float v[32];
 #pragma unroll
-    for (int i = 0; i < 64; ++i) v[i] = 0.f;
-    tmem_st64(touter, v);
+    for (int i = 0; i < 32; ++i) v[i] = 0.f;
+    tmem_st32(touter, v);
     for (int g = 0; g < ngroups; ++g) {
       const int b = g % ACC_NBUF;
       bool got = (drain > 1) ? mbar_wait_sleep(&tfull[b], (g / ACC_NBUF) & 1, WAIT_LIMIT, args.err, 256u)
@@ -569,17 +590,17 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
       if (!got) { if (lane == 0) atomicCAS((int*)abort_flag, 0, 24); break; }
       tc_fence_after();
-      tmem_ld64(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colhalf), v);
+      tmem_ld32(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colq), v);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
 #pragma unroll
-      for (int i = 0; i < 64; ++i) inner[i] += v[i];
+      for (int i = 0; i < 32; ++i) inner[i] += v[i];
       if ((g % ACC_FOLD) == ACC_FOLD - 1) {
-        tmem_ld64(touter, v);
+        tmem_ld32(touter, v);
 #pragma unroll
-        for (int i = 0; i < 64; ++i) { v[i] += inner[i]; inner[i] = 0.f; }
-        tmem_st64(touter, v);
+        for (int i = 0; i < 32; ++i) { v[i] += inner[i]; inner[i] = 0.f; }
+        tmem_st32(touter, v);
       }
     }
   }
@@ -592,16 +613,13 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       for (int kb = *consumed; kb < *issued; ++kb)
         (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
     }
-  } else if (warp < 8) {
-    const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
-    float v[64], out[32];
-    tmem_ld64(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colhalf), v);
+  } else if (warp < ACC_DW) {
+    const int lanebase = 32 * (warp & 3), colq = 32 * (warp >> 2);
+    float v[32], out[32];
+    tmem_ld32(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colq), v);
 #pragma unroll
     for (int i = 0; i < 32; ++i) out[i] = v[i] + inner[i];
-    epilogue_store(args, m0 + lanebase + lane, n0 + colhalf, out);
-#pragma unroll
-    for (int i = 0; i < 32; ++i) out[i] = v[32 + i] + inner[32 + i];
-    epilogue_store(args, m0 + lanebase + lane, n0 + colhalf + 32, out);
+    epilogue_store(args, m0 + lanebase + lane, n0 + colq, out);
   }
   tc_fence_before();
   __syncthreads();
