@@ -65,6 +65,32 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
   const zd kt = A.kt;
   if (d > A.near_band) {
     const int q = A.q_far;
+    // Element pairs whose point pairs all lie in the expansion range share
+    // the phase and damping of the expansion, evaluated once at the
+    // reference argument x0 = k |c_e - c_f| (c: mean of the element's
+    // points, every point within 0.45 h of it, so |k R - x0| <= 0.9 k h).
+    bool rot = false;
+    double x0 = 0.0, damp0 = 0.0;
+    zd ph0 = mkz(0.0);
+    if (A.kt_pair && A.rot_ok) {
+      double cex = 0.0, cey = 0.0, cfx = 0.0, cfy = 0.0;
+      for (int p = 0; p < q; ++p) {
+        cex += A.far.x[e * q + p];
+        cey += A.far.y[e * q + p];
+        cfx += A.far.x[f * q + p];
+        cfy += A.far.y[f * q + p];
+      }
+      const double iq = 1.0 / (double)q;
+      const double ddx = (cex - cfx) * iq, ddy = (cey - cfy) * iq;
+      x0 = k * sqrt(ddx * ddx + ddy * ddy);
+      if (x0 >= 20.0 + k * h) {
+        rot = true;
+        double s0, c0;
+        sincos(x0 - 0.25 * WCS_PI, &s0, &c0);
+        ph0 = mkz(c0, s0);
+        damp0 = exp(-x0 * A.ktp.t);
+      }
+    }
     for (int p = 0; p < q; ++p) {
       const int64_t ip = e * q + p;
       const double xt = A.far.x[ip], yt = A.far.y[ip], nxt = A.far.nx[ip], nyt = A.far.ny[ip];
@@ -73,11 +99,22 @@ __device__ void pair_integrals(const AsmArgs& A, int64_t e, int64_t f, PairOut& 
         const int64_t ir = f * q + r;
         const double dx = xt - A.far.x[ir], dy = yt - A.far.y[ir];
         const double nxs = A.far.nx[ir], nys = A.far.ny[ir];
-        const double R = sqrt(dx * dx + dy * dy);
-        const double gg = (dx * nxs + dy * nys) / R;
         const double nd = nxt * nxs + nyt * nys;
         Hankel01 Hk, Ht;
-        hankel_k_kt(A, R, Hk, Ht);
+        double R, gg;
+        if (rot) {
+          // one reciprocal square root each for 1/R and for (k R)^-1/2
+          const double R2 = dx * dx + dy * dy;
+          const double ri = rsqrt(R2);
+          R = R2 * ri;
+          gg = (dx * nxs + dy * nys) * ri;
+          const double x = k * R;
+          hankel01_asymptotic_rot(x, rsqrt(x), x0, ph0, damp0, A.ktp, Hk, Ht);
+        } else {
+          R = sqrt(dx * dx + dy * dy);
+          gg = (dx * nxs + dy * nys) / R;
+          hankel_k_kt(A, R, Hk, Ht);
+        }
         const zd gk = i4(Hk.H0);
         const zd gt = i4(Ht.H0);
         const zd dgk = (k * gg) * i4(Hk.H1);

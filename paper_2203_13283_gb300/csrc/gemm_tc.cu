@@ -436,15 +436,12 @@ __global__ void k_splitk_reduce(TcArgs a, int splits) {
 // TMEM sum spans more than one step.  Register sums are two-level (an inner
 // sum over 64 steps folded into an outer sum), which keeps the FP32 rounding
 // of ~K/16 additions near 1e-7 at a quarter of the cost of compensated
-// summation.  Tile 128 x 128; warps 0-15 drain (warp w: TMEM lanes 32 (w % 4),
-// columns 32 (w / 4)), warp 16 loads (TMA), warp 17 issues the MMAs.  The
-// drain is bound by the latency of the TMEM load, so sixteen warps each move
-// 32 columns per step (eight warps of 64 columns kept the tensor pipe at ~70%
-// of its issue rate with six products per step) and keep only the inner sums
-// in registers; the outer sums live in the last 128 TMEM columns, after three
-// step buffers (384 columns).
-constexpr int ACC_DW = 16;                       // drain warps
-constexpr int ACC_NT = 128, ACC_THREADS = 32 * (ACC_DW + 2), ACC_FOLD = 64, ACC_NBUF = 3;
+// summation.  Tile 128 x 128; warps 0-7 drain (warp w: TMEM lanes 32 (w % 4),
+// columns 64 (w / 4)), warp 8 loads (TMA), warp 9 issues the MMAs.  The drain
+// is bound by the latency of the TMEM load, so each warp moves its 64 columns
+// in one load and keeps only the inner sums in registers; the outer sums live
+// in the last 128 TMEM columns, after three step buffers (384 columns).
+constexpr int ACC_NT = 128, ACC_THREADS = 320, ACC_FOLD = 64, ACC_NBUF = 3;
 constexpr int ACC_OUTER = ACC_NBUF * ACC_NT;   // first TMEM column of the outer sums
 
 template <int PA, int PB, int STAGES>
@@ -485,7 +482,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
 
   if (threadIdx.x == 0) {
     for (int q = 0; q < STAGES; ++q) { mbar_init(&full[q], 1); mbar_init(&empty[q], 1); }
-    for (int q = 0; q < ACC_NBUF; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], ACC_DW); }
+    for (int q = 0; q < ACC_NBUF; ++q) { mbar_init(&tfull[q], 1); mbar_init(&tempty[q], 8); }
     *abort_flag = 0;
     *issued = 0;
     *consumed = 0;
@@ -505,11 +502,11 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
   const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(ACC_NT >> 3) << 17) |
                          ((uint32_t)(TC_BM >> 4) << 24);
 
-  float inner[32];
+  float inner[64];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) inner[i] = 0.f;
+  for (int i = 0; i < 64; ++i) inner[i] = 0.f;
 
-  if (warp == ACC_DW) {
+  if (warp == 8) {
     if (lane == 0) {
       for (int kb = 0; kb < nk; ++kb) {
         const int st = kb % STAGES;
@@ -527,7 +524,7 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
         *issued = kb + 1;
       }
     }
-  } else if (warp == ACC_DW + 1) {
+  } else if (warp == 9) {
     if (lane == 0) {
       // products of order < planes, smallest first (the order of tc_products,
       // checked on the host); descriptors are formed once per stage and the
@@ -577,12 +574,12 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
     }
   } else {
     // drain warps
-    const int lanebase = 32 * (warp & 3), colq = 32 * (warp >> 2);
-    const uint32_t touter = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colq);
-    float v[32];
+    const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
+    const uint32_t touter = tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colhalf);
+    float v[64];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = 0.f;
-    tmem_st32(touter, v);
+    for (int i = 0; i < 64; ++i) v[i] = 0.f;
+    tmem_st64(touter, v);
     for (int g = 0; g < ngroups; ++g) {
       const int b = g % ACC_NBUF;
       bool got = (drain > 1) ? mbar_wait_sleep(&tfull[b], (g / ACC_NBUF) & 1, WAIT_LIMIT, args.err, 256u)
@@ -590,17 +587,17 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       got = __all_sync(0xffffffffu, got) && (__shfl_sync(0xffffffffu, *abort_flag, 0) == 0);
       if (!got) { if (lane == 0) atomicCAS((int*)abort_flag, 0, 24); break; }
       tc_fence_after();
-      tmem_ld32(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colq), v);
+      tmem_ld64(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(b * ACC_NT + colhalf), v);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&tempty[b])) : "memory");
 #pragma unroll
-      for (int i = 0; i < 32; ++i) inner[i] += v[i];
+      for (int i = 0; i < 64; ++i) inner[i] += v[i];
       if ((g % ACC_FOLD) == ACC_FOLD - 1) {
-        tmem_ld32(touter, v);
+        tmem_ld64(touter, v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) { v[i] += inner[i]; inner[i] = 0.f; }
-        tmem_st32(touter, v);
+        for (int i = 0; i < 64; ++i) { v[i] += inner[i]; inner[i] = 0.f; }
+        tmem_st64(touter, v);
       }
     }
   }
@@ -613,13 +610,16 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
       for (int kb = *consumed; kb < *issued; ++kb)
         (void)mbar_wait(&full[kb % STAGES], (kb / STAGES) & 1, WAIT_LIMIT, &zero_flag);
     }
-  } else if (warp < ACC_DW) {
-    const int lanebase = 32 * (warp & 3), colq = 32 * (warp >> 2);
-    float v[32], out[32];
-    tmem_ld32(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colq), v);
+  } else if (warp < 8) {
+    const int lanebase = 32 * (warp & 3), colhalf = 64 * (warp >> 2);
+    float v[64], out[32];
+    tmem_ld64(tmem + ((uint32_t)lanebase << 16) + (uint32_t)(ACC_OUTER + colhalf), v);
 #pragma unroll
     for (int i = 0; i < 32; ++i) out[i] = v[i] + inner[i];
-    epilogue_store(args, m0 + lanebase + lane, n0 + colq, out);
+    epilogue_store(args, m0 + lanebase + lane, n0 + colhalf, out);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) out[i] = v[32 + i] + inner[32 + i];
+    epilogue_store(args, m0 + lanebase + lane, n0 + colhalf + 32, out);
   }
   tc_fence_before();
   __syncthreads();

@@ -363,6 +363,69 @@ __device__ inline void hankel01_asymptotic_fixed(double x, const KtPair& kp, Han
   hk.J0 = hk.J1 = ht.J0 = ht.J1 = mkz(0.0);
 }
 
+// The same expansion for the point pairs of one far element pair whose phase
+// and damping were evaluated once at a reference argument x0 (the element
+// reference points): exp(i(x - pi/4)) = exp(i(x0 - pi/4)) exp(i dl) and
+// exp(-x t) = exp(-x0 t) exp(-dl t) with dl = x - x0, |dl| <= 1.05 (the caller
+// takes this route only when k h <= 1.2 and t <= 0.019); exp(i dl) by its
+// Taylor series to dl^19 (first omitted term below 2e-17), exp(-dl t) by its
+// series to (dl t)^8 (|dl t| <= 0.02, omitted term below 1e-21).  rs = x^-1/2
+// supplies both u = 1/x and the amplitude.
+__device__ inline void hankel01_asymptotic_rot(double x, double rs, double x0, zd ph0, double damp0,
+                                               const KtPair& kp, Hankel01& hk, Hankel01& ht) {
+  const double u = rs * rs, u2 = u * u;
+  zd S[2], St[2];
+  if (x >= kp.xth[0]) asym_sums<2>(u, u2, kp, S, St);
+  else if (x >= kp.xth[1]) asym_sums<3>(u, u2, kp, S, St);
+  else if (x >= kp.xth[2]) asym_sums<4>(u, u2, kp, S, St);
+  else if (x >= kp.xth[3]) asym_sums<5>(u, u2, kp, S, St);
+  else if (x >= kp.xth[4]) asym_sums<7>(u, u2, kp, S, St);
+  else asym_sums<ASYM_M>(u, u2, kp, S, St);
+  const double dl = x - x0, d2 = dl * dl;
+  double c = -1.5619206968586225e-16;
+  c = fma(c, d2, 4.779477332387385e-14);
+  c = fma(c, d2, -1.1470745597729725e-11);
+  c = fma(c, d2, 2.08767569878681e-09);
+  c = fma(c, d2, -2.755731922398589e-07);
+  c = fma(c, d2, 2.48015873015873e-05);
+  c = fma(c, d2, -0.001388888888888889);
+  c = fma(c, d2, 0.041666666666666664);
+  c = fma(c, d2, -0.5);
+  c = fma(c, d2, 1.0);
+  double sn = 2.8114572543455206e-15;
+  sn = fma(sn, d2, -7.647163731819816e-13);
+  sn = fma(sn, d2, 1.6059043836821613e-10);
+  sn = fma(sn, d2, -2.505210838544172e-08);
+  sn = fma(sn, d2, 2.7557319223985893e-06);
+  sn = fma(sn, d2, -0.0001984126984126984);
+  sn = fma(sn, d2, 0.008333333333333333);
+  sn = fma(sn, d2, -0.16666666666666666);
+  sn = fma(sn, d2, 1.0);
+  sn *= dl;
+  const zd ph = ph0 * mkz(c, sn);
+  const double amp = 0.79788456080286541 * rs;          // sqrt(2 / pi) x^-1/2
+  const zd f = mkz(amp * ph.x, amp * ph.y);
+  const double z = -dl * kp.t;   // |z| <= 0.02: sum z^j / j! to j = 8 (omitted term < 1e-21)
+  double e = 2.48015873015873e-05;
+  e = fma(e, z, 0.0001984126984126984);
+  e = fma(e, z, 0.001388888888888889);
+  e = fma(e, z, 0.008333333333333333);
+  e = fma(e, z, 0.041666666666666664);
+  e = fma(e, z, 0.16666666666666666);
+  e = fma(e, z, 0.5);
+  e = fma(e, z, 1.0);
+  e = fma(e, z, 1.0);
+  const double dmp = damp0 * e;
+  const zd ft = (f * kp.c2) * dmp;
+  hk.H0 = f * S[0];
+  zd h1 = f * S[1];
+  hk.H1 = mkz(h1.y, -h1.x);
+  ht.H0 = ft * St[0];
+  h1 = ft * St[1];
+  ht.H1 = mkz(h1.y, -h1.x);
+  hk.J0 = hk.J1 = ht.J0 = ht.J1 = mkz(0.0);
+}
+
 // H0, H1 (and J0, J1 below the expansion range) at k R = x and at k~ R
 __device__ inline void hankel01_pair(double x, const KtPair& kp, Hankel01& hk, Hankel01& ht) {
   if (x >= 20.0) { hankel01_asymptotic_fixed(x, kp, hk, ht); return; }

@@ -100,6 +100,7 @@ struct AsmArgs {
   double h, k;
   zd kt;
   int kt_pair = 0;                 // 1: both wavenumbers from one real evaluation (k~ = k (1 + i t))
+  int rot_ok = 0;                  // 1: far element pairs may share a reference phase (k h <= 1.2, t <= 0.019)
   KtPair ktp;
   int q_far, q_near, near_band;
   Points far, near;                // point tables (far: q_far per element, near: q_near)

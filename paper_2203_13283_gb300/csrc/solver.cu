@@ -965,6 +965,10 @@ static AsmArgs asm_args(wcs_ctx* c, bool circle) {
     // the mixed form stores entries to 24 bits: its expansion stops at 1e-13;
     // the FP64 form and the circle rows (the eigenvalues) keep 1e-16
     fill_asymptotic(A.ktp, (c->mixed && !circle) ? 1e-13 : 1e-16);
+    // the reference-phase route of the far pairs needs |k R - x0| <= 1.05
+    // (points within 0.45 h of their element's reference point) and
+    // |(k R - x0) t| <= 0.02 (see hankel01_asymptotic_rot)
+    A.rot_ok = (c->k * c->h <= 1.2 && t <= 0.019) ? 1 : 0;
   }
   return A;
 }
