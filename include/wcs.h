@@ -217,7 +217,12 @@ int wcs_skeleton(wcs_ctx* ctx, double tol, int max_rank, uint64_t seed, int* ran
 
 /* Factor C = C_c (I + C_c^{-1} U V^T) (Eq. 8): W = C_c^{-1} U by FFT, the
  * capacitance matrix K = I + V^T W and its inverse, for the Woodbury identity
- * of Eq. (9). */
+ * of Eq. (9).  K^-1: FP64 Gauss-Jordan in the FP64 form and for rank < 256;
+ * in the mixed form otherwise a Newton-Schulz iteration on the tensor cores
+ * closed by two steps with exact fixed-point products (its residual
+ * ||I - K K^-1||_F / sqrt(rank), ~1e-11, is reported in
+ * wcs_info.capacitance_residual).  Returns WCS_ERR_SINGULAR when K is
+ * singular or the iteration does not converge. */
 int wcs_factor(wcs_ctx* ctx);
 
 /* Checkpoint of a factored context.  The paper defines no file format; this
