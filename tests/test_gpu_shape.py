@@ -156,3 +156,43 @@ def test_operator_shape_derivative_forms_vs_oracle(oracle_operator_derivatives, 
     ref = np.array([np.sum(u.conj() * (d[op] @ v)) for d in dX])
     print(op, np.max(np.abs(T - ref)) / np.max(np.abs(ref)))
     assert np.max(np.abs(T - ref)) <= 1e-8 * np.max(np.abs(ref)), (T, ref)
+
+
+def test_operator_shape_derivative_forms_in_expansion_range():
+    # N = 256 (k = 29.9): element pairs farther than R = 20 / k ~ 0.67 take the
+    # Hankel expansion branch of the derivative kernel, which N = 64 never
+    # reaches; one cosine and one sine parameter at the asymmetric point,
+    # all four operators against the oracle's differenced dense operators
+    built()
+    from paper_2203_13283_gb300 import Solver
+    w = workloads.WORKLOADS["ellipse_n8192"]
+    fam, base = w["family"], w["params"]
+    n = 256
+    k = 2.0 * np.pi * (n / 10.0) / geometry.Contour(fam, base).L
+    Mp = 4
+    p = np.zeros(2 * Mp)
+    p[3] = 0.01                   # alpha_3
+    p[Mp + 1] = 0.01              # beta_2
+    params = [2, Mp + 2]          # alpha_2, beta_3
+    d = 1e-6
+    dX = []
+    for i in params:
+        e = np.zeros(2 * Mp)
+        e[i] = d
+        op_p, _, _, _ = shape.operators_at(fam, base, p + e, Mp, n, k, INC[:1], OBS[:1])
+        op_m, _, _, _ = shape.operators_at(fam, base, p - e, Mp, n, k, INC[:1], OBS[:1])
+        dX.append({key: (op_p[key] - op_m[key]) / (2 * d) for key in ("S", "D", "Dt", "N")})
+    g = np.random.default_rng(11)
+    u = g.standard_normal((n, 2)) + 1j * g.standard_normal((n, 2))
+    v = g.standard_normal((n, 2)) + 1j * g.standard_normal((n, 2))
+    s = Solver(precision=0)
+    s.contour(fam, **base).perturb(p[:Mp], p[Mp:]).mesh(n, k).assemble()
+    for op in ("S", "D", "Dt", "N"):
+        T = s.shape_operator_forms(op, u, v, Mp, params=(params[0], params[0] + 1))
+        T2 = s.shape_operator_forms(op, u, v, Mp, params=(params[1], params[1] + 1))
+        got = np.array([T[0], T2[0]])
+        ref = np.array([np.sum(u.conj() * (dd[op] @ v)) for dd in dX])
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        print(op, f"{err:.1e}")
+        assert err <= 1e-8, (op, got, ref)
+    s.close()
