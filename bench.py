@@ -329,6 +329,8 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="override the workload's N (k then follows 10 elements per wavelength); small "
                          "cases of the same contour for profiler captures")
+    ap.add_argument("--block", type=int, default=64,
+                    help="columns per block of the skeleton's range finder (1..64)")
     ap.add_argument("--rhs-chunk", type=int, default=None,
                     help="right-hand sides per solve block (default 1024 mixed, 64 FP64)")
     ap.add_argument("--profile-solve", action="store_true",
@@ -389,7 +391,7 @@ def main():
     rtol = args.refine_tol if args.refine_tol is not None else (5e-7 if mixed else 1e-11)
     extra = {} if args.zfast is None else {"zfast": args.zfast}
     S = Solver(device=f"cuda:{local}", precision=1 if mixed else 0, refine_tol=rtol, max_refine=12 if mixed else 30,
-               rhs_chunk=args.rhs_chunk or (1024 if mixed else 64), block=64, sample_planes=args.sample_planes,
+               rhs_chunk=args.rhs_chunk or (1024 if mixed else 64), block=args.block, sample_planes=args.sample_planes,
                **extra)
     stream = S.stream
     angles = w["angles"]

@@ -72,10 +72,10 @@ typedef struct wcs_options {
   double zfast;       /* mixed form: far pairs with k R >= zfast + 2 k h are integrated in FP32
                          around float-float element-centre phases (9 is the smallest safe value),
                          nearer ones in FP64; 0: every pair in FP64.  Default -1 = automatic:
-                         2000 in the mixed form.  Measured at N = 32768 (superellipse, k = 3642)
+                         1000 in the mixed form.  Measured at N = 32768 (superellipse, k = 3642)
                          against the FP64 form, for incidence grazing the flat faces: 9.8e-7 with
-                         zfast = 9 (assembly 0.9 s), 3.8e-7 with 2000 (3.1 s), 2.4e-7 with 0
-                         (10.9 s).  The FP32 part loses accuracy where the two terms of the
+                         zfast = 9, 7.8e-7 with 500, 6.1e-7 with 1000 (assembly 1.7 s), 3.8e-7
+                         with 2000 (2.3 s), 2.4e-7 with 0.  The FP32 part loses accuracy where the two terms of the
                          Maue form of N cancel (pairs on one flat face), and there its roundings
                          repeat along each diagonal of the operator. */
   int sample_planes;  /* mixed form: bf16 planes of each operand in the skeleton's sampling

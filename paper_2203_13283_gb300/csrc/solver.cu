@@ -749,7 +749,7 @@ int wcs_default_options(wcs_options* o) {
   o->rhs_chunk = 256;
   o->mixed_planes = 3;
   o->rhs_planes = 3;
-  o->zfast = -1.0;  // automatic: 2000 in the mixed form (FP32 far pairs beyond k R = 2000), unused in FP64
+  o->zfast = -1.0;  // automatic: 1000 in the mixed form (FP32 far pairs beyond k R = 1000), unused in FP64
   return WCS_OK;
 }
 
@@ -765,11 +765,12 @@ int wcs_create(wcs_ctx** out, const wcs_options* opt, void* stream) {
   if (o.q_far == 0) o.q_far = (o.precision == WCS_PREC_MIXED) ? 4 : 6;
   if (o.q_near == 0) o.q_near = (o.precision == WCS_PREC_MIXED) ? 8 : 12;
   if (o.sample_planes == 0) o.sample_planes = 2;
-  // FP32 far pairs beyond k R = 2000: at N = 32768 (k = 3642, superellipse)
-  // this keeps the error against the FP64 form at 3.8e-7 for grazing
-  // incidence (all far pairs in FP32: 9.8e-7) with 3.1 s of assembly (all in
-  // FP64: 10.9 s); smaller problems have no pairs that far and stay in FP64
-  if (o.zfast < 0.0) o.zfast = (o.precision == WCS_PREC_MIXED) ? 2000.0 : 0.0;
+  // FP32 far pairs beyond k R = 1000: at N = 32768 (k = 3642, superellipse)
+  // this keeps the error against the FP64 form at 6.1e-7 for grazing
+  // incidence (2000: 3.8e-7; all far pairs in FP32: 9.8e-7) with 1.7 s of
+  // assembly (2000: 2.3 s); smaller problems have few pairs that far and stay
+  // mostly in FP64
+  if (o.zfast < 0.0) o.zfast = (o.precision == WCS_PREC_MIXED) ? 1000.0 : 0.0;
   if (o.sample_planes < 1 || o.sample_planes > 2) { set_error("sample_planes must be 1 or 2"); return WCS_ERR_ARG; }
   if (o.exact_residual != 0 && o.exact_residual != 1) { set_error("exact_residual must be 0 or 1"); return WCS_ERR_ARG; }
   if (o.q_far < 2 || o.q_far > 16 || o.q_near < 4 || o.q_near > 16 || o.near_band < 1 ||

@@ -69,3 +69,31 @@ def test_batch_rejects_bad_arguments():
         batch_solve_fourier([{"cos": [-1.0], "N": 64}], [0.0])               # negative mean radius
     with pytest.raises(WCSError):
         batch_solve_fourier([{"cos": [1.0], "N": 64}], [0.0], workers=9)
+
+
+def test_batch_mid_size_matches_single_contexts():
+    # star contours at N = 2048, 1500 (Bluestein) and 1024 in the mixed form:
+    # the FP32 circulant transform (powers of two), the shared reference
+    # phase of the FP64 far pairs and the FP32 far-pair kernel all run in
+    # three concurrent contexts; each contour must equal its single-context
+    # solve and meet the residual target
+    built()
+    from paper_2203_13283_gb300.solver import batch_solve_fourier
+    base = workloads.star_contours(count=3, seed=7)
+    sizes = [2048, 1500, 1024]
+    ang = workloads.uniform_angles(8)
+    contours = [{"cos": w["params"]["cos"], "sin": w["params"]["sin"], "N": n} for w, n in zip(base, sizes)]
+    opts = dict(precision=1, refine_tol=5e-7, max_refine=12)
+    js, st = batch_solve_fourier(contours, ang, tol=1e-6, rank_div=8, seed=3, workers=3, **opts)
+    assert sorted({s["worker"] for s in st}) == [0, 1, 2]
+    for w, n, j, s in zip(base, sizes, js, st):
+        assert s["status"] == 0 and s["rel_residual"] <= 5e-7, s
+        one = make_solver(dict(w, N=n), **opts)
+        one.assemble()
+        one.skeleton(1e-6, max_rank=n // 8, seed=3, allow_cap=True)
+        one.factor()
+        j1 = to_np(one.solve_planewaves(ang))
+        one.close()
+        err = np.max(np.abs(j - j1)) / np.max(np.abs(j1))
+        print(n, s, f"{err:.1e}")
+        assert err <= 1e-13, (n, err)
