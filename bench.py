@@ -205,7 +205,7 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
     if cat in ("gemm_tc", "gemm_tc_acc", "gemm_tc_per"):
         achieved = v["work"] / sec / 1e12
         name, nprod, mode = {"gemm_tc": ("k_gemm_tc", 3, "one accumulator, 2 planes"),
-                             "gemm_tc_acc": ("k_gemm_tc_acc", 6, "drained every K = 16 step, 3 planes"),
+                             "gemm_tc_acc": ("k_gemm_tc_acc", 6, "drained once per K = 64 stage, products smallest first, 3 planes"),
                              "gemm_tc_per": ("k_gemm_tc_per", 3, "drained every 64 steps, 2 planes")}[cat]
         prof_file = {"gemm_tc": "k_gemm_tc_ellipse_n4096_mixed.md", "gemm_tc_acc": "k_gemm_tc_acc_ellipse_n4096_mixed.md",
                      "gemm_tc_per": "k_gemm_tc_per_superellipse_n4096_mixed.md"}[cat]

@@ -375,8 +375,11 @@ int wcs_gemm_split_bf16(int64_t M, int64_t Nc, int64_t K, const double* A_dev, i
  * MMA truncates, so its error grows with the number of K = 16 steps it spans.
  * accurate = 1 drains the tensor-memory accumulator into FP32 register sums
  * after every step (~1e-7 relative with 3 planes); accurate = n > 1 drains
- * every n steps (n = 64: ~1e-5 at close to the speed of accurate = 0);
- * planes must then be 2 or 3. */
+ * every n steps (n = 64: ~1e-5 at close to the speed of accurate = 0).
+ * accurate = 4 drains once per shared-memory stage of K = 64 and issues the
+ * stage's products smallest first across its four steps, which keeps the
+ * error of accurate = 1 at ~80% of its time (the solver's refinement
+ * residual uses it).  planes must be 2 or 3 when accurate != 0. */
 int wcs_gemm_split_bf16_ex(int64_t M, int64_t Nc, int64_t K, const double* A_dev, int64_t lda,
                            const double* B_dev, int64_t ldb, int planes, int accurate, double* D_dev,
                            int64_t ldd, void* stream);

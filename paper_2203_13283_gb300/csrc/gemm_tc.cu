@@ -530,6 +530,32 @@ __global__ void __launch_bounds__(ACC_THREADS, 1)
           da[p] = sw128_desc(sp + IA[p] * L::A_BYTES);
           db[p] = sw128_desc(sp + PA * L::A_BYTES + IB[p] * L::B_BYTES);
         }
+        if (drain == TC_BK / 16) {
+          // one group per stage, issued product-major: every step's small
+          // plane products enter the fresh accumulator before any large one,
+          // so the truncating accumulator cuts them at their own scale, not
+          // at the scale of the leading product
+          if (q >= ACC_NBUF) {
+            if (!mbar_wait(&tempty[b], ((q / ACC_NBUF) - 1) & 1, WAIT_LIMIT, args.err)) {
+              *abort_flag = 25;
+              mma_commit(&empty[st]);
+              break;
+            }
+            tc_fence_after();
+          }
+          const uint32_t dt = tmem + (uint32_t)(b * ACC_NT);
+#pragma unroll
+          for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk)
+              mma_bf16(dt, da[p] + (uint64_t)(2 * kk), db[p] + (uint64_t)(2 * kk), idesc,
+                       (p == 0 && kk == 0) ? 0u : 1u);
+          mma_commit(&tfull[b]);
+          ++q;
+          b = (b == ACC_NBUF - 1) ? 0 : b + 1;
+          mma_commit(&empty[st]);
+          continue;
+        }
 #pragma unroll
         for (int kk = 0; kk < TC_BK / 16; ++kk) {
           if (ingroup == 0 && q >= ACC_NBUF) {

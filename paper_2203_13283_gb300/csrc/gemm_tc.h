@@ -41,8 +41,9 @@ struct TcArgs {
   int force_kper = 0;
   int no_reduce = 0;
   // gemm_tc_accurate: K = 16 steps accumulated in tensor memory before each
-  // drain into FP32 registers (1: every step, error ~1e-7; 64: error ~1e-5 at
-  // close to the speed of gemm_tc)
+  // drain into FP32 registers (1: every step, error ~1e-7; 4: once per K = 64
+  // stage, products issued smallest first across it, error ~1e-7; 64: error
+  // ~1e-5 at close to the speed of gemm_tc)
   int drain = 1;
 };
 

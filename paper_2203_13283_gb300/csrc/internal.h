@@ -238,9 +238,10 @@ int gram_matrix(const zd* X, int64_t ld, int64_t m, int b, zd* G, zd* work, cuda
 // numerical rank r (pivots >= tol^2 * max) and writes R (upper, r x b in permuted order)
 // and the pivot permutation.  Runs in one thread block.
 int pivoted_cholesky(zd* Gm, int b, double rel_tol, int* perm, int* rank_dev, cudaStream_t s);
-// Y(:, 0:r) = X(:, perm[0:r]) R[0:r, 0:r]^{-1}
+// Y(:, 0:r) = X(:, perm[0:r]) R[0:r, 0:r]^{-1} (b <= 64; work: r x r scratch for
+// R^{-1}; Y must not alias X)
 int trsm_right_upper(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
-                     const int* rank_dev, int rank_host, zd* Y, int64_t ldy, cudaStream_t s);
+                     const int* rank_dev, int rank_host, zd* Y, int64_t ldy, zd* work, cudaStream_t s);
 // LU with partial pivoting of an n x n column-major matrix (in place) and explicit inverse.
 int lu_inverse(zd* A, int64_t n, zd* Ainv, int* piv, int* info_dev, double* minpiv_dev,
                cudaStream_t s);

@@ -2,6 +2,7 @@
 // (Eq. 6), randomized range finding for the skeleton (Eq. 7) and the
 // capacitance matrix of the Woodbury identity (Eq. 9).
 #include <algorithm>
+#include <climits>
 #include <vector>
 
 #include "internal.h"
@@ -393,100 +394,177 @@ int gram_matrix(const zd* X, int64_t ld, int64_t m, int b, zd* G, zd* work, cuda
 }
 
 // =========================================================================== pivoted Cholesky
-// In-place on a Hermitian b x b matrix (column-major, ld = b), one CTA.
-// After return: rank r, perm[0:b], and R (upper, row j holds R[j, j..b-1]
-// in permuted order) stored in Gm's upper triangle.
+// On a Hermitian b x b matrix (column-major, ld = b, b <= 64), one CTA, the
+// matrix held in shared memory.  After return: rank r, perm[0:b], and R
+// (upper, row j holds R[j, j..b-1] in permuted order) in Gm's upper triangle.
+// Pivot: the largest remaining diagonal entry, the first of equal ones; the
+// factorisation stops when it is <= rel_tol^2 times the first pivot (or <= 0).
 __global__ void k_pchol(zd* Gm, int b, double rel_tol, int* perm, int* rank_out) {
-  __shared__ double dmax_s;
-  __shared__ int piv_s;
-  __shared__ int stop_s;
+  extern __shared__ zd G[];
+  __shared__ double best_s, dmax_s;
+  __shared__ int piv_s, perm_s[64];
   const int tid = threadIdx.x;
-  for (int i = tid; i < b; i += blockDim.x) perm[i] = i;
-  if (tid == 0) { dmax_s = 0.0; stop_s = 0; }
+  for (int u = tid; u < b * b; u += blockDim.x) G[u] = Gm[u];
+  for (int i = tid; i < b; i += blockDim.x) perm_s[i] = i;
   __syncthreads();
   int rank = b;
   for (int j = 0; j < b; ++j) {
-    if (tid == 0) {
-      int p = j;
-      double best = -1.0;
-      for (int i = j; i < b; ++i) {
-        double d = Gm[i * b + i].x;
-        if (d > best) { best = d; p = i; }
+    if (tid < 32) {
+      // warp argmax over the remaining diagonal; ties go to the lower index
+      double v = -1.0;
+      int p = INT_MAX;
+      for (int i = j + tid; i < b; i += 32) {
+        const double d = G[i * b + i].x;
+        if (d > v) { v = d; p = i; }
       }
-      if (j == 0) dmax_s = best;
-      piv_s = p;
-      stop_s = (best <= rel_tol * rel_tol * dmax_s || best <= 0.0) ? 1 : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_down_sync(0xffffffffu, v, o);
+        const int p2 = __shfl_down_sync(0xffffffffu, p, o);
+        if (v2 > v || (v2 == v && p2 < p)) { v = v2; p = p2; }
+      }
+      if (tid == 0) {
+        if (p == INT_MAX) { p = j; v = -1.0; }
+        if (j == 0) dmax_s = v;
+        piv_s = p;
+        best_s = v;
+      }
     }
     __syncthreads();
-    if (stop_s) { rank = j; break; }
+    const double best = best_s;
+    if (best <= rel_tol * rel_tol * dmax_s || best <= 0.0) { rank = j; break; }
     const int p = piv_s;
     if (p != j) {
       // symmetric swap of rows/columns j and p
       for (int i = tid; i < b; i += blockDim.x) {
-        zd t = Gm[j * b + i]; Gm[j * b + i] = Gm[p * b + i]; Gm[p * b + i] = t;  // columns
+        zd t = G[j * b + i]; G[j * b + i] = G[p * b + i]; G[p * b + i] = t;  // columns
       }
       __syncthreads();
       for (int i = tid; i < b; i += blockDim.x) {
-        zd t = Gm[i * b + j]; Gm[i * b + j] = Gm[i * b + p]; Gm[i * b + p] = t;  // rows
+        zd t = G[i * b + j]; G[i * b + j] = G[i * b + p]; G[i * b + p] = t;  // rows
       }
-      if (tid == 0) { int t = perm[j]; perm[j] = perm[p]; perm[p] = t; }
+      if (tid == 0) { int t = perm_s[j]; perm_s[j] = perm_s[p]; perm_s[p] = t; }
       __syncthreads();
     }
-    const double rjj = sqrt(Gm[j * b + j].x);
+    const double rjj = sqrt(G[j * b + j].x);
     __syncthreads();
     // row j of R: R[j, i] = G[j, i] / rjj  (G[j, i] at column i, row j)
     for (int i = tid; i < b; i += blockDim.x) {
-      if (i > j) Gm[i * b + j] = (1.0 / rjj) * Gm[i * b + j];
-      if (i == j) Gm[j * b + j] = mkz(rjj);
+      if (i > j) G[i * b + j] = (1.0 / rjj) * G[i * b + j];
+      if (i == j) G[j * b + j] = mkz(rjj);
     }
     __syncthreads();
     // Schur complement: G[l, i] -= conj(R[j, l]) R[j, i], l, i > j
     const int rem = b - j - 1;
     for (int u = tid; u < rem * rem; u += blockDim.x) {
       const int l = j + 1 + u % rem, i = j + 1 + u / rem;
-      Gm[i * b + l] -= conj(Gm[l * b + j]) * Gm[i * b + j];
+      G[i * b + l] -= conj(G[l * b + j]) * G[i * b + j];
     }
     __syncthreads();
   }
+  __syncthreads();
+  for (int u = tid; u < b * b; u += blockDim.x) Gm[u] = G[u];
+  for (int i = tid; i < b; i += blockDim.x) perm[i] = perm_s[i];
   if (tid == 0) *rank_out = rank;
 }
 
 int pivoted_cholesky(zd* Gm, int b, double rel_tol, int* perm, int* rank_dev, cudaStream_t s) {
-  k_pchol<<<1, 512, 0, s>>>(Gm, b, rel_tol, perm, rank_dev);
+  if (b < 1 || b > 64) { set_error("pivoted_cholesky: 1 <= b <= 64"); return 1; }
+  const int smem = (int)sizeof(zd) * b * b;
+  static DeviceOnce attr;
+  if (attr.need()) {
+    cudaError_t e = cudaFuncSetAttribute(k_pchol, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(zd) * 64 * 64);
+    if (e != cudaSuccess) { set_error(std::string("pivoted_cholesky: ") + cudaGetErrorString(e)); return 3; }
+    attr.done();
+  }
+  k_pchol<<<1, 512, smem, s>>>(Gm, b, rel_tol, perm, rank_dev);
   note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(cudaGetErrorString(err)); return 3; }
   return 0;
 }
 
-// Y(i, 0:r) = X(i, perm[0:r]) R^{-1}: solve y R = x row by row (R upper, r x r)
-__global__ void k_trsm_rows(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
-                            const int* rank_dev, zd* Y, int64_t ldy) {
-  extern __shared__ zd Rs[];
+// Y(i, 0:r) = X(i, perm[0:r]) R^{-1}, R the r x r upper factor of k_pchol
+// (R[i][l] at R[l * b + i]).  Two kernels: Z = R^{-1} column by column (CTA c
+// solves R z = e_c by back substitution, the update of each finished entry
+// spread over the threads), then Y = X_perm Z over row tiles, where each row
+// is independent: no dependency chain through memory, so the FP64 pipe is
+// the bound.
+__global__ void k_tri_inv(const zd* R, int b, const int* rank_dev, zd* Z) {
+  __shared__ zd zl_s;
+  const int r = *rank_dev, c = blockIdx.x, i = threadIdx.x;
+  if (c >= r) return;
+  zd s = mkz(i == c ? 1.0 : 0.0);
+  for (int l = c; l >= 0; --l) {
+    if (i == l) {
+      zl_s = s * zrecip(R[l * b + l]);
+      Z[c * r + l] = zl_s;
+    }
+    __syncthreads();
+    const zd z = zl_s;
+    if (i < l) s -= R[l * b + i] * z;
+    __syncthreads();
+  }
+  for (int u = c + 1 + i; u < r; u += blockDim.x) Z[c * r + u] = mkz(0.0);
+}
+
+constexpr int TRSM_ROWS = 32, TRSM_COLS = 16;   // rows per CTA; columns per warp
+
+// 4 warps: warp g forms columns 16 g .. 16 g + 15 of 32 rows; X tile and Z in
+// shared memory (Z read as broadcasts, X row-consecutive across the lanes).
+__global__ void __launch_bounds__(128) k_trsm_apply(const zd* X, int64_t ldx, int64_t m, const zd* Z,
+                                                    const int* perm, const int* rank_dev, zd* Y,
+                                                    int64_t ldy) {
+  extern __shared__ zd sm[];
   const int r = *rank_dev;
-  for (int u = threadIdx.x; u < r * r; u += blockDim.x) {
-    const int row = u % r, col = u / r;
-    // diagonal stored as its reciprocal: one division per entry of R, not per row
-    Rs[col * r + row] = (row < col) ? R[col * b + row] : ((row == col) ? zrecip(R[col * b + row]) : mkz(0.0));
+  zd* Zs = sm;                 // r x r, column-major
+  zd* xs = sm + r * r;         // r x TRSM_ROWS
+  const int tid = threadIdx.x, lane = tid & 31, g = tid >> 5;
+  const int64_t row0 = (int64_t)blockIdx.x * TRSM_ROWS;
+  for (int u = tid; u < r * r; u += blockDim.x) Zs[u] = Z[u];
+  for (int u = tid; u < r * TRSM_ROWS; u += blockDim.x) {
+    const int l = u / TRSM_ROWS, rr = u % TRSM_ROWS;
+    xs[u] = (row0 + rr < m) ? X[(int64_t)perm[l] * ldx + row0 + rr] : mkz(0.0);
   }
-  __shared__ int ps[128];
-  for (int u = threadIdx.x; u < r; u += blockDim.x) ps[u] = perm[u];
   __syncthreads();
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= m) return;
-  for (int j = 0; j < r; ++j) {
-    zd v = X[(int64_t)ps[j] * ldx + i];
-    for (int l = 0; l < j; ++l) v -= Y[(int64_t)l * ldy + i] * Rs[j * r + l];
-    Y[(int64_t)j * ldy + i] = v * Rs[j * r + j];
+  const int c0 = g * TRSM_COLS;
+  if (c0 >= r) return;
+  zd acc[TRSM_COLS];
+#pragma unroll
+  for (int k = 0; k < TRSM_COLS; ++k) acc[k] = mkz(0.0);
+  const int lmax = min(r, c0 + TRSM_COLS);
+  for (int l = 0; l < lmax; ++l) {
+    const zd x = xs[l * TRSM_ROWS + lane];
+#pragma unroll
+    for (int k = 0; k < TRSM_COLS; ++k) {
+      const int c = c0 + k;
+      if (c < r && l <= c) zfma(acc[k], x, Zs[c * r + l]);
+    }
   }
+  const int64_t i = row0 + lane;
+  if (i >= m) return;
+#pragma unroll
+  for (int k = 0; k < TRSM_COLS; ++k)
+    if (c0 + k < r) Y[(int64_t)(c0 + k) * ldy + i] = acc[k];
 }
 
 int trsm_right_upper(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
-                     const int* rank_dev, int rank_host, zd* Y, int64_t ldy, cudaStream_t s) {
-  if (b > 128) { set_error("trsm: block too wide"); return 1; }
-  const size_t smem = sizeof(zd) * rank_host * rank_host;
-  cudaFuncSetAttribute(k_trsm_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(smem, 1));
-  k_trsm_rows<<<(unsigned)((m + 127) / 128), 128, smem, s>>>(X, ldx, m, R, b, perm, rank_dev, Y, ldy);
+                     const int* rank_dev, int rank_host, zd* Y, int64_t ldy, zd* work, cudaStream_t s) {
+  if (b > 64 || rank_host > b) { set_error("trsm: block too wide"); return 1; }
+  if (rank_host <= 0) return 0;
+  k_tri_inv<<<(unsigned)rank_host, 64, 0, s>>>(R, b, rank_dev, work);
+  note_launch();
+  const size_t smem = sizeof(zd) * ((size_t)rank_host * rank_host + (size_t)rank_host * TRSM_ROWS);
+  static DeviceOnce attr;
+  if (attr.need()) {
+    cudaError_t e = cudaFuncSetAttribute(k_trsm_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(zd) * (64 * 64 + 64 * TRSM_ROWS)));
+    if (e != cudaSuccess) { set_error(std::string("trsm: ") + cudaGetErrorString(e)); return 3; }
+    attr.done();
+  }
+  k_trsm_apply<<<(unsigned)((m + TRSM_ROWS - 1) / TRSM_ROWS), 128, smem, s>>>(X, ldx, m, work, perm, rank_dev,
+                                                                                Y, ldy);
   note_launch();
   cudaError_t err = cudaGetLastError();
   if (err != cudaSuccess) { set_error(std::string("trsm: ") + cudaGetErrorString(err)); return 3; }

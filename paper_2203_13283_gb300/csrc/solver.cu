@@ -204,8 +204,8 @@ static int check_tc(wcs_ctx* c);
 // Precision of a tensor-core operator product (mixed form):
 //   PREC_FAST      two leading planes, one accumulator over all of K (~1e-4 at
 //                  K ~ 1e5): skeleton sampling, Woodbury products
-//   PREC_ACCURATE  all stored planes, accumulator drained every K = 16 step
-//                  (~1e-7): refinement residual, preconditioned right-hand side
+//   PREC_ACCURATE  all stored planes, accumulator drained every ACC_DRAIN
+//                  K = 16 steps (~1e-7): refinement residual
 //   PREC_PERIODIC  two leading planes, accumulator drained every 64 steps
 //                  (~1e-5): residual updates R <- R - C dx, whose error scales
 //                  with |dx|
@@ -215,6 +215,14 @@ static int check_tc(wcs_ctx* c);
 //                  products, FP64 sums (exact.cu): residuals of refinement
 //                  below the accurate floor (forward products only)
 enum { PREC_FAST = 0, PREC_ACCURATE = 1, PREC_PERIODIC = 2, PREC_FAST1 = 3, PREC_EXACT = 4 };
+
+// K = 16 steps per drain of the accurate product: one shared-memory stage
+// (K = 64), whose products the kernel issues smallest first across the four
+// steps.  Measured at N = 32768 (K = 65536, 1024 plane waves) against a solve
+// with exact residuals: drain 1 took 45.1 ms per product and left 3.0e-7
+// (max over 64 columns), drain 4 issued step by step 36.7 ms and 3.5e-7; the
+// error floor is set by the three-plane split, not by the drain.
+constexpr int ACC_DRAIN = 4;
 
 // Algorithmic HBM bytes of one contraction: every plane of A and B read once,
 // the complex FP64 output written (and read when beta != 0).
@@ -248,7 +256,7 @@ static int tc_apply(wcs_ctx* c, int op, bool adjoint, DevBuf& buf, int64_t cols,
   t.alpha = alpha;
   t.beta = beta;
   t.err = (int*)c->tcerr.p;
-  t.drain = (mode == PREC_PERIODIC) ? 64 : 1;
+  t.drain = (mode == PREC_PERIODIC) ? 64 : (accurate ? ACC_DRAIN : 1);
   const bool drained = (mode == PREC_ACCURATE || mode == PREC_PERIODIC);
   ProfScope ps(c, mode == PREC_PERIODIC ? CAT_GEMM_PER : (drained ? CAT_GEMM_ACC : CAT_GEMM_TC),
                2.0 * t.M * (double)t.Nc * t.K,
@@ -279,10 +287,12 @@ static int check_tc(wcs_ctx* c) {
 // C (m x n, column-major ldc) = alpha * A (m x k view) * X (k x n, column-major) + beta * C.
 // Mixed form: on the tensor cores through staged split-bf16 planes; FP64 form: zgemm.
 static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A, const zd* X, int64_t ldx,
-                 zd beta, zd* C, int64_t ldc) {
+                 zd beta, zd* C, int64_t ldc, bool accurate = false) {
   if (m <= 0 || n <= 0) return 0;
   if (!c->mixed || k < 64) return zgemm(m, n, k, alpha, A, blk(X, ldx), beta, C, ldc, c->s);
-  const int P = 2;
+  // fast: two planes, one accumulator; accurate: three planes, the drained
+  // accumulation of the refinement residual
+  const int P = accurate ? 3 : 2;
   const int64_t ldk = ((2 * k + 63) / 64) * 64;
   // grow the staging buffers geometrically: the skeleton calls this with a
   // basis that widens block by block
@@ -314,8 +324,13 @@ static int cgemm(wcs_ctx* c, int64_t m, int64_t n, int64_t k, zd alpha, ZView A,
   TRY(c->gW.ensure((size_t)32 << 20));
   t.ws = (float*)c->gW.p;
   t.ws_elems = (int64_t)(c->gW.bytes / sizeof(float));
-  ProfScope ps(c, CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, tc_bytes(t, P, P));
-  TRY(gemm_tc(oa, ob, t, c->s));
+  ProfScope ps(c, accurate ? CAT_GEMM_ACC : CAT_GEMM_TC, 2.0 * t.M * (double)t.Nc * t.K, tc_bytes(t, P, P));
+  if (accurate) {
+    t.drain = ACC_DRAIN;
+    TRY(gemm_tc_accurate(oa, ob, t, c->s));
+  } else {
+    TRY(gemm_tc(oa, ob, t, c->s));
+  }
   return 0;
 }
 
@@ -1258,7 +1273,7 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   DevBuf Zb, Gb, Ib, Nb, GW;
   TRY(GW.ensure(sizeof(zd) * ((N + 255) / 256) * b * b));
   TRY(Zb.ensure(sizeof(zd) * (cap + b) * b));
-  TRY(Gb.ensure(sizeof(zd) * b * b));
+  TRY(Gb.ensure(sizeof(zd) * 2 * b * b));   // Gram / Cholesky factor, then R^{-1}
   TRY(Ib.ensure(sizeof(int) * (b + 1)));
   TRY(Nb.ensure(sizeof(double) * b));
   int64_t ell = 0;
@@ -1330,7 +1345,8 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
       if (rk_new == 0) { rk = 0; break; }
       zd* dst = (pass == 0) ? c->w3.z() : Q + ell * N;
       TRY(dbg_check(c, Gb.z(), cols, cols, cols, "cholesky"));
-      TRY(trsm_right_upper(src, N, N, Gb.z(), cols, (int*)Ib.p, (int*)Ib.p + b, rk_new, dst, N, c->s));
+      TRY(trsm_right_upper(src, N, N, Gb.z(), cols, (int*)Ib.p, (int*)Ib.p + b, rk_new, dst, N, Gb.z() + b * b,
+                           c->s));
       TRY(dbg_check(c, dst, N, rk_new, N, "trsm"));
       rk = rk_new;
       if (pass == 0) {
@@ -1493,26 +1509,37 @@ int wcs_factor(wcs_ctx* c) {
         std::swap(X, Xn);
       }
       if (!(res < 0.1 * std::sqrt((double)r))) { set_error("capacitance iteration did not converge"); return WCS_ERR_SINGULAR; }
-      // The split-bf16 iteration stalls near 1e-4 per direction.  Two closing
-      // steps with exact products (each squares the residual) carry K^-1 to
-      // the products' own precision (42 bits below each chunk's scale,
-      // ~1e-11 per direction), and a third exact product measures ||I - K X||_F.
-      {
-        for (int it = 0; it < 2; ++it) {
-          TRY(exact_square(c, Kb.z(), r, X, r, T.z()));          // T = K X
-          k_two_minus<<<(unsigned)((r * r + 255) / 256), 256, 0, c->s>>>(T.z(), r);
-          note_launch();
-          TRY(exact_square(c, X, r, T.z(), r, Xn));             // X <- X (2I - K X)
-          std::swap(X, Xn);
-        }
-        TRY(exact_square(c, Kb.z(), r, X, r, T.z()));
+      // The two-plane iteration stalls near 1e-4 per direction.  One step with
+      // the drained three-plane product (~1e-7) and then exact steps (each
+      // squares the residual; the exact products carry 42 bits below each
+      // chunk's scale, ~1e-11 per direction) close it: an exact product
+      // measures ||I - K X||_F after every exact step, and a step is added
+      // while that is above 1e-10 per direction (at most three).
+      auto eye_residual = [&](double& out) -> int {
         k_eye_partial<<<EYE_BLOCKS, 256, 0, c->s>>>(T.z(), r, cs + 3 * r);
         note_launch();
         k_eye_finish<<<1, 256, 0, c->s>>>(cs + 3 * r, EYE_BLOCKS, cs + 2 * r);
         note_launch();
-        cudaMemcpyAsync(&res, cs + 2 * r, sizeof(double), cudaMemcpyDeviceToHost, c->s);
-        TRY(sync(c));
-        c->kinv_res = res / std::sqrt((double)r);
+        cudaMemcpyAsync(&out, cs + 2 * r, sizeof(double), cudaMemcpyDeviceToHost, c->s);
+        return sync(c);
+      };
+      {
+        TRY(cgemm(c, r, r, r, mkz(1.0), blk(Kb.z(), r), X, r, mkz(0.0), T.z(), r, true));   // T = K X
+        k_two_minus<<<(unsigned)((r * r + 255) / 256), 256, 0, c->s>>>(T.z(), r);
+        note_launch();
+        TRY(cgemm(c, r, r, r, mkz(1.0), blk(X, r), T.z(), r, mkz(0.0), Xn, r, true));    // X <- X (2I - K X)
+        std::swap(X, Xn);
+        TRY(exact_square(c, Kb.z(), r, X, r, T.z()));
+        for (int it = 0; it < 3; ++it) {
+          k_two_minus<<<(unsigned)((r * r + 255) / 256), 256, 0, c->s>>>(T.z(), r);
+          note_launch();
+          TRY(exact_square(c, X, r, T.z(), r, Xn));             // X <- X (2I - K X)
+          std::swap(X, Xn);
+          TRY(exact_square(c, Kb.z(), r, X, r, T.z()));          // T = K X
+          TRY(eye_residual(res));
+          c->kinv_res = res / std::sqrt((double)r);
+          if (!(c->kinv_res >= 1e-10)) break;
+        }
         if (!(c->kinv_res < 1e-6)) { set_error("capacitance iteration did not reach FP64 accuracy"); return WCS_ERR_SINGULAR; }
       }
       if (X != Kinv.z())

@@ -285,7 +285,8 @@ def gemm_split_bf16(A, B, planes=2, accurate=False):
     """D = A @ B.T on the tensor cores with split-bf16 operands (FP64 in/out, cuda).
 
     accurate: False/0 one accumulator over all of K; True/1 accumulator
-    drained every K = 16 step; an int n > 1 drains every n steps."""
+    drained every K = 16 step; an int n > 1 drains every n steps (4: once per
+    K = 64 stage, products issued smallest first across it)."""
     A = torch.as_tensor(A, dtype=torch.float64, device="cuda").contiguous()
     B = torch.as_tensor(B, dtype=torch.float64, device="cuda").contiguous()
     M, K = A.shape

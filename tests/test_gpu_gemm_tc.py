@@ -79,3 +79,27 @@ def test_split_bf16_gemm_periodic_drain(M, Nc, K, planes):
     err = ((D - ref).norm() / ref.norm()).item()
     bound = {2: 4e-5, 3: 2e-5}[planes]
     assert err < bound, err
+
+
+@pytest.mark.parametrize("M,Nc,K", [(128, 64, 64), (300, 200, 1000), (256, 128, 65536), (130, 70, 300)])
+@pytest.mark.parametrize("planes", [2, 3])
+def test_split_bf16_gemm_stage_drain(M, Nc, K, planes):
+    """Accumulator drained once per shared-memory stage (four K = 16 steps),
+    the products issued smallest first across the stage: within the bound of
+    the every-step drain, and no more than twice its error (issued step by
+    step, the small products of later steps are cut at the scale of the
+    leading product)."""
+    built()
+    from paper_2203_13283_gb300.solver import gemm_split_bf16
+    g = torch.Generator(device="cpu").manual_seed(M + 7 * Nc + K)
+    A = torch.randn(M, K, generator=g, dtype=torch.float64).cuda()
+    B = torch.randn(Nc, K, generator=g, dtype=torch.float64).cuda()
+    ref = A @ B.T
+    D1 = gemm_split_bf16(A, B, planes, accurate=True)
+    D4 = gemm_split_bf16(A, B, planes, accurate=4)
+    e1 = ((D1 - ref).norm() / ref.norm()).item()
+    e4 = ((D4 - ref).norm() / ref.norm()).item()
+    print(f"planes {planes} K {K}: drain 1 {e1:.2e}, drain 4 {e4:.2e}")
+    bound = {2: 3e-5, 3: 5e-7}[planes]
+    assert e4 < bound, e4
+    assert e4 <= 2.0 * e1 + 1e-9, (e1, e4)
