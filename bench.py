@@ -385,7 +385,7 @@ def main():
     mixed = args.form == "mixed"
     tol = args.tol if args.tol is not None else (1e-6 if mixed else 1e-2)
     max_rank = args.max_rank if args.max_rank is not None else (w["N"] // 8 if mixed else 512)
-    # mixed form: the drained residual's floor is ~3e-7, so the metric run
+    # mixed form: the drained residual's floor is ~2e-7, so the metric run
     # refines to 5e-7 (it converges; the error against the FP64 form is
     # reported below); the exact-residual leg refines to 1e-10
     rtol = args.refine_tol if args.refine_tol is not None else (5e-7 if mixed else 1e-11)

@@ -87,7 +87,7 @@ typedef struct wcs_options {
                          costs 6 bf16 slices of each operator (96 N^2 bytes in all, built at the
                          first such solve).  Adjoint solves keep the drained residual.  0
                          (default): residuals in split-bf16 with FP32 accumulation, which floor
-                         near 3e-7. */
+                         near 2e-7. */
 } wcs_options;
 
 typedef struct wcs_info {

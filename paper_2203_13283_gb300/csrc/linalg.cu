@@ -401,7 +401,7 @@ int gram_matrix(const zd* X, int64_t ld, int64_t m, int b, zd* G, zd* work, cuda
 // factorisation stops when it is <= rel_tol^2 times the first pivot (or <= 0).
 __global__ void k_pchol(zd* Gm, int b, double rel_tol, int* perm, int* rank_out) {
   extern __shared__ zd G[];
-  __shared__ double best_s, dmax_s;
+  __shared__ double best_s, dmax_s, rjj_s, rinv_s;
   __shared__ int piv_s, perm_s[64];
   const int tid = threadIdx.x;
   for (int u = tid; u < b * b; u += blockDim.x) G[u] = Gm[u];
@@ -446,19 +446,31 @@ __global__ void k_pchol(zd* Gm, int b, double rel_tol, int* perm, int* rank_out)
       if (tid == 0) { int t = perm_s[j]; perm_s[j] = perm_s[p]; perm_s[p] = t; }
       __syncthreads();
     }
-    const double rjj = sqrt(G[j * b + j].x);
+    // sqrt and reciprocal once: on the FP64 pipe of one SM, 512 copies of
+    // them would cost more than the whole Schur update of the step
+    if (tid == 0) {
+      rjj_s = sqrt(G[j * b + j].x);
+      rinv_s = 1.0 / rjj_s;
+    }
     __syncthreads();
+    const double rjj = rjj_s, rinv = rinv_s;
     // row j of R: R[j, i] = G[j, i] / rjj  (G[j, i] at column i, row j)
     for (int i = tid; i < b; i += blockDim.x) {
-      if (i > j) G[i * b + j] = (1.0 / rjj) * G[i * b + j];
+      if (i > j) G[i * b + j] = rinv * G[i * b + j];
       if (i == j) G[j * b + j] = mkz(rjj);
     }
     __syncthreads();
-    // Schur complement: G[l, i] -= conj(R[j, l]) R[j, i], l, i > j
-    const int rem = b - j - 1;
-    for (int u = tid; u < rem * rem; u += blockDim.x) {
-      const int l = j + 1 + u % rem, i = j + 1 + u / rem;
-      G[i * b + l] -= conj(G[l * b + j]) * G[i * b + j];
+    // Schur complement: G[l, i] -= conj(R[j, l]) R[j, i] for j < l <= i
+    // (warp w: columns i = j + 1 + w + 16 t; lanes: rows l), mirrored into
+    // the lower triangle, which the pivot swaps read
+    const int warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+    for (int i = j + 1 + warp; i < b; i += nw) {
+      const zd rji = G[i * b + j];
+      for (int l = j + 1 + lane; l <= i; l += 32) {
+        const zd v = G[i * b + l] - conj(G[l * b + j]) * rji;
+        G[i * b + l] = v;
+        if (l < i) G[l * b + i] = conj(v);
+      }
     }
     __syncthreads();
   }
@@ -492,27 +504,37 @@ int pivoted_cholesky(zd* Gm, int b, double rel_tol, int* perm, int* rank_dev, cu
 // is independent: no dependency chain through memory, so the FP64 pipe is
 // the bound.
 __global__ void k_tri_inv(const zd* R, int b, const int* rank_dev, zd* Z) {
-  __shared__ zd zl_s;
-  const int r = *rank_dev, c = blockIdx.x, i = threadIdx.x;
+  extern __shared__ zd Rs[];   // R[0:c+1, 0:c+1], column-major, ld c + 1 (64 KB at c = 63)
+  __shared__ zd dinv[64], zl_s;
+  const int r = *rank_dev, c = blockIdx.x, i = threadIdx.x, n = c + 1;
   if (c >= r) return;
+  for (int u = i; u < n * n; u += blockDim.x) {
+    const int row = u % n, col = u / n;
+    Rs[u] = (row <= col) ? R[col * b + row] : mkz(0.0);
+  }
+  if (i < n) dinv[i] = zrecip(R[i * b + i]);
+  __syncthreads();
   zd s = mkz(i == c ? 1.0 : 0.0);
   for (int l = c; l >= 0; --l) {
     if (i == l) {
-      zl_s = s * zrecip(R[l * b + l]);
+      zl_s = s * dinv[l];
       Z[c * r + l] = zl_s;
     }
     __syncthreads();
     const zd z = zl_s;
-    if (i < l) s -= R[l * b + i] * z;
+    if (i < l) s -= Rs[l * n + i] * z;
     __syncthreads();
   }
   for (int u = c + 1 + i; u < r; u += blockDim.x) Z[c * r + u] = mkz(0.0);
 }
 
-constexpr int TRSM_ROWS = 32, TRSM_COLS = 16;   // rows per CTA; columns per warp
+constexpr int TRSM_ROWS = 32;   // rows per CTA
 
-// 4 warps: warp g forms columns 16 g .. 16 g + 15 of 32 rows; X tile and Z in
-// shared memory (Z read as broadcasts, X row-consecutive across the lanes).
+// 4 warps: warp g forms columns g, g + 4, ..., g + 60 of 32 rows (interleaved,
+// so the triangle's work is even over the warps), each column over its own
+// l <= c only (a predicated-off FP64 FMA still takes its issue slot in the
+// FP64 pipe); X tile and Z in shared memory (Z read as broadcasts, X
+// row-consecutive across the lanes).
 __global__ void __launch_bounds__(128) k_trsm_apply(const zd* X, int64_t ldx, int64_t m, const zd* Z,
                                                     const int* perm, const int* rank_dev, zd* Y,
                                                     int64_t ldy) {
@@ -528,41 +550,37 @@ __global__ void __launch_bounds__(128) k_trsm_apply(const zd* X, int64_t ldx, in
     xs[u] = (row0 + rr < m) ? X[(int64_t)perm[l] * ldx + row0 + rr] : mkz(0.0);
   }
   __syncthreads();
-  const int c0 = g * TRSM_COLS;
-  if (c0 >= r) return;
-  zd acc[TRSM_COLS];
-#pragma unroll
-  for (int k = 0; k < TRSM_COLS; ++k) acc[k] = mkz(0.0);
-  const int lmax = min(r, c0 + TRSM_COLS);
-  for (int l = 0; l < lmax; ++l) {
-    const zd x = xs[l * TRSM_ROWS + lane];
-#pragma unroll
-    for (int k = 0; k < TRSM_COLS; ++k) {
-      const int c = c0 + k;
-      if (c < r && l <= c) zfma(acc[k], x, Zs[c * r + l]);
-    }
-  }
   const int64_t i = row0 + lane;
-  if (i >= m) return;
-#pragma unroll
-  for (int k = 0; k < TRSM_COLS; ++k)
-    if (c0 + k < r) Y[(int64_t)(c0 + k) * ldy + i] = acc[k];
+  for (int c = g; c < r; c += 4) {
+    // two partial sums (even and odd l) for two independent FMA chains
+    zd a0 = mkz(0.0), a1 = mkz(0.0);
+    const zd* zc = Zs + c * r;
+    int l = 0;
+    for (; l + 1 <= c; l += 2) {
+      zfma(a0, xs[l * TRSM_ROWS + lane], zc[l]);
+      zfma(a1, xs[(l + 1) * TRSM_ROWS + lane], zc[l + 1]);
+    }
+    if (l == c) zfma(a0, xs[l * TRSM_ROWS + lane], zc[l]);
+    if (i < m) Y[(int64_t)c * ldy + i] = a0 + a1;
+  }
 }
 
 int trsm_right_upper(const zd* X, int64_t ldx, int64_t m, const zd* R, int b, const int* perm,
                      const int* rank_dev, int rank_host, zd* Y, int64_t ldy, zd* work, cudaStream_t s) {
   if (b > 64 || rank_host > b) { set_error("trsm: block too wide"); return 1; }
   if (rank_host <= 0) return 0;
-  k_tri_inv<<<(unsigned)rank_host, 64, 0, s>>>(R, b, rank_dev, work);
-  note_launch();
-  const size_t smem = sizeof(zd) * ((size_t)rank_host * rank_host + (size_t)rank_host * TRSM_ROWS);
   static DeviceOnce attr;
   if (attr.need()) {
     cudaError_t e = cudaFuncSetAttribute(k_trsm_apply, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(zd) * (64 * 64 + 64 * TRSM_ROWS)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tri_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(zd) * 64 * 64));
     if (e != cudaSuccess) { set_error(std::string("trsm: ") + cudaGetErrorString(e)); return 3; }
     attr.done();
   }
+  k_tri_inv<<<(unsigned)rank_host, 64, sizeof(zd) * rank_host * rank_host, s>>>(R, b, rank_dev, work);
+  note_launch();
+  const size_t smem = sizeof(zd) * ((size_t)rank_host * rank_host + (size_t)rank_host * TRSM_ROWS);
   k_trsm_apply<<<(unsigned)((m + TRSM_ROWS - 1) / TRSM_ROWS), 128, smem, s>>>(X, ldx, m, work, perm, rank_dev,
                                                                                 Y, ldy);
   note_launch();

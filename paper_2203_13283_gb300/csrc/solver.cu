@@ -203,12 +203,13 @@ static int check_tc(wcs_ctx* c);
 
 // Precision of a tensor-core operator product (mixed form):
 //   PREC_FAST      two leading planes, one accumulator over all of K (~1e-4 at
-//                  K ~ 1e5): skeleton sampling, Woodbury products
+//                  K ~ 1e5): Woodbury products, the range finder's projections
 //   PREC_ACCURATE  all stored planes, accumulator drained every ACC_DRAIN
 //                  K = 16 steps (~1e-7): refinement residual
 //   PREC_PERIODIC  two leading planes, accumulator drained every 64 steps
 //                  (~1e-5): residual updates R <- R - C dx, whose error scales
-//                  with |dx|
+//                  with |dx|; the skeleton's samples and V_w (the wide-tile
+//                  kernel is also the faster one at these widths)
 //   PREC_FAST1     leading plane only, one product (~4e-3): optional skeleton
 //                  sampling (sample_planes = 1)
 //   PREC_EXACT     fixed-point slices of operator and vector, integer
@@ -1306,7 +1307,7 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
       TRY(dbg_check(c, Om, N, batch_cols, N, "gaussian"));
       offset += (uint64_t)N * batch_cols;
       TRY(apply_remainder(c, Om, N, Ys, N, batch_cols, false,
-                          (c->mixed && c->opt.sample_planes == 1) ? PREC_FAST1 : PREC_FAST));
+                          (c->mixed && c->opt.sample_planes == 1) ? PREC_FAST1 : PREC_PERIODIC));
       TRY(dbg_check(c, Ys, N, batch_cols, N, "sample"));
     }
     zd* Y = Ys + batch_used * N;
@@ -1379,7 +1380,7 @@ int wcs_skeleton(wcs_ctx* c, double tol, int max_rank, uint64_t seed, int* rank_
   TRY(ensure_work(c, wide));
   for (int64_t c0 = 0; c0 < ell; c0 += wide) {
     const int64_t cc = std::min<int64_t>(wide, ell - c0);
-    TRY(apply_remainder(c, Q + c0 * N, N, c->Vw.z() + c0 * N, N, cc, true));
+    TRY(apply_remainder(c, Q + c0 * N, N, c->Vw.z() + c0 * N, N, cc, true, PREC_PERIODIC));
   }
   TRY(sync(c));
   if (rank_out) *rank_out = (int)ell;
@@ -2034,7 +2035,7 @@ static int solve_block(wcs_ctx* c, const zd* b, int64_t ldb, zd* x, int64_t ldx,
         // the update's error is ~2e-5 of |C dx| ~ the carried residual in the
         // periodic drain: while that would exceed a tenth of the target (a
         // poor approximate inverse, a large residual), the drained product
-        // (~3e-7) carries it instead, so the carried residual does not drift
+        // (~2e-7) carries it instead, so the carried residual does not drift
         // from the true one
         const int m = (2e-5 * upd <= 0.1 * c->opt.refine_tol) ? PREC_PERIODIC : PREC_ACCURATE;
         TRY(apply_C(c, dx, N, T, N, cc, adj, m));

@@ -10,7 +10,7 @@ residual (wcs_options.exact_residual).
   decades across chunks and within chunks, and K not a multiple of 1024.
   The drained split-bf16 product of the same inputs is ~1e-7 off.
 * The mixed form with exact residuals refines to 1e-11 against its stored
-  operator, where the drained residual stalls near 3e-7, and its solutions
+  operator, where the drained residual stalls near 2e-7, and its solutions
   stay within 1e-6 of the dense FP64 oracle (the operator's own accuracy)."""
 
 import numpy as np
