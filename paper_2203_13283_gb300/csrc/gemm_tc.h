@@ -91,8 +91,10 @@ int gemm_tc(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s)
 // and args.ws_elems >= that need, so two callers that provide the need get
 // identical results.
 int gemm_tc_split_plan(int M, int Nc, int K, int planesA, int planesB, int epi, int64_t* ws_elems);
-// Same contraction with the accumulator drained every K = 16 step into
-// compensated FP32 registers (accuracy ~1e-7 independent of K).
+// Same contraction with the accumulator drained into two-level FP32 register
+// sums every args.drain K = 16 steps (accuracy ~1e-7 independent of K for
+// drain 1, and for drain 4, where each K = 64 stage is one group issued
+// product-major).
 int gemm_tc_accurate(const TcOperand& A, const TcOperand& B, TcArgs args, cudaStream_t s);
 
 // Product lists for 1, 2 or 3 planes per operand (terms of order <= planes-1),
