@@ -235,6 +235,7 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
                 else "k_assemble_fast_superellipse_n4096_zfast9.md")
         fpu, fsrc = profile_figure(prof, "fp64_flops_per_far_point_pair" if fp64 else "fp32_flops_per_far_point_pair")
         bpu, _ = profile_figure(prof, "dram_bytes_per_far_point_pair")
+        busy, _ = profile_figure(prof, "pipe_active_frac")
         peak = fma.get(64 if fp64 else 32)
         name = ("k_assemble<1> (FP64 point-pair integration, tiles within k R < zfast)" if fp64
                 else "k_assemble_fast (FP32 far point pairs, k R >= zfast)")
@@ -250,7 +251,12 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
                 "work": f"far point pairs (element pairs of the kernel's tiles x q_far^2) = {units:.3e} per launch "
                         f"x {fpu:.0f} counted {'FP64' if fp64 else 'FP32'} flops per pair",
                 "peak_source": f"{'FP64' if fp64 else 'FP32'} FMA issue rate measured by wcs_fma_rate in this run",
-                "figures_source": fsrc, "launches": per, "ms_total": v["ms"]}
+                "figures_source": fsrc, "launches": per, "ms_total": v["ms"],
+                # the pipe's busy fraction under ncu (same capture): the counted
+                # flops are its algorithmic part, the rest of its issue is the
+                # sqrt, reciprocal, sincos and exp sequences and conversions
+                "pipe_active_frac": busy,
+                "pipe": "FP64 pipe" if fp64 else "FMA (FP32) pipe"}
     return None
 
 
