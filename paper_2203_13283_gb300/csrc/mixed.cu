@@ -1,23 +1,11 @@
-// Staging of FP64 data into split-bf16 planes for the tensor-core contraction.
-// x = p0 + p1 (+ p2): p0 = bf16(x), p1 = bf16(x - p0), p2 = bf16(x - p0 - p1),
-// all with round-to-nearest, so each extra plane adds about 8 bits.
-#include <cuda_bf16.h>
-
+// Staging of FP64 data into split-bf16 planes for the tensor-core contraction
+// (split.cuh: x = p0 + p1 (+ p2), each plane the exact remainder rounded to
+// nearest, formed with integer operations so that staging runs at memory
+// speed rather than at GB300's FP64 rate).
 #include "gemm_tc.h"
+#include "split.cuh"
 
 namespace wcs {
-
-__device__ __forceinline__ void split3(double x, int planes, uint16_t* o0, uint16_t* o1, uint16_t* o2) {
-  __nv_bfloat16 h0 = __double2bfloat16(x);
-  double r = x - (double)__bfloat162float(h0);
-  *o0 = __bfloat16_as_ushort(h0);
-  if (planes > 1) {
-    __nv_bfloat16 h1 = __double2bfloat16(r);
-    r -= (double)__bfloat162float(h1);
-    *o1 = __bfloat16_as_ushort(h1);
-    if (planes > 2) *o2 = __bfloat16_as_ushort(__double2bfloat16(r));
-  }
-}
 
 __global__ void k_split_real(const double* X, int64_t rows, int64_t cols, int64_t ld, int planes,
                              uint16_t* p0, uint16_t* p1, uint16_t* p2, int64_t ldp) {
@@ -26,7 +14,7 @@ __global__ void k_split_real(const double* X, int64_t rows, int64_t cols, int64_
   if (c >= cols) return;
   const int64_t o = r * ldp + c;
   uint16_t d1, d2;
-  split3(X[r * ld + c], planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
+  split3_bits(X[r * ld + c], planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
 }
 
 int split_real_f64(const double* X, int64_t rows, int64_t cols, int64_t ld, int planes, uint16_t* const* P,
@@ -55,14 +43,20 @@ __global__ void k_stage_rhs(const zd* X, int64_t n, int64_t B, int64_t ldx, int 
   if (i >= n) return;
   zd x = X[j * ldx + i];
   if (conj_in) x.y = -x.y;
-  // row 2j: (Re x, -Im x); row 2j+1: (Im x, Re x)
-  const double v[4] = {x.x, -x.y, x.y, x.x};
-  const int64_t o[4] = {(2 * j) * ldp + 2 * i, (2 * j) * ldp + 2 * i + 1, (2 * j + 1) * ldp + 2 * i,
-                        (2 * j + 1) * ldp + 2 * i + 1};
-  uint16_t d1, d2;
+  // row 2j: (Re x, -Im x); row 2j+1: (Im x, Re x), each pair one 32-bit store
+  // (ldp and 2 i are even)
+  uint16_t re[3] = {0, 0, 0}, im[3] = {0, 0, 0}, nim[3] = {0, 0, 0};
+  split3_bits(x.x, planes, &re[0], &re[1], &re[2]);
+  split3_bits(x.y, planes, &im[0], &im[1], &im[2]);
+  split3_bits(-x.y, planes, &nim[0], &nim[1], &nim[2]);
+  uint16_t* P[3] = {p0, p1, p2};
+  const int64_t o0 = (2 * j) * ldp + 2 * i, o1 = (2 * j + 1) * ldp + 2 * i;
 #pragma unroll
-  for (int t = 0; t < 4; ++t)
-    split3(v[t], planes, p0 + o[t], planes > 1 ? p1 + o[t] : &d1, planes > 2 ? p2 + o[t] : &d2);
+  for (int t = 0; t < 3; ++t) {
+    if (t >= planes) break;
+    *(uint32_t*)(P[t] + o0) = (uint32_t)re[t] | ((uint32_t)nim[t] << 16);
+    *(uint32_t*)(P[t] + o1) = (uint32_t)im[t] | ((uint32_t)re[t] << 16);
+  }
 }
 
 int stage_rhs(const zd* X, int64_t n, int64_t B, int64_t ldx, int conj_in, int planes, uint16_t* const* P,
@@ -86,12 +80,16 @@ __global__ void k_stage_view(const zd* X, int64_t rows, int64_t cols, int64_t rs
   const int64_t i = blockIdx.y;
   if (j >= cols) return;
   const zd x = X[i * rs + j * cs];
-  const double v[2] = {x.x, conj ? -x.y : x.y};
-  uint16_t d1, d2;
+  // (Re x, Im x) adjacent: one 32-bit store per plane (ldp and 2 j are even)
+  uint16_t re[3] = {0, 0, 0}, im[3] = {0, 0, 0};
+  split3_bits(x.x, planes, &re[0], &re[1], &re[2]);
+  split3_bits(conj ? -x.y : x.y, planes, &im[0], &im[1], &im[2]);
+  uint16_t* P[3] = {p0, p1, p2};
+  const int64_t o = i * ldp + 2 * j;
 #pragma unroll
-  for (int t = 0; t < 2; ++t) {
-    const int64_t o = i * ldp + 2 * j + t;
-    split3(v[t], planes, p0 + o, planes > 1 ? p1 + o : &d1, planes > 2 ? p2 + o : &d2);
+  for (int t = 0; t < 3; ++t) {
+    if (t >= planes) break;
+    *(uint32_t*)(P[t] + o) = (uint32_t)re[t] | ((uint32_t)im[t] << 16);
   }
 }
 
