@@ -218,11 +218,13 @@ int wcs_skeleton(wcs_ctx* ctx, double tol, int max_rank, uint64_t seed, int* ran
 /* Factor C = C_c (I + C_c^{-1} U V^T) (Eq. 8): W = C_c^{-1} U by FFT, the
  * capacitance matrix K = I + V^T W and its inverse, for the Woodbury identity
  * of Eq. (9).  K^-1: FP64 Gauss-Jordan in the FP64 form and for rank < 256;
- * in the mixed form otherwise a Newton-Schulz iteration on the tensor cores
- * closed by two steps with exact fixed-point products (its residual
- * ||I - K K^-1||_F / sqrt(rank), ~1e-11, is reported in
- * wcs_info.capacitance_residual).  Returns WCS_ERR_SINGULAR when K is
- * singular or the iteration does not converge. */
+ * in the mixed form otherwise a Newton-Schulz iteration on the tensor cores,
+ * closed by one step with the drained three-plane product and then by steps
+ * with exact fixed-point products until ||I - K K^-1||_F / sqrt(rank),
+ * measured with an exact product after each, is below 1e-10 (at most three;
+ * ~3e-11 at rank 4096; reported in wcs_info.capacitance_residual).  Returns
+ * WCS_ERR_SINGULAR when K is singular, the iteration does not converge, or
+ * the closing steps leave that residual at 1e-6 or above. */
 int wcs_factor(wcs_ctx* ctx);
 
 /* Checkpoint of a factored context.  The paper defines no file format; this
