@@ -473,7 +473,8 @@ int wcs_profile(wcs_ctx* ctx, int enable);
  * FP32 far-pair assembly kernel (work = far point pairs of its tiles; the
  * assembly category then counts the FP64 kernel over the other tiles),
  * periodically drained tensor-core contraction (work as the first; the
- * drained category then counts the every-step drain only).
+ * drained category then counts the three-plane product drained once per
+ * K = 64 stage only).
  * reset != 0 clears the records. */
 int wcs_profile_read(wcs_ctx* ctx, int reset, double* out_host);
 
