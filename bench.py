@@ -210,9 +210,14 @@ def roofline_entry(cat, prof, hbm, bf16s, fma):
         prof_file = {"gemm_tc": "k_gemm_tc_ellipse_n4096_mixed.md", "gemm_tc_acc": "k_gemm_tc_acc_ellipse_n4096_mixed.md",
                      "gemm_tc_per": "k_gemm_tc_per_superellipse_n4096_mixed.md"}[cat]
         ratio, src = profile_figure(prof_file, "dram_bytes_per_algorithmic_byte")
+        changed, _ = profile_figure(prof_file, "kernel_changed_since_capture")
+        if changed:
+            ratio = None   # counters taken before the kernel last changed: no traffic figure
         return {"bound": "tensor", "achieved": achieved, "peak": bf16s, "unit": "TFLOP/s", "frac": achieved / bf16s,
                 "issued_frac": nprod * achieved / bf16s,
                 "traffic": (ratio * v["bytes"] / per) if ratio else None,
+                "traffic_note": ("kernel changed since its ncu capture (epilogue); traffic withheld until recaptured"
+                                 if changed else None),
                 "algorithmic_bytes_per_launch": v["bytes"] / per, "traffic_source": src,
                 "kernel": f"{name} (tcgen05 split-bf16 complex operator product, {mode})",
                 "work": f"useful complex-product flops 2*M*Nc*K; split-bf16 issues {nprod} products of these "
